@@ -1,0 +1,399 @@
+"""Walker-step throughput of the GB300 ph-AFQMC library.
+
+One bench step is one measurement block of the hot path: 20 imaginary-time
+steps of every walker (force bias, field draw, one-body operator, Taylor
+propagation, overlaps, weights), with orthonormalisation every 2 steps and
+the local energy plus comb population control at the end of the block. The
+metric is walker-steps per second over the whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c1|c3] [--precision fp64|fp32|tf32|tf32x3]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own Philox
+stream tag); there is no data-path collective. The reference arm times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s"
+BLOCK = 20  # imaginary-time steps per bench step (one measurement/comb block)
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 and FP32 SIMT peaks from unit counts: 152 SMs at the 2070 MHz maximum
+# clock; FP32 128 FMA lanes per SM, FP64 from the nominal 1.25 TFLOP/s.
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP32_SIMT_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_TFLOPS = 1.25
+TF32_OVER_BF16 = 0.5   # nominal dense TF32 : BF16 tensor throughput
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, rank=0):
+    from synth import CONFIGS
+    s = CONFIGS[name]()
+    return s.replace(run_id=rank)
+
+
+def describe(s):
+    return (f"{s.name}: M={s.M} N={s.n_up}+{s.n_dn} n_chol={s.n_chol} "
+            f"W={s.n_walkers} dtau={s.dtau} det={s.n_det}")
+
+
+# ------------------------------------------------------------------ peaks
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def roofline_for(kernel_stats, precision, peaks, src):
+    """Dominant kernel of the timed region against its bound."""
+    best = max(kernel_stats.items(), key=lambda kv: kv[1]["total_ms"])
+    name, st = best
+    avg_s = st["total_ms"] / max(1, st["launches"]) / 1e3
+    if st["is_bytes"]:
+        bound, unit = "hbm", "GB/s"
+        achieved = st["work"] / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        peak_src = f"hbm_gbs ({src})"
+    elif precision == "fp64":
+        bound, unit = "alu", "TFLOP/s"
+        achieved = st["work"] / avg_s / 1e12
+        peak = FP64_TFLOPS
+        peak_src = "FP64 nominal 1.25 TFLOP/s"
+    elif precision == "fp32":
+        bound, unit = "alu", "TFLOP/s"
+        achieved = st["work"] / avg_s / 1e12
+        peak = FP32_SIMT_TFLOPS
+        peak_src = "FP32 SIMT: 152 SM x 128 lanes x 2 x 2070 MHz"
+    else:
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = st["work"] / avg_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * TF32_OVER_BF16
+        peak_src = f"bf16 sustained ({src}) x 0.5 nominal TF32 ratio"
+    traffic = lookup_traffic(name, precision)
+    return {"kernel": name, "bound": bound, "achieved": round(achieved, 3),
+            "peak": round(peak, 3), "unit": unit, "frac": round(achieved / peak, 4),
+            "peak_source": peak_src,
+            "traffic": traffic,
+            "launches": st["launches"], "avg_launch_us": round(avg_s * 1e6, 2),
+            "work_per_launch": st["work"]}
+
+
+def lookup_traffic(kernel, precision):
+    """DRAM bytes per launch from the committed ncu summary, if one matches."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        t = line.split()
+        if len(t) >= 4 and not line.startswith("#") and t[0] == kernel and t[1] == precision:
+            return float(t[2])
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
+        mx = max((float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 4 + i and r[4 + i].lower() == "active":
+                    reasons.add(n)
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+_WORKER_SYSTEM = {}
+
+
+def _oracle_init(name):
+    # never raise here: a failing pool initializer respawns workers forever
+    try:
+        from synth import CONFIGS
+        import oracle.afqmc  # noqa: F401
+        _WORKER_SYSTEM[name] = CONFIGS[name]().replace(measure_every=0, pc_every=0)
+    except Exception as e:  # reported by the first task
+        _WORKER_SYSTEM["error"] = repr(e)
+
+
+def _oracle_worker(args):
+    name, walker_ids, n_steps = args
+    if "error" in _WORKER_SYSTEM:
+        raise RuntimeError(_WORKER_SYSTEM["error"])
+    from oracle import afqmc as O
+    s = _WORKER_SYSTEM[name]
+    run = O.OracleRun(s, walker_ids=walker_ids)
+    t0 = time.perf_counter()
+    run.run(n_steps)
+    if n_steps >= BLOCK:
+        run.local_energies()      # the block's one energy measurement
+    return time.perf_counter() - t0
+
+
+def cpu_oracle(name, budget_s=20.0):
+    """The FP64 oracle as it stands, one process per host core (spawned, one
+    BLAS thread each), each following its own walkers for a few steps plus
+    one energy measurement. Returns (walker-steps/s, cores, sample text)."""
+    import multiprocessing as mp
+    from synth import CONFIGS
+    s = CONFIGS[name]()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    # probe: one walker, one step, to size the sample to the budget
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1")
+    old = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+    os.environ.update({"OPENBLAS_NUM_THREADS": "1", "OMP_NUM_THREADS": "1"})
+    try:
+        with ctx.Pool(cores, initializer=_oracle_init, initargs=(name,)) as pool:
+            t1 = pool.map(_oracle_worker, [(name, [0], 2)])[0]
+            per_ws = max(t1 / 2.0, 1e-5)
+            steps = BLOCK        # one block: ortho every 2, energy at the end
+            per_core = max(1, int(budget_s / (per_ws * steps)))
+            per_core = min(per_core, max(1, s.n_walkers // cores))
+            jobs = [(name, list(range(c * per_core, (c + 1) * per_core)), steps)
+                    for c in range(cores)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, jobs)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    ws = cores * per_core * steps
+    sample = (f"{describe(s)}; {cores} processes x {per_core} walkers x {steps} steps "
+              f"(orthonormalisation every 2, one local-energy evaluation at the end, "
+              f"no comb); full M, N, n_chol")
+    return ws / wall, cores, sample
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1804_03310_gb300 import Afqmc
+
+    s = workload(args.workload, rank)
+    s = s.replace(measure_every=BLOCK, pc_every=BLOCK, ortho_every=2)
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        return _timed(args, s, stream, rank, world)
+
+
+def _timed(args, s, stream, rank, world):
+    import torch
+    from paper_1804_03310_gb300 import Afqmc
+    ctx = Afqmc.from_system(s, precision=args.precision, stream=stream.cuda_stream)
+    flush = torch.zeros(256 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    for _ in range(args.warmup):
+        ctx.afqmc_propagate(BLOCK)
+    torch.cuda.synchronize()
+    ctx.afqmc_set_kernel_timing(True)
+    n0 = ctx.afqmc_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    with ClockSampler(rank % max(1, torch.cuda.device_count())) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.afqmc_propagate(BLOCK)
+            b.record(stream)
+            b.synchronize()
+            total_ms += a.elapsed_time(b)
+    torch.cuda.synchronize()
+    launches = ctx.afqmc_launch_count() - n0
+    from paper_1804_03310_gb300 import KERNEL_IDS
+    kstats = {k: ctx.afqmc_kernel_stats(k) for k in KERNEL_IDS}
+    kstats = {k: v for k, v in kstats.items() if v["launches"] > 0}
+    ctx.afqmc_synchronize()
+    hist = ctx.afqmc_energy_history()
+    ctx.close()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    e2e = None if args.no_e2e else run_e2e(args, s)
+    return s, total_ms, launches, kstats, clk.summary(), hist, e2e
+
+
+def run_e2e(args, s):
+    """Same metric through the public API with host buffers: create (host
+    inputs copied to the device), K blocks each ending with the weights and
+    local energies read back to the host, destroy."""
+    import numpy as np
+    import torch
+    from paper_1804_03310_gb300 import Afqmc
+    h2d = (s.h1.nbytes + s.L.nbytes + s.C_up.nbytes + s.C_dn.nbytes + s.occ_up.nbytes
+           + s.occ_dn.nbytes + s.ci.nbytes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = Afqmc.from_system(s, precision=args.precision)
+    d2h = 0
+    for _ in range(args.steps):
+        ctx.afqmc_propagate(BLOCK)
+        w, lo = ctx.afqmc_weights()
+        e, em = ctx.afqmc_local_energy()
+        d2h += w.nbytes + lo.nbytes + e.nbytes + 8
+    ctx.close()
+    wall = time.perf_counter() - t0
+    return {"value": round(s.n_walkers * BLOCK * args.steps / wall, 1), "unit": METRIC,
+            "h2d_bytes_per_step": int(h2d / args.steps),
+            "d2h_bytes_per_step": int(d2h / args.steps),
+            "includes": "context creation with setup precompute, host read-back every block"}
+
+
+def dtype_of(precision):
+    return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[precision]
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return reference_arm(args)
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    s, total_ms, launches, kstats, clocks, hist, e2e = run_ours(args, rank, world)
+    if rank != 0:
+        return 0
+    peaks, src = load_peaks()
+    ws = s.n_walkers * BLOCK * args.steps * world
+    value = ws / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.precision),
+        "data": "synthetic (seeded Hamiltonian and trial of the workload's shape)",
+        "config": {"workload": describe(s), "precision": args.precision,
+                   "step": f"{BLOCK} imaginary-time steps: ortho every 2, energy + comb at the end",
+                   "l2": "flushed (256 MB write) between timed iterations",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "gpu_launches": int(launches),
+        "roofline": roofline_for(kstats, args.precision, peaks, src),
+        "kernels_ms": {k: round(v["total_ms"], 3) for k, v in kstats.items()},
+        "clocks": clocks,
+        "energy_last": float(hist[-1][1]) if len(hist) else None,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        v, cores, sample = cpu_oracle(args.workload)
+        line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    print(json.dumps(line))
+    return 0
+
+
+def reference_arm(args):
+    from synth import CONFIGS
+    s = CONFIGS[args.workload]()
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.warmup + args.steps):
+        v, cores, sample = cpu_oracle(args.workload, budget_s=8.0)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    timed = vals[args.warmup:]
+    value = sum(timed) / len(timed)
+    line = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(wall / max(1, len(vals)) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": describe(s), "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": round(value, 2), "unit": METRIC, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 2), "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

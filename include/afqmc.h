@@ -1,0 +1,197 @@
+/*
+ * afqmc.h - C ABI of the GB300 ph-AFQMC walker-step library (libafqmc.so).
+ *
+ * The library propagates a population of Slater-determinant walkers in
+ * imaginary time with the phaseless auxiliary-field QMC step of Shee et al.
+ * (arXiv:1804.03310): force bias, auxiliary-field draw and hybrid weight with
+ * the phaseless cut (Sec. II), the one-body operator sum_g x_g L_g and its
+ * Taylor exponential applied to the walker orbitals (Sec. II, Eq. 2-3,
+ * Thouless propagation by matrix products), overlaps and Green's functions
+ * from batched small inverses and Sherman-Morrison-Woodbury updates for
+ * multi-determinant trials (Sec. III, Eq. 4), the local energy through the
+ * precomputed trial-contracted tensor (Sec. III, Eq. 5), walker
+ * orthonormalisation and comb population control (Sec. IV.A, Sec. V).
+ *
+ * Conventions for every call:
+ *  - Matrices are row-major, double precision, on the HOST unless a
+ *    parameter says "device". Complex numbers are two doubles (re, im).
+ *  - Inputs are copied during the call; the caller keeps ownership of all
+ *    buffers it passes. Outputs go to caller-allocated host buffers.
+ *  - Every call returns an afqmc_status. Nothing aborts, traps or exits.
+ *    After a failure afqmc_last_error(ctx) describes it. A context that hit
+ *    AFQMC_E_CUDA is poisoned: only afqmc_last_error and afqmc_destroy are
+ *    then accepted.
+ *  - All GPU work of a context is issued on its stream (the caller's stream
+ *    when one is given at creation). Calls returning host data synchronise
+ *    that stream. Calls on one context are not thread-safe.
+ *  - All device memory a context uses is allocated in afqmc_create and freed
+ *    in afqmc_destroy; propagation allocates nothing.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afqmc_ctx afqmc_ctx;
+
+typedef enum {
+  AFQMC_OK = 0,
+  AFQMC_E_INVALID = 1,    /* bad argument or unsupported size */
+  AFQMC_E_OOM = 2,        /* device allocation failed */
+  AFQMC_E_CUDA = 3,       /* a CUDA call failed; the context is poisoned */
+  AFQMC_E_POPULATION = 4, /* every walker weight is zero (comb impossible) */
+  AFQMC_E_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+  AFQMC_E_NUMERIC = 6,    /* non-finite setup quantity (e.g. trial energy) */
+  AFQMC_E_STATE = 7       /* checkpoint buffer does not match the context */
+} afqmc_status;
+
+/* Arithmetic of the walker step.
+ * FP64:    complex128 walkers, every contraction in FP64.
+ * FP32:    complex64 walkers, FP32 SIMT contractions.
+ * TF32:    complex64 walkers, dense contractions on tcgen05 tensor cores with
+ *          TF32 operands and FP32 accumulation.
+ * TF32X3:  as TF32 with split (hi + lo) operands, three products per term.
+ * The mixed modes keep FP64 for log-determinants, orthonormalisation, weights
+ * and population-control sums. */
+typedef enum {
+  AFQMC_FP64 = 0,
+  AFQMC_FP32 = 1,
+  AFQMC_TF32 = 2,
+  AFQMC_TF32X3 = 3
+} afqmc_precision;
+
+typedef struct {
+  int32_t M;             /* orbitals (one-particle basis size), 1..256 */
+  int32_t n_up, n_dn;    /* electrons per spin, 0..M each, n_up + n_dn >= 1 */
+  int32_t n_chol;        /* Cholesky / density-fitting vectors L_g, >= 1 */
+  int32_t n_det;         /* determinants in the trial, >= 1 */
+  int32_t n_walkers;     /* walkers, >= 1 */
+  double dtau;           /* imaginary-time step (Ha^-1), > 0 */
+  uint64_t seed;         /* Philox key for the field draws and the comb */
+  int32_t run_id;        /* Philox stream tag, 0 .. 2^29-1 */
+  int32_t precision;     /* afqmc_precision */
+  int32_t ortho_every;   /* orthonormalise after every k-th step (0: never) */
+  int32_t measure_every; /* local-energy measurement cadence (0: never) */
+  int32_t pc_every;      /* comb population-control cadence (0: never) */
+  int32_t taylor_order;  /* terms of the exponential's Taylor series, 1..12 */
+  double fb_cap;         /* cap on |xbar_g|; <= 0 disables the cap */
+  double e_shift;        /* energy shift E_T; NaN: local energy of the reference determinant */
+  int32_t reserved[8];   /* must be zero */
+} afqmc_params;
+
+/* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,
+ * ortho_every 2, measure_every 20, pc_every 20, everything else zero. */
+void afqmc_params_default(afqmc_params* p);
+
+/* Create a context: copy the Hamiltonian and trial to the device, precompute
+ * the one-body remainder H1' = h1 - 1/2 sum_g L_g L_g (two-body term of Eq. 1
+ * written as -1/2 sum_g v_g^2, Sec. II), B_half = exp(-dtau/2 H1') (symmetric
+ * Trotter split), the half-rotated vectors D^H L_g, the exchange part of the
+ * Eq. 5 tensor, and initialise every walker to the reference determinant with
+ * weight 1. Setup is not part of the propagation time (Sec. III).
+ *
+ *  h1      [M*M]            symmetric one-body matrix T_ij of Eq. 1
+ *  L       [n_chol*M*M]     each L_g symmetric; V_ijkl = sum_g L_g,ik L_g,jl
+ *  C_up    [M*M]            orbitals for spin up, column p = orbital p
+ *  C_dn    [M*M]            orbitals for spin down
+ *  occ_up  [n_det*n_up]     orbital indices of each determinant; row 0 is the
+ *  occ_dn  [n_det*n_dn]     reference. Determinants must be orthonormal
+ *                           (orthonormal C, distinct occupation rows).
+ *  ci      [2*n_det]        CI coefficients (re, im); |Psi_T> = sum_i c_i |D_i>
+ *  stream  cudaStream_t of the caller, or NULL for a stream the context owns.
+ *  out     receives the context.
+ * Returns AFQMC_E_INVALID for sizes outside the documented ranges or a
+ * non-orthonormal trial, AFQMC_E_OOM when device memory is short. */
+afqmc_status afqmc_create(const afqmc_params* params, const double* h1,
+                          const double* L, const double* C_up,
+                          const double* C_dn, const int32_t* occ_up,
+                          const int32_t* occ_dn, const double* ci,
+                          void* stream, afqmc_ctx** out);
+
+/* Advance every walker by n_steps imaginary-time steps (Sec. II): force
+ * bias, field draw, propagation, new overlap and hybrid phaseless weight;
+ * after step count s (1-based) orthonormalise when s % ortho_every == 0,
+ * measure the local energy when s % measure_every == 0, comb when
+ * s % pc_every == 0. Asynchronous on the context's stream; a later call that
+ * returns host data reports AFQMC_E_POPULATION if a comb found all weights 0. */
+afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t n_steps);
+
+/* Orthonormalise every walker now (modified Gram-Schmidt in FP64); the
+ * log-overlap drops by ln det R (Sec. IV.A). */
+afqmc_status afqmc_orthonormalize(afqmc_ctx* ctx);
+
+/* Comb population control now (Sec. V final comments); offset drawn from
+ * Philox stream 1 at the current step counter. */
+afqmc_status afqmc_population_control(afqmc_ctx* ctx);
+
+/* Local energy E_L = <Psi_T|H|phi>/<Psi_T|phi> of every walker (Sec. II,
+ * via Eq. 5). e_loc [2*n_walkers] (re, im) or NULL; e_mixed receives
+ * sum_w W Re E_L / sum_w W (NaN if all weights are 0), or NULL. */
+afqmc_status afqmc_local_energy(afqmc_ctx* ctx, double* e_loc, double* e_mixed);
+
+/* Walker weights [n_walkers] and, if log_ovlp is not NULL, the
+ * log-overlaps ln <Psi_T|phi> [2*n_walkers] (re, im). */
+afqmc_status afqmc_weights(afqmc_ctx* ctx, double* w, double* log_ovlp);
+
+/* Mixed Green's functions G_ij = <c+_i c_j> of one walker, [2*M*M] each
+ * (re, im interleaved, row-major); either pointer may be NULL. */
+afqmc_status afqmc_green(afqmc_ctx* ctx, int32_t walker, double* G_up,
+                         double* G_dn);
+
+/* Force bias xbar of the last step, [n_walkers * n_chol * 2] (re, im). */
+afqmc_status afqmc_force_bias(afqmc_ctx* ctx, double* xbar);
+
+/* Mixed energies recorded by measurements inside afqmc_propagate:
+ * up to max_n pairs (step count, energy) into out[2*i], out[2*i+1];
+ * *n receives the number recorded so far (history keeps the last 4096). */
+afqmc_status afqmc_energy_history(afqmc_ctx* ctx, double* out, int32_t max_n,
+                                  int32_t* n);
+
+/* Checkpoint. With buf == NULL, *bytes receives the size needed. Otherwise
+ * writes a self-describing image (header, walker orbitals as complex128
+ * [n_walkers][n_up+n_dn][M], weights, log-overlaps, step counter) of at most
+ * *bytes bytes and sets *bytes to the size written. */
+afqmc_status afqmc_get_state(afqmc_ctx* ctx, void* buf, size_t* bytes);
+
+/* Restore an image written by afqmc_get_state for a context of the same
+ * sizes (precision may differ). AFQMC_E_STATE if it does not match. The
+ * Philox counter is a pure function of (seed, run, step, walker, field), so
+ * a resumed run draws exactly the fields the uninterrupted run would. */
+afqmc_status afqmc_set_state(afqmc_ctx* ctx, const void* buf, size_t bytes);
+
+/* Wait for all work of the context. */
+afqmc_status afqmc_synchronize(afqmc_ctx* ctx);
+
+/* Per-kernel device timing, for roofline accounting. When enabled, CUDA
+ * events bracket every launch of the kernels listed below on the context's
+ * stream. afqmc_kernel_stats returns for kernel id k the number of launches,
+ * the summed device time in ms, and the algorithmic work per launch (flops
+ * for contractions, bytes for bandwidth-bound kernels; *is_bytes says which).
+ * Ids: 0 force bias, 1 field draw, 2 one-body operator, 3 propagation,
+ * 4 overlap/Green's, 5 weights, 6 orthonormalisation, 7 energy contraction,
+ * 8 comb. Returns AFQMC_E_INVALID for an unknown id. */
+afqmc_status afqmc_set_kernel_timing(afqmc_ctx* ctx, int32_t enable);
+afqmc_status afqmc_kernel_stats(afqmc_ctx* ctx, int32_t kernel_id,
+                                int64_t* launches, double* total_ms,
+                                double* work_per_launch, int32_t* is_bytes);
+#define AFQMC_N_KERNEL_IDS 9
+
+/* Number of kernel launches issued since creation (all of this library's). */
+int64_t afqmc_launch_count(const afqmc_ctx* ctx);
+
+/* Text of the last error on this context ("" if none); valid until the next
+ * call on the context. ctx may be NULL for errors of afqmc_create. */
+const char* afqmc_last_error(const afqmc_ctx* ctx);
+
+/* Free all device memory of the context and the stream it owns. */
+void afqmc_destroy(afqmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -153,6 +153,7 @@ def force_bias(L, Gu, Gd, dtau, cap):
     each xbar_g scaled down to modulus ``cap`` when larger (cap <= 0: none)."""
     X = np.einsum("gik,wik->wg", L, Gu + Gd)
     xbar = -1j * np.sqrt(dtau) * X
+    xbar = np.where(np.isfinite(xbar), xbar, 0.0)   # a walker with no defined bias
     if cap > 0:
         a = np.abs(xbar)
         xbar = np.where(a > cap, xbar * (cap / np.where(a > 0, a, 1.0)), xbar)
@@ -370,15 +371,20 @@ class OracleRun:
     == 0, measure if n % measure_every == 0, comb if n % pc_every == 0.
     """
 
-    def __init__(self, system, e_shift: Optional[float] = None):
+    def __init__(self, system, e_shift: Optional[float] = None,
+                 walker_ids=None):
         s = system
         self.s = s
+        # global walker indices (they key the Philox counters); a subset
+        # reproduces those walkers exactly until the first comb
+        self.walker_ids = (np.arange(s.n_walkers) if walker_ids is None
+                           else np.asarray(walker_ids, dtype=np.int64))
         self.trial = Trial.from_system(s)
         self.h1 = np.asarray(s.h1, dtype=np.float64)
         self.L = np.asarray(s.L, dtype=np.float64)
         self.h1p = one_body_remainder(self.h1, self.L)
         self.Bhalf = half_step_propagator(self.h1p, s.dtau)
-        W = s.n_walkers
+        W = self.walker_ids.size
         self.Phi_up = np.repeat(self.trial.D_up[0][None], W, axis=0).copy()
         self.Phi_dn = np.repeat(self.trial.D_dn[0][None], W, axis=0).copy()
         self.weight = np.ones(W)
@@ -395,7 +401,7 @@ class OracleRun:
     def fields(self, step=None):
         st = self.step_count if step is None else step
         return gaussian_fields(self.s.seed, self.s.run_id, st,
-                               np.arange(self.s.n_walkers), self.s.n_chol)
+                               self.walker_ids, self.s.n_chol)
 
     def step(self):
         s = self.s
@@ -430,17 +436,18 @@ class OracleRun:
         E = self.local_energies()
         w = self.weight
         sw = np.sum(w)
-        emix = float(np.sum(w * E.real) / sw) if sw > 0 else float("nan")
+        live = w > 0
+        emix = float(np.sum(w[live] * E.real[live]) / sw) if sw > 0 else float("nan")
         self.energies.append((self.step_count, emix, E))
         return emix, E
 
     def population_control(self):
-        u = comb_uniform(self.s.seed, self.s.run_id, self.step_count - 1)
+        u = comb_uniform(self.s.seed, self.s.run_id, self.step_count)
         parent, wnew = comb(self.weight, u)
         self.Phi_up = self.Phi_up[parent].copy()
         self.Phi_dn = self.Phi_dn[parent].copy()
         self.logO = self.logO[parent].copy()
-        self.weight = np.full(self.s.n_walkers, wnew)
+        self.weight = np.full(self.walker_ids.size, wnew)
         self.last["parent"] = parent
         return parent
 

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libafqmc.so (include/afqmc.h).
+
+Argument marshalling only: numpy arrays in, numpy arrays out, every step of
+the walker propagation runs in the library's CUDA kernels. There is no CPU
+fallback; loading fails loudly if the shared library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libafqmc.so")
+
+AFQMC_FP64, AFQMC_FP32, AFQMC_TF32, AFQMC_TF32X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": AFQMC_FP64, "fp32": AFQMC_FP32, "tf32": AFQMC_TF32,
+              "tf32x3": AFQMC_TF32X3}
+STATUS = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_POPULATION",
+          5: "E_TIMEOUT", 6: "E_NUMERIC", 7: "E_STATE"}
+KERNEL_IDS = ["force_bias", "fields", "one_body", "propagate", "overlap",
+              "weights", "orthonormalize", "energy", "comb"]
+
+
+class afqmc_params(C.Structure):
+    _fields_ = [("M", C.c_int32), ("n_up", C.c_int32), ("n_dn", C.c_int32),
+                ("n_chol", C.c_int32), ("n_det", C.c_int32),
+                ("n_walkers", C.c_int32), ("dtau", C.c_double),
+                ("seed", C.c_uint64), ("run_id", C.c_int32),
+                ("precision", C.c_int32), ("ortho_every", C.c_int32),
+                ("measure_every", C.c_int32), ("pc_every", C.c_int32),
+                ("taylor_order", C.c_int32), ("fb_cap", C.c_double),
+                ("e_shift", C.c_double), ("reserved", C.c_int32 * 8)]
+
+
+class AfqmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libafqmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_1804_03310_gb300.build`")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    d = P(C.c_double)
+    i32 = P(C.c_int32)
+    vp = C.c_void_p
+    sig = {
+        "afqmc_params_default": (None, [P(afqmc_params)]),
+        "afqmc_create": (C.c_int, [P(afqmc_params), d, d, d, d, i32, i32, d, vp, P(vp)]),
+        "afqmc_propagate": (C.c_int, [vp, C.c_int32]),
+        "afqmc_orthonormalize": (C.c_int, [vp]),
+        "afqmc_population_control": (C.c_int, [vp]),
+        "afqmc_local_energy": (C.c_int, [vp, d, d]),
+        "afqmc_weights": (C.c_int, [vp, d, d]),
+        "afqmc_green": (C.c_int, [vp, C.c_int32, d, d]),
+        "afqmc_force_bias": (C.c_int, [vp, d]),
+        "afqmc_energy_history": (C.c_int, [vp, d, C.c_int32, i32]),
+        "afqmc_get_state": (C.c_int, [vp, vp, P(C.c_size_t)]),
+        "afqmc_set_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "afqmc_synchronize": (C.c_int, [vp]),
+        "afqmc_set_kernel_timing": (C.c_int, [vp, C.c_int32]),
+        "afqmc_kernel_stats": (C.c_int, [vp, C.c_int32, P(C.c_int64), d, d, i32]),
+        "afqmc_launch_count": (C.c_int64, [vp]),
+        "afqmc_last_error": (C.c_char_p, [vp]),
+        "afqmc_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def default_params() -> afqmc_params:
+    p = afqmc_params()
+    load_library().afqmc_params_default(C.byref(p))
+    return p
+
+
+class Afqmc:
+    """One ph-AFQMC context (a population of walkers of one system)."""
+
+    def __init__(self, h1, L, C_up, C_dn, occ_up, occ_dn, ci, *, dtau,
+                 n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
+                 measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
+                 e_shift=None, stream=None):
+        lib = load_library()
+        self._lib = lib
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        L = np.ascontiguousarray(L, dtype=np.float64)
+        C_up = np.ascontiguousarray(C_up, dtype=np.float64)
+        C_dn = np.ascontiguousarray(C_dn, dtype=np.float64)
+        occ_up = np.ascontiguousarray(occ_up, dtype=np.int32)
+        occ_dn = np.ascontiguousarray(occ_dn, dtype=np.int32)
+        ci = np.ascontiguousarray(np.asarray(ci, dtype=np.complex128).view(np.float64))
+        M = h1.shape[0]
+        p = default_params()
+        p.M = M
+        p.n_up = occ_up.shape[1]
+        p.n_dn = occ_dn.shape[1]
+        p.n_chol = L.shape[0]
+        p.n_det = occ_up.shape[0]
+        p.n_walkers = n_walkers
+        p.dtau = dtau
+        p.seed = seed
+        p.run_id = run_id
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        p.ortho_every = ortho_every
+        p.measure_every = measure_every
+        p.pc_every = pc_every
+        p.taylor_order = taylor_order
+        p.fb_cap = fb_cap
+        p.e_shift = math.nan if e_shift is None else e_shift
+        self.params = p
+        self.M, self.n_up, self.n_dn = M, p.n_up, p.n_dn
+        self.n_chol, self.n_walkers = p.n_chol, n_walkers
+        self._h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        s = lib.afqmc_create(C.byref(p), _dptr(h1), _dptr(L), _dptr(C_up),
+                             _dptr(C_dn), _iptr(occ_up), _iptr(occ_dn),
+                             _dptr(ci), st, C.byref(self._h))
+        if s != 0:
+            raise AfqmcError(s, lib.afqmc_last_error(None).decode())
+
+    @classmethod
+    def from_system(cls, system, **kw):
+        args = dict(dtau=system.dtau, n_walkers=system.n_walkers,
+                    seed=system.seed, run_id=system.run_id,
+                    ortho_every=system.ortho_every,
+                    measure_every=system.measure_every,
+                    pc_every=system.pc_every, taylor_order=system.taylor_order,
+                    fb_cap=system.fb_cap)
+        args.update(kw)
+        return cls(system.h1, system.L, system.C_up, system.C_dn,
+                   system.occ_up, system.occ_dn, system.ci, **args)
+
+    # -- helpers ------------------------------------------------------------
+    def _check(self, s):
+        if s != 0:
+            raise AfqmcError(s, self._lib.afqmc_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.afqmc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the C calls ---------------------------------------------------------
+    def afqmc_propagate(self, n_steps: int):
+        self._check(self._lib.afqmc_propagate(self._h, n_steps))
+
+    def afqmc_orthonormalize(self):
+        self._check(self._lib.afqmc_orthonormalize(self._h))
+
+    def afqmc_population_control(self):
+        self._check(self._lib.afqmc_population_control(self._h))
+
+    def afqmc_local_energy(self):
+        e = np.zeros(2 * self.n_walkers)
+        em = np.zeros(1)
+        self._check(self._lib.afqmc_local_energy(self._h, _dptr(e), _dptr(em)))
+        return e.view(np.complex128), float(em[0])
+
+    def afqmc_weights(self):
+        w = np.zeros(self.n_walkers)
+        lo = np.zeros(2 * self.n_walkers)
+        self._check(self._lib.afqmc_weights(self._h, _dptr(w), _dptr(lo)))
+        return w, lo.view(np.complex128)
+
+    def afqmc_green(self, walker: int):
+        gu = np.zeros(2 * self.M * self.M)
+        gd = np.zeros(2 * self.M * self.M)
+        self._check(self._lib.afqmc_green(self._h, walker, _dptr(gu), _dptr(gd)))
+        return (gu.view(np.complex128).reshape(self.M, self.M),
+                gd.view(np.complex128).reshape(self.M, self.M))
+
+    def afqmc_force_bias(self):
+        x = np.zeros(2 * self.n_walkers * self.n_chol)
+        self._check(self._lib.afqmc_force_bias(self._h, _dptr(x)))
+        return x.view(np.complex128).reshape(self.n_walkers, self.n_chol)
+
+    def afqmc_energy_history(self):
+        n = C.c_int32()
+        self._check(self._lib.afqmc_energy_history(self._h, None, 0, C.byref(n)))
+        k = min(n.value, 4096)
+        out = np.zeros(2 * max(k, 1))
+        self._check(self._lib.afqmc_energy_history(self._h, _dptr(out), k, C.byref(n)))
+        return out[: 2 * k].reshape(k, 2)
+
+    def afqmc_get_state(self) -> bytes:
+        nb = C.c_size_t()
+        self._check(self._lib.afqmc_get_state(self._h, None, C.byref(nb)))
+        buf = C.create_string_buffer(nb.value)
+        self._check(self._lib.afqmc_get_state(self._h, buf, C.byref(nb)))
+        return buf.raw[: nb.value]
+
+    def afqmc_set_state(self, state: bytes):
+        buf = C.create_string_buffer(state, len(state))
+        self._check(self._lib.afqmc_set_state(self._h, buf, len(state)))
+
+    def afqmc_synchronize(self):
+        self._check(self._lib.afqmc_synchronize(self._h))
+
+    def afqmc_set_kernel_timing(self, enable: bool):
+        self._check(self._lib.afqmc_set_kernel_timing(self._h, int(enable)))
+
+    def afqmc_kernel_stats(self, kernel):
+        kid = KERNEL_IDS.index(kernel) if isinstance(kernel, str) else kernel
+        n = C.c_int64()
+        ms = C.c_double()
+        wk = C.c_double()
+        isb = C.c_int32()
+        self._check(self._lib.afqmc_kernel_stats(self._h, kid, C.byref(n), C.byref(ms),
+                                                 C.byref(wk), C.byref(isb)))
+        return dict(launches=n.value, total_ms=ms.value, work=wk.value,
+                    is_bytes=bool(isb.value))
+
+    def afqmc_launch_count(self) -> int:
+        return int(self._lib.afqmc_launch_count(self._h))
+
+    # -- views of the state --------------------------------------------------
+    def walkers(self):
+        """Walker orbitals as complex128 arrays Phi_up [W, M, n_up], Phi_dn [W, M, n_dn],
+        plus weights, log-overlaps and the step counter, from a checkpoint image."""
+        return decode_state(self.afqmc_get_state(), self.n_chol)
+
+
+HEADER = np.dtype([("magic", "S8"), ("M", "<i4"), ("n_up", "<i4"), ("n_dn", "<i4"),
+                   ("n_walkers", "<i4"), ("step", "<i8"), ("seed", "<u8"),
+                   ("run_id", "<i4"), ("n_chol", "<i4")])
+
+
+def decode_state(buf: bytes, n_chol=None):
+    h = np.frombuffer(buf, dtype=HEADER, count=1)[0]
+    M, nu, nd, W = int(h["M"]), int(h["n_up"]), int(h["n_dn"]), int(h["n_walkers"])
+    N = nu + nd
+    off = HEADER.itemsize
+    z = np.frombuffer(buf, dtype=np.complex128, count=W * N * M, offset=off)
+    z = z.reshape(W, N, M)
+    off += W * N * M * 16
+    w = np.frombuffer(buf, dtype=np.float64, count=W, offset=off).copy()
+    off += W * 8
+    lo = np.frombuffer(buf, dtype=np.complex128, count=W, offset=off).copy()
+    Phi = np.swapaxes(z, 1, 2)
+    return dict(Phi_up=Phi[:, :, :nu].copy(), Phi_dn=Phi[:, :, nu:].copy(), weight=w,
+                logO=lo, step=int(h["step"]))
+
+
+def encode_state(template: bytes, Phi_up, Phi_dn, weight, logO, step=None) -> bytes:
+    """Replace the walkers of a checkpoint image (same sizes)."""
+    h = np.frombuffer(template, dtype=HEADER, count=1).copy()
+    if step is not None:
+        h["step"] = step
+    W = Phi_up.shape[0]
+    z = np.concatenate([Phi_up, Phi_dn], axis=2)           # [W, M, N]
+    z = np.ascontiguousarray(np.swapaxes(z, 1, 2), dtype=np.complex128)
+    return (h.tobytes() + z.tobytes() + np.asarray(weight, np.float64).tobytes()
+            + np.asarray(logO, np.complex128).tobytes())

@@ -1,0 +1,905 @@
+// C ABI of the ph-AFQMC walker-step library: context lifetime, setup
+// precompute, the per-step schedule and read-out calls. See include/afqmc.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/afqmc.h"
+#include "kernels.h"
+#include "tc.h"
+
+using namespace afqmc;
+
+namespace {
+
+struct TimedPair {
+  int id;
+  cudaEvent_t a, b;
+};
+
+struct StateHeader {
+  char magic[8];     // "AFQMCST1"
+  int32_t M, n_up, n_dn, n_walkers;
+  int64_t step;
+  uint64_t seed;
+  int32_t run_id, n_chol;
+};
+
+}  // namespace
+
+struct afqmc_ctx {
+  afqmc_params p;
+  int M, nu, nd, N, G, W, ndet;
+  bool fp64;
+  cudaStream_t st;
+  bool own_stream;
+  long step;
+  long n_meas;
+  double e_shift;
+  std::string err;
+  bool poisoned;
+  int64_t launches;
+
+  // walker state and step intermediates (element type by precision)
+  void *Phi, *Phi2, *Phi3, *Theta, *Theta2, *V, *X, *S, *xbar, *Z;
+  // precomputed operators in the step precision
+  void *L, *Ltil, *Bhalf, *PsiT, *Yx_up, *Yx_dn;
+  double* PsiT64;
+  double *weight, *scan, *wnew, *escalar;
+  double2 *logO, *logO2, *logO_new, *logdet, *lw, *eloc, *hist;
+  int *parent, *status;
+  std::vector<void*> allocs;
+
+  // tensor-core operand copies (TF32 modes)
+  TcPlan* tc;
+
+  bool timing;
+  std::vector<TimedPair> pending;
+  std::vector<cudaEvent_t> free_events;
+  int64_t k_launch[AFQMC_N_KERNEL_IDS];
+  double k_ms[AFQMC_N_KERNEL_IDS];
+};
+
+namespace {
+
+const int kHist = 4096;
+thread_local std::string g_create_err;
+
+afqmc_status fail(afqmc_ctx* c, afqmc_status s, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (s == AFQMC_E_CUDA) c->poisoned = true;
+  } else {
+    g_create_err = msg;
+  }
+  return s;
+}
+
+#define CK(expr)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? AFQMC_E_OOM : AFQMC_E_CUDA,\
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+#define LK(expr)            \
+  do {                      \
+    CK(expr);               \
+    c->launches += 1;       \
+  } while (0)
+
+size_t esize(const afqmc_ctx* c) { return c->fp64 ? sizeof(double) : sizeof(float); }
+
+afqmc_status dalloc(afqmc_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, AFQMC_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  c->allocs.push_back(*p);
+  return AFQMC_OK;
+}
+
+#define DALLOC(ptr, bytes)                                      \
+  do {                                                          \
+    void* tmp_ = nullptr;                                       \
+    afqmc_status s_ = dalloc(c, &tmp_, (bytes));                \
+    if (s_ != AFQMC_OK) return s_;                              \
+    ptr = reinterpret_cast<decltype(ptr)>(tmp_);                \
+  } while (0)
+
+cudaEvent_t get_event(afqmc_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct KTimer {
+  afqmc_ctx* c;
+  int id;
+  cudaEvent_t a;
+  KTimer(afqmc_ctx* c_, int id_) : c(c_), id(id_), a(nullptr) {
+    if (c->timing) {
+      a = get_event(c);
+      cudaEventRecord(a, c->st);
+    }
+  }
+  ~KTimer() {
+    if (c->timing && a) {
+      cudaEvent_t b = get_event(c);
+      cudaEventRecord(b, c->st);
+      c->pending.push_back({id, a, b});
+      c->k_launch[id] += 1;
+    }
+  }
+};
+
+afqmc_status drain_timers(afqmc_ctx* c) {
+  if (c->pending.empty()) return AFQMC_OK;
+  CK(cudaStreamSynchronize(c->st));
+  for (auto& t : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    c->k_ms[t.id] += ms;
+    c->free_events.push_back(t.a);
+    c->free_events.push_back(t.b);
+  }
+  c->pending.clear();
+  return AFQMC_OK;
+}
+
+afqmc_status check_status(afqmc_ctx* c) {
+  int s = 0;
+  CK(cudaMemcpyAsync(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (s & 2) {
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+    return fail(c, AFQMC_E_POPULATION, "population control found every walker weight zero");
+  }
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Step pieces, templated on the walker element type.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+afqmc_status force_bias_contraction(afqmc_ctx* c) {
+  const int W = c->W, N = c->N, M = c->M, G = c->G;
+  KTimer t(c, 0);
+  if (c->tc) {
+    LK(tc_force_bias(c->tc, c->st, (const float*)c->Theta, (float*)c->X));
+  } else {
+    LK(gemm<T>(c->st, false, true, 2 * W, G + 1, N * M, T(1), (const T*)c->Theta,
+               (long)N * M, 0, (const T*)c->Ltil, (long)N * M, 0, T(0), (T*)c->X,
+               G + 1, 0, 1));
+  }
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status measure_T(afqmc_ctx* c, bool record) {
+  const int W = c->W, N = c->N, M = c->M, G = c->G;
+  afqmc_status s = force_bias_contraction<T>(c);
+  if (s != AFQMC_OK) return s;
+  {
+    KTimer t(c, 7);
+    long zoff = 0;
+    for (int sig = 0; sig < 2; ++sig) {
+      const int ns = sig ? c->nd : c->nu;
+      const int j0 = sig ? c->nu : 0;
+      if (ns == 0) continue;
+      const long J = (long)ns * M;
+      const T* Y = (const T*)(sig ? c->Yx_dn : c->Yx_up);
+      if (c->tc) {
+        LK(tc_exchange(c->tc, c->st, sig, (const float*)c->Theta, (float*)c->Z + zoff));
+      } else {
+        LK(gemm<T>(c->st, false, false, 2 * W, (int)J, (int)J, T(1),
+                   (const T*)c->Theta + (long)j0 * M, (long)N * M, 0, Y, J, 0, T(0),
+                   (T*)c->Z + zoff, J, 0, 1));
+      }
+      zoff += 2L * W * J;
+    }
+    LK(launch_energy_reduce<T>(c->st, W, M, c->nu, c->nd, G, (const T*)c->X, G + 1,
+                               (const T*)c->Theta, (const T*)c->Z, c->eloc));
+  }
+  LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, (double)c->step,
+                         record ? c->hist : nullptr, (int)(c->n_meas % kHist),
+                         c->escalar));
+  if (record) c->n_meas += 1;
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status mgs_T(afqmc_ctx* c) {
+  KTimer t(c, 6);
+  LK(launch_mgs<T>(c->st, c->W, c->M, c->nu, c->nd, (T*)c->Phi, c->logO));
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status comb_T(afqmc_ctx* c) {
+  const int W = c->W;
+  KTimer t(c, 8);
+  LK(launch_comb(c->st, W, c->weight, c->p.seed, c->p.run_id, c->step, c->parent, c->scan,
+                 c->wnew, c->status));
+  const long pe = (long)c->N * 2 * c->M;
+  LK(launch_gather<T>(c->st, W, pe, pe, c->parent, (const T*)c->Phi, (T*)c->Phi2,
+                      (const T*)c->Theta, (T*)c->Theta2, c->logO, c->logO2, c->wnew,
+                      c->weight));
+  std::swap(c->Phi, c->Phi2);
+  std::swap(c->Theta, c->Theta2);
+  std::swap(c->logO, c->logO2);
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
+  LK(launch_overlap<T>(c->st, c->W, c->M, c->nu, c->nd, (const T*)c->Phi,
+                       (const T*)c->PsiT, (T*)c->Theta, c->logdet, nullptr));
+  LK(launch_logdet_sum(c->st, c->W, c->logdet, logO_out));
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status step_T(afqmc_ctx* c) {
+  const int W = c->W, N = c->N, M = c->M, G = c->G;
+  const double dt = c->p.dtau;
+  afqmc_status s = force_bias_contraction<T>(c);
+  if (s != AFQMC_OK) return s;
+  {
+    KTimer t(c, 1);
+    LK(launch_fields<T>(c->st, W, G, (const T*)c->X, G + 1, sqrt(dt), c->p.fb_cap,
+                        c->p.seed, c->p.run_id, c->step, (T*)c->S, (T*)c->xbar, c->lw));
+  }
+  {
+    KTimer t(c, 2);
+    if (c->tc) {
+      LK(tc_one_body(c->tc, c->st, (const float*)c->S, (float*)c->V));
+    } else {
+      LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, G, 0,
+                 (const T*)c->L, (long)M * M, 0, T(0), (T*)c->V, (long)M * M, 0, 1));
+    }
+  }
+  {
+    KTimer t(c, 3);
+    if (c->tc) {
+      LK(tc_propagate(c->tc, c->st, (const float*)c->V, (float*)c->Phi, (float*)c->Phi2,
+                      (float*)c->Phi3));
+    } else {
+      const int rows = W * N * 2;
+      LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi, M, 0,
+                 (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi2, M, 0, 1));
+      LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V,
+                          (const T*)c->Phi2, (T*)c->Phi3));
+      LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi3, M, 0,
+                 (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi, M, 0, 1));
+    }
+  }
+  {
+    KTimer t(c, 4);
+    s = overlap_T<T>(c, c->logO_new);
+    if (s != AFQMC_OK) return s;
+  }
+  {
+    KTimer t(c, 5);
+    LK(launch_weights(c->st, W, c->logO_new, c->lw, dt, c->e_shift, c->weight, c->logO));
+  }
+  c->step += 1;
+  const long n = c->step;
+  if (c->p.ortho_every > 0 && n % c->p.ortho_every == 0) {
+    s = mgs_T<T>(c);
+    if (s != AFQMC_OK) return s;
+  }
+  if (c->p.measure_every > 0 && n % c->p.measure_every == 0) {
+    s = measure_T<T>(c, true);
+    if (s != AFQMC_OK) return s;
+  }
+  if (c->p.pc_every > 0 && n % c->p.pc_every == 0) {
+    s = comb_T<T>(c);
+    if (s != AFQMC_OK) return s;
+  }
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Setup
+// ---------------------------------------------------------------------------
+
+afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
+                      const double* Cu, const double* Cd, const int32_t* ou,
+                      const int32_t* od, const double* ci) {
+  afqmc_ctx* c = nullptr;
+  if (!p || !h1 || !L || !Cu || !Cd || !ou || !od || !ci)
+    return fail(c, AFQMC_E_INVALID, "null argument");
+  for (int i = 0; i < 8; ++i)
+    if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
+  const int M = p->M;
+  if (M < 1 || M > 256) return fail(c, AFQMC_E_INVALID, "M must be in 1..256");
+  if (p->n_up < 0 || p->n_dn < 0 || p->n_up > M || p->n_dn > M || p->n_up + p->n_dn < 1)
+    return fail(c, AFQMC_E_INVALID, "electron counts out of range");
+  if (p->n_chol < 1) return fail(c, AFQMC_E_INVALID, "n_chol must be >= 1");
+  if (p->n_det != 1)
+    return fail(c, AFQMC_E_INVALID, "multi-determinant trials are not available in this build");
+  if (p->n_walkers < 1 || p->n_walkers > 32768)
+    return fail(c, AFQMC_E_INVALID, "n_walkers must be in 1..32768");
+  if (!(p->dtau > 0.0)) return fail(c, AFQMC_E_INVALID, "dtau must be > 0");
+  if (p->taylor_order < 1 || p->taylor_order > 12)
+    return fail(c, AFQMC_E_INVALID, "taylor_order must be in 1..12");
+  if (p->precision < AFQMC_FP64 || p->precision > AFQMC_TF32X3)
+    return fail(c, AFQMC_E_INVALID, "unknown precision");
+  if (p->run_id < 0 || p->run_id >= (1 << 29)) return fail(c, AFQMC_E_INVALID, "run_id out of range");
+  if (p->ortho_every < 0 || p->measure_every < 0 || p->pc_every < 0)
+    return fail(c, AFQMC_E_INVALID, "cadences must be >= 0");
+  const int nmax = p->n_up > p->n_dn ? p->n_up : p->n_dn;
+  if ((size_t)nmax * 2 * nmax * 16 + nmax * 16 > 227 * 1024)
+    return fail(c, AFQMC_E_INVALID, "electrons per spin too large for the on-chip inverse");
+  if ((size_t)nmax * M * 16 > 227 * 1024)
+    return fail(c, AFQMC_E_INVALID, "M x electrons per spin too large for on-chip Gram-Schmidt");
+  // symmetry of h1 and L
+  double scale = 0.0;
+  for (long e = 0; e < (long)M * M; ++e) scale = fmax(scale, fabs(h1[e]));
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < i; ++j)
+      if (fabs(h1[i * M + j] - h1[j * M + i]) > 1e-12 * (1.0 + scale))
+        return fail(c, AFQMC_E_INVALID, "h1 is not symmetric");
+  for (long g = 0; g < p->n_chol; ++g) {
+    const double* Lg = L + g * M * M;
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < i; ++j)
+        if (fabs(Lg[i * M + j] - Lg[j * M + i]) > 1e-12 * (1.0 + fabs(Lg[i * M + j])))
+          return fail(c, AFQMC_E_INVALID, "L_g is not symmetric (g = " + std::to_string(g) + ")");
+  }
+  // occupations and orthonormality of the used orbitals
+  for (int sig = 0; sig < 2; ++sig) {
+    const int ns = sig ? p->n_dn : p->n_up;
+    const int32_t* occ = sig ? od : ou;
+    const double* C = sig ? Cd : Cu;
+    std::vector<char> used(M, 0);
+    for (long d = 0; d < p->n_det; ++d) {
+      std::vector<char> seen(M, 0);
+      for (int a = 0; a < ns; ++a) {
+        int o = occ[d * ns + a];
+        if (o < 0 || o >= M) return fail(c, AFQMC_E_INVALID, "occupation index out of range");
+        if (seen[o]) return fail(c, AFQMC_E_INVALID, "repeated orbital in a determinant");
+        seen[o] = 1;
+        used[o] = 1;
+      }
+    }
+    for (int a = 0; a < M; ++a) {
+      if (!used[a]) continue;
+      for (int b = 0; b <= a; ++b) {
+        if (!used[b]) continue;
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s += C[k * M + a] * C[k * M + b];
+        if (fabs(s - (a == b ? 1.0 : 0.0)) > 1e-8)
+          return fail(c, AFQMC_E_INVALID, "trial orbitals are not orthonormal");
+      }
+    }
+  }
+  (void)ci;
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
+                     const double* Cu, const double* Cd, const int32_t* ou,
+                     const int32_t* od) {
+  const int M = c->M, N = c->N, G = c->G, W = c->W;
+  const long MM = (long)M * M;
+  cudaStream_t st = c->st;
+  // FP64 staging
+  double *h1, *L, *PsiT, *h1p, *Bh, *Ltil, *ta, *tb, *tcur, *tnext;
+  std::vector<void*> tmp;
+  auto tmalloc = [&](double** p, size_t n) -> afqmc_status {
+    cudaError_t e = cudaMalloc((void**)p, (n ? n : 1) * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      for (void* q : tmp) cudaFree(q);
+      return fail(c, AFQMC_E_OOM, "setup allocation failed");
+    }
+    tmp.push_back(*p);
+    return AFQMC_OK;
+  };
+#define TM(p, n) do { afqmc_status s_ = tmalloc(&p, (n)); if (s_ != AFQMC_OK) return s_; } while (0)
+  TM(h1, MM); TM(L, (size_t)G * MM); TM(PsiT, (size_t)N * M); TM(h1p, MM); TM(Bh, MM);
+  TM(Ltil, (size_t)(G + 1) * N * M); TM(ta, MM); TM(tb, MM); TM(tcur, MM); TM(tnext, MM);
+  std::vector<double> psiT_h((size_t)N * M);
+  for (int a = 0; a < N; ++a) {
+    const bool up = a < c->nu;
+    const double* C = up ? Cu : Cd;
+    const int orb = up ? ou[a] : od[a - c->nu];
+    for (int k = 0; k < M; ++k) psiT_h[(size_t)a * M + k] = C[(size_t)k * M + orb];
+  }
+  CK(cudaMemcpyAsync(h1, h1_h, MM * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(L, L_h, (size_t)G * MM * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(PsiT, psiT_h.data(), psiT_h.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->PsiT64, psiT_h.data(), psiT_h.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, st));
+  // H1' = h1 - 1/2 sum_g L_g L_g
+  LK(launch_h1_remainder(st, M, G, h1, L, h1p));
+  // B_half = exp(-dt/2 H1'): scaling and squaring of a Taylor series
+  std::vector<double> hp(MM);
+  CK(cudaMemcpyAsync(hp.data(), h1p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double fro = 0.0;
+  for (double v : hp) fro += v * v;
+  fro = sqrt(fro) * 0.5 * c->p.dtau;
+  int sq = 0;
+  while (fro / ldexp(1.0, sq) > 0.25 && sq < 60) ++sq;
+  const double a = -0.5 * c->p.dtau / ldexp(1.0, sq);
+  LK(launch_scale_identity(st, M, h1p, a, Bh, tcur));   // Bh = I + A, tcur = A
+  CK(cudaMemcpyAsync(ta, tcur, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  for (int k = 2; k <= 24; ++k) {
+    LK(gemm<double>(st, false, false, M, M, M, 1.0 / k, tcur, M, 0, ta, M, 0, 0.0, tnext,
+                    M, 0, 1));
+    LK(launch_axpy_d(st, MM, 1.0, tnext, Bh));
+    std::swap(tcur, tnext);
+  }
+  for (int i = 0; i < sq; ++i) {
+    LK(gemm<double>(st, false, false, M, M, M, 1.0, Bh, M, 0, Bh, M, 0, 0.0, tb, M, 0, 1));
+    std::swap(Bh, tb);
+  }
+  // half-rotated L~_g = D^T L_g (rows: up orbitals, then down), plus D^T h1
+  LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, L, M, MM, 0.0, Ltil, M,
+                  (long)N * M, G));
+  LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, h1, M, 0, 0.0,
+                  Ltil + (size_t)G * N * M, M, 0, 1));
+  // exchange part of the Eq. 5 tensor, per spin
+  for (int sig = 0; sig < 2; ++sig) {
+    const int ns = sig ? c->nd : c->nu;
+    const int j0 = sig ? c->nu : 0;
+    if (ns == 0) continue;
+    const long J = (long)ns * M;
+    double *gram, *yx;
+    TM(gram, (size_t)J * J);
+    TM(yx, (size_t)J * J);
+    LK(gemm<double>(st, true, false, (int)J, (int)J, G, 1.0, Ltil + (size_t)j0 * M,
+                    (long)N * M, 0, Ltil + (size_t)j0 * M, (long)N * M, 0, 0.0, gram, J, 0, 1));
+    LK(launch_yx_permute(st, ns, M, gram, yx));
+    void* dst = sig ? c->Yx_dn : c->Yx_up;
+    LK(launch_convert<T>(st, J * J, yx, (T*)dst));
+  }
+  LK(launch_convert<T>(st, (long)G * MM, L, (T*)c->L));
+  LK(launch_convert<T>(st, (long)(G + 1) * N * M, Ltil, (T*)c->Ltil));
+  LK(launch_convert<T>(st, MM, Bh, (T*)c->Bhalf));
+  LK(launch_convert<T>(st, (long)N * M, PsiT, (T*)c->PsiT));
+  CK(cudaStreamSynchronize(st));
+  for (void* q : tmp) cudaFree(q);
+#undef TM
+  // walkers start at the reference determinant, weight 1
+  LK(launch_init_walkers<T>(st, W, M, N, (const T*)c->PsiT, (T*)c->Phi, c->weight));
+  afqmc_status s = overlap_T<T>(c, c->logO);
+  if (s != AFQMC_OK) return s;
+  if (isnan(c->p.e_shift)) {
+    s = measure_T<T>(c, false);
+    if (s != AFQMC_OK) return s;
+    double2 e0;
+    CK(cudaMemcpyAsync(&e0, c->eloc, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!isfinite(e0.x)) return fail(c, AFQMC_E_NUMERIC, "trial energy is not finite");
+    c->e_shift = e0.x;
+  } else {
+    c->e_shift = c->p.e_shift;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
+                         const double* Cu, const double* Cd, const int32_t* ou,
+                         const int32_t* od) {
+  const int M = c->M, N = c->N, G = c->G, W = c->W;
+  const size_t es = esize(c);
+  const size_t MM = (size_t)M * M;
+  const size_t phi = (size_t)W * N * 2 * M;
+  DALLOC(c->Phi, phi * es);
+  DALLOC(c->Phi2, phi * es);
+  DALLOC(c->Phi3, phi * es);
+  DALLOC(c->Theta, phi * es);
+  DALLOC(c->Theta2, phi * es);
+  DALLOC(c->V, (size_t)W * 2 * MM * es);
+  DALLOC(c->X, (size_t)W * 2 * (G + 1) * es);
+  DALLOC(c->S, (size_t)W * 2 * G * es);
+  DALLOC(c->xbar, (size_t)W * 2 * G * es);
+  const size_t Jt = (size_t)c->nu * c->nu * MM + (size_t)c->nd * c->nd * MM;
+  DALLOC(c->Z, (size_t)2 * W * ((size_t)c->nu * M + (size_t)c->nd * M) * es);
+  DALLOC(c->L, (size_t)G * MM * es);
+  DALLOC(c->Ltil, (size_t)(G + 1) * N * M * es);
+  DALLOC(c->Bhalf, MM * es);
+  DALLOC(c->PsiT, (size_t)N * M * es);
+  DALLOC(c->PsiT64, (size_t)N * M * sizeof(double));
+  DALLOC(c->Yx_up, (size_t)c->nu * c->nu * MM * es);
+  DALLOC(c->Yx_dn, (size_t)c->nd * c->nd * MM * es);
+  (void)Jt;
+  DALLOC(c->weight, W * sizeof(double));
+  DALLOC(c->scan, W * sizeof(double));
+  DALLOC(c->wnew, sizeof(double));
+  DALLOC(c->escalar, sizeof(double));
+  DALLOC(c->logO, W * sizeof(double2));
+  DALLOC(c->logO2, W * sizeof(double2));
+  DALLOC(c->logO_new, W * sizeof(double2));
+  DALLOC(c->logdet, 2 * W * sizeof(double2));
+  DALLOC(c->lw, W * sizeof(double2));
+  DALLOC(c->eloc, W * sizeof(double2));
+  DALLOC(c->hist, kHist * sizeof(double2));
+  DALLOC(c->parent, W * sizeof(int));
+  DALLOC(c->status, sizeof(int));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+  CK(cudaMemsetAsync(c->lw, 0, W * sizeof(double2), c->st));
+  CK(cudaMemsetAsync(c->xbar, 0, (size_t)W * 2 * G * es, c->st));
+  afqmc_status s = c->fp64 ? setup_T<double>(c, h1, L, Cu, Cd, ou, od)
+                           : setup_T<float>(c, h1, L, Cu, Cd, ou, od);
+  if (s != AFQMC_OK) return s;
+  if (c->p.precision == AFQMC_TF32 || c->p.precision == AFQMC_TF32X3) {
+    TcShape sh{c->W, c->M, c->nu, c->nd, c->G, c->p.taylor_order,
+               c->p.precision == AFQMC_TF32X3};
+    cudaError_t e = tc_plan_create(&c->tc, sh, c->st, (const float*)c->L,
+                                   (const float*)c->Ltil, (const float*)c->Bhalf,
+                                   (const float*)c->Yx_up, (const float*)c->Yx_dn);
+    if (e != cudaSuccess)
+      return fail(c, e == cudaErrorMemoryAllocation ? AFQMC_E_OOM : AFQMC_E_CUDA,
+                  std::string("tensor-core plan: ") + cudaGetErrorString(e));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return AFQMC_OK;
+}
+
+
+#define GUARD(c)                                                        \
+  do {                                                                  \
+    if (!(c)) return AFQMC_E_INVALID;                                   \
+    if ((c)->poisoned) return fail((c), AFQMC_E_CUDA, "context is poisoned by an earlier CUDA error: " + (c)->err); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+void afqmc_params_default(afqmc_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->n_det = 1;
+  p->taylor_order = 6;
+  p->fb_cap = 1.0;
+  p->e_shift = NAN;
+  p->precision = AFQMC_FP64;
+  p->ortho_every = 2;
+  p->measure_every = 20;
+  p->pc_every = 20;
+}
+
+afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const double* L,
+                          const double* C_up, const double* C_dn, const int32_t* occ_up,
+                          const int32_t* occ_dn, const double* ci, void* stream,
+                          afqmc_ctx** out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, AFQMC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  afqmc_status s = validate(params, h1, L, C_up, C_dn, occ_up, occ_dn, ci);
+  if (s != AFQMC_OK) return s;
+  afqmc_ctx* c = new afqmc_ctx();
+  c->p = *params;
+  c->M = params->M;
+  c->nu = params->n_up;
+  c->nd = params->n_dn;
+  c->N = c->nu + c->nd;
+  c->G = params->n_chol;
+  c->W = params->n_walkers;
+  c->ndet = params->n_det;
+  c->fp64 = params->precision == AFQMC_FP64;
+  c->step = 0;
+  c->n_meas = 0;
+  c->poisoned = false;
+  c->launches = 0;
+  c->timing = false;
+  c->tc = nullptr;
+  for (int i = 0; i < AFQMC_N_KERNEL_IDS; ++i) { c->k_launch[i] = 0; c->k_ms[i] = 0.0; }
+  if (stream) {
+    c->st = (cudaStream_t)stream;
+    c->own_stream = false;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, AFQMC_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  s = create_impl(c, h1, L, C_up, C_dn, occ_up, occ_dn);
+  if (s != AFQMC_OK) {
+    g_create_err = c->err;
+    afqmc_destroy(c);
+    return s;
+  }
+  *out = c;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_propagate(afqmc_ctx* c, int32_t n_steps) {
+  GUARD(c);
+  if (n_steps < 0) return fail(c, AFQMC_E_INVALID, "n_steps < 0");
+  for (int i = 0; i < n_steps; ++i) {
+    afqmc_status s = c->fp64 ? step_T<double>(c) : step_T<float>(c);
+    if (s != AFQMC_OK) return s;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_orthonormalize(afqmc_ctx* c) {
+  GUARD(c);
+  return c->fp64 ? mgs_T<double>(c) : mgs_T<float>(c);
+}
+
+afqmc_status afqmc_population_control(afqmc_ctx* c) {
+  GUARD(c);
+  afqmc_status s = c->fp64 ? comb_T<double>(c) : comb_T<float>(c);
+  if (s != AFQMC_OK) return s;
+  return check_status(c);
+}
+
+afqmc_status afqmc_local_energy(afqmc_ctx* c, double* e_loc, double* e_mixed) {
+  GUARD(c);
+  afqmc_status s = c->fp64 ? measure_T<double>(c, false) : measure_T<float>(c, false);
+  if (s != AFQMC_OK) return s;
+  if (e_loc)
+    CK(cudaMemcpyAsync(e_loc, c->eloc, c->W * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+  double em = 0.0;
+  CK(cudaMemcpyAsync(&em, c->escalar, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (e_mixed) *e_mixed = em;
+  return check_status(c);
+}
+
+afqmc_status afqmc_weights(afqmc_ctx* c, double* w, double* log_ovlp) {
+  GUARD(c);
+  if (w) CK(cudaMemcpyAsync(w, c->weight, c->W * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if (log_ovlp)
+    CK(cudaMemcpyAsync(log_ovlp, c->logO, c->W * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return check_status(c);
+}
+
+afqmc_status afqmc_green(afqmc_ctx* c, int32_t walker, double* G_up, double* G_dn) {
+  GUARD(c);
+  if (walker < 0 || walker >= c->W) return fail(c, AFQMC_E_INVALID, "walker out of range");
+  const int M = c->M, N = c->N;
+  const size_t es = esize(c);
+  std::vector<unsigned char> th(2 * (size_t)N * M * es);
+  CK(cudaMemcpyAsync(th.data(), (const unsigned char*)c->Theta + (size_t)walker * 2 * N * M * es,
+                     th.size(), cudaMemcpyDeviceToHost, c->st));
+  std::vector<double> psi((size_t)N * M);
+  CK(cudaMemcpyAsync(psi.data(), c->PsiT64, psi.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  auto theta = [&](int cc, int a, int k) -> double {
+    size_t idx = ((size_t)cc * N + a) * M + k;
+    return c->fp64 ? ((const double*)th.data())[idx] : (double)((const float*)th.data())[idx];
+  };
+  // G_ij = sum_a Theta_ja D_ia (G^T = Theta D^H, real trial orbitals)
+  for (int sig = 0; sig < 2; ++sig) {
+    double* G = sig ? G_dn : G_up;
+    if (!G) continue;
+    const int ns = sig ? c->nd : c->nu, j0 = sig ? c->nu : 0;
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        double re = 0.0, im = 0.0;
+        for (int a = 0; a < ns; ++a) {
+          double d = psi[(size_t)(j0 + a) * M + i];
+          re += theta(0, j0 + a, j) * d;
+          im += theta(1, j0 + a, j) * d;
+        }
+        G[2 * ((size_t)i * M + j)] = re;
+        G[2 * ((size_t)i * M + j) + 1] = im;
+      }
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_force_bias(afqmc_ctx* c, double* xbar) {
+  GUARD(c);
+  if (!xbar) return fail(c, AFQMC_E_INVALID, "xbar is NULL");
+  const size_t n = (size_t)c->W * 2 * c->G;
+  std::vector<unsigned char> buf(n * esize(c));
+  CK(cudaMemcpyAsync(buf.data(), c->xbar, buf.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int w = 0; w < c->W; ++w)
+    for (int cc = 0; cc < 2; ++cc)
+      for (int g = 0; g < c->G; ++g) {
+        size_t src = ((size_t)w * 2 + cc) * c->G + g;
+        double v = c->fp64 ? ((double*)buf.data())[src] : (double)((float*)buf.data())[src];
+        xbar[((size_t)w * c->G + g) * 2 + cc] = v;
+      }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_energy_history(afqmc_ctx* c, double* out, int32_t max_n, int32_t* n) {
+  GUARD(c);
+  const long have = c->n_meas < kHist ? c->n_meas : kHist;
+  if (n) *n = (int32_t)c->n_meas;
+  if (out && max_n > 0) {
+    std::vector<double2> h(kHist);
+    CK(cudaMemcpyAsync(h.data(), c->hist, kHist * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    long first = c->n_meas - have;
+    long cnt = have < max_n ? have : max_n;
+    for (long i = 0; i < cnt; ++i) {
+      double2 v = h[(first + i) % kHist];
+      out[2 * i] = v.x;
+      out[2 * i + 1] = v.y;
+    }
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_get_state(afqmc_ctx* c, void* buf, size_t* bytes) {
+  GUARD(c);
+  if (!bytes) return fail(c, AFQMC_E_INVALID, "bytes is NULL");
+  const int W = c->W, N = c->N, M = c->M;
+  const size_t need = sizeof(StateHeader) + (size_t)W * N * M * 16 + (size_t)W * 8 +
+                      (size_t)W * 16;
+  if (!buf) { *bytes = need; return AFQMC_OK; }
+  if (*bytes < need) return fail(c, AFQMC_E_INVALID, "state buffer too small");
+  const size_t es = esize(c);
+  const size_t phi = (size_t)W * N * 2 * M;
+  std::vector<unsigned char> ph(phi * es);
+  unsigned char* out = (unsigned char*)buf;
+  StateHeader h;
+  memcpy(h.magic, "AFQMCST1", 8);
+  h.M = M; h.n_up = c->nu; h.n_dn = c->nd; h.n_walkers = W;
+  h.step = c->step; h.seed = c->p.seed; h.run_id = c->p.run_id; h.n_chol = c->G;
+  memcpy(out, &h, sizeof(h));
+  double* z = (double*)(out + sizeof(h));
+  double* wt = z + (size_t)W * N * M * 2;
+  double* lo = wt + W;
+  CK(cudaMemcpyAsync(ph.data(), c->Phi, ph.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(wt, c->weight, W * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(lo, c->logO, W * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (size_t w = 0; w < (size_t)W; ++w)
+    for (int j = 0; j < N; ++j)
+      for (int cc = 0; cc < 2; ++cc)
+        for (int k = 0; k < M; ++k) {
+          size_t src = ((w * N + j) * 2 + cc) * M + k;
+          double v = c->fp64 ? ((double*)ph.data())[src] : (double)((float*)ph.data())[src];
+          z[((w * N + j) * M + k) * 2 + cc] = v;
+        }
+  *bytes = need;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_state(afqmc_ctx* c, const void* buf, size_t bytes) {
+  GUARD(c);
+  const int W = c->W, N = c->N, M = c->M;
+  const size_t need = sizeof(StateHeader) + (size_t)W * N * M * 16 + (size_t)W * 8 +
+                      (size_t)W * 16;
+  if (!buf || bytes < need) return fail(c, AFQMC_E_STATE, "state image too small");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, "AFQMCST1", 8) != 0 || h.M != M || h.n_up != c->nu ||
+      h.n_dn != c->nd || h.n_walkers != W || h.n_chol != c->G)
+    return fail(c, AFQMC_E_STATE, "state image does not match this context");
+  const double* z = (const double*)((const unsigned char*)buf + sizeof(h));
+  const double* wt = z + (size_t)W * N * M * 2;
+  const double* lo = wt + W;
+  const size_t es = esize(c);
+  const size_t phi = (size_t)W * N * 2 * M;
+  std::vector<unsigned char> ph(phi * es);
+  for (size_t w = 0; w < (size_t)W; ++w)
+    for (int j = 0; j < N; ++j)
+      for (int cc = 0; cc < 2; ++cc)
+        for (int k = 0; k < M; ++k) {
+          size_t dst = ((w * N + j) * 2 + cc) * M + k;
+          double v = z[((w * N + j) * M + k) * 2 + cc];
+          if (c->fp64) ((double*)ph.data())[dst] = v;
+          else ((float*)ph.data())[dst] = (float)v;
+        }
+  CK(cudaMemcpyAsync(c->Phi, ph.data(), ph.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->weight, wt, W * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->logO, lo, W * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+  c->step = h.step;
+  afqmc_status s = c->fp64 ? overlap_T<double>(c, c->logO_new) : overlap_T<float>(c, c->logO_new);
+  if (s != AFQMC_OK) return s;
+  CK(cudaStreamSynchronize(c->st));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_synchronize(afqmc_ctx* c) {
+  GUARD(c);
+  CK(cudaStreamSynchronize(c->st));
+  return check_status(c);
+}
+
+afqmc_status afqmc_set_kernel_timing(afqmc_ctx* c, int32_t enable) {
+  GUARD(c);
+  afqmc_status s = drain_timers(c);
+  if (s != AFQMC_OK) return s;
+  c->timing = enable != 0;
+  for (int i = 0; i < AFQMC_N_KERNEL_IDS; ++i) { c->k_launch[i] = 0; c->k_ms[i] = 0.0; }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_kernel_stats(afqmc_ctx* c, int32_t id, int64_t* launches, double* total_ms,
+                                double* work, int32_t* is_bytes) {
+  GUARD(c);
+  if (id < 0 || id >= AFQMC_N_KERNEL_IDS) return fail(c, AFQMC_E_INVALID, "unknown kernel id");
+  afqmc_status s = drain_timers(c);
+  if (s != AFQMC_OK) return s;
+  const double W = c->W, M = c->M, N = c->N, G = c->G, T = c->p.taylor_order;
+  const double es = (double)esize(c);
+  double wk = 0.0;
+  int byt = 0;
+  switch (id) {
+    case 0: wk = 4.0 * W * G * N * M; break;                         // Theta . L~^T
+    case 1: wk = W * 2 * G * es * 3 + W * 16; byt = 1; break;        // X in, S + xbar out
+    case 2: wk = 4.0 * W * G * M * M; break;                         // S . L
+    case 3: wk = 8.0 * T * M * M * N * W + 8.0 * M * M * N * W; break;
+    case 4: {
+      double f = 0.0;
+      for (int sig = 0; sig < 2; ++sig) {
+        double ns = sig ? c->nd : c->nu;
+        f += 12.0 * M * ns * ns + 8.0 * ns * ns * ns;
+      }
+      wk = f * W;
+      break;
+    }
+    case 5: wk = W * (8 + 16 + 16 + 16 + 8 + 16); byt = 1; break;
+    case 6: {
+      double f = 0.0;
+      for (int sig = 0; sig < 2; ++sig) {
+        double ns = sig ? c->nd : c->nu;
+        f += 8.0 * M * ns * ns;
+      }
+      wk = f * W;
+      break;
+    }
+    case 7: {
+      double f = 0.0;
+      for (int sig = 0; sig < 2; ++sig) {
+        double J = (sig ? c->nd : c->nu) * M;
+        f += 4.0 * J * J;
+      }
+      wk = f * W;
+      break;
+    }
+    case 8: wk = W * (2.0 * (2 * N * 2 * M * es) + 16 + 8 + 8); byt = 1; break;
+  }
+  if (launches) *launches = c->k_launch[id];
+  if (total_ms) *total_ms = c->k_ms[id];
+  if (work) *work = wk;
+  if (is_bytes) *is_bytes = byt;
+  return AFQMC_OK;
+}
+
+int64_t afqmc_launch_count(const afqmc_ctx* c) { return c ? c->launches : 0; }
+
+const char* afqmc_last_error(const afqmc_ctx* c) {
+  if (!c) return g_create_err.c_str();
+  return c->err.c_str();
+}
+
+void afqmc_destroy(afqmc_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (auto& t : c->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  for (auto e : c->free_events) cudaEventDestroy(e);
+  if (c->tc) tc_plan_destroy(c->tc);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+}  // extern "C"

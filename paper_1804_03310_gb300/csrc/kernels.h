@@ -1,0 +1,100 @@
+// Launchers of the library's kernels. All take the stream first, return the
+// launch error, and read/write device memory only.
+//
+// Walker layouts (T = double on the FP64 path, float otherwise):
+//   Phi    [W][N][2][M]   column j of walker w (j < n_up: spin up), re plane
+//                         then im plane, M basis coefficients each
+//   Theta  [W][2][N][M]   Theta = Phi (D^H Phi)^-1, re block then im block,
+//                         so row (w, c) is one contiguous N*M vector
+//   V      [W][2][M][M]   one-body operator per walker (complex symmetric)
+//   X      [W][2][ldx]    force-bias contraction per walker, re row, im row
+//   S      [W][2][n_chol] i sqrt(dt) (x - xbar) per walker
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace afqmc {
+
+template <typename T>
+cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, T alpha,
+                 const T* A, long lda, long sA, const T* B, long ldb, long sB,
+                 T beta, T* C, long ldc, long sC, int batch);
+
+// K1 + K3: Philox fields, capped force bias, shifted fields and the log of
+// the importance factor sum_g (x xbar - xbar^2/2) per walker.
+template <typename T>
+cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
+                          double sqdt, double cap, uint64_t seed, int run_id,
+                          long step, T* S, T* xbar, double2* lw);
+
+// K5 on the CUDA cores: Phi_out = sum_{n<=order} V^n Phi_in / n!.
+template <typename T>
+cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
+                          const T* V, const T* Phi_in, T* Phi_out);
+
+// K6: A = D^H Phi per spin in FP64, Gauss-Jordan inverse with partial
+// pivoting, ln det A, Theta = Phi A^-1. PsiT [N][M] holds the reference
+// determinant's orbitals as rows (up orbitals then down orbitals).
+// Ainv (optional) [W][2][nmax][nmax] double2 receives A^-1 per spin.
+template <typename T>
+cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
+                           const T* Phi, const T* PsiT, T* Theta,
+                           double2* logdet, double2* Ainv);
+
+// K7: hybrid weight and phaseless cut from the new log-overlap.
+cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
+                           const double2* lw, double dtau, double e_shift,
+                           double* weight, double2* logO);
+
+// Sum of the two spins' log-determinants (single-determinant overlap).
+cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
+                              double2* out);
+
+// K10: modified Gram-Schmidt in FP64 per walker and spin; logO -= ln det R.
+template <typename T>
+cudaError_t launch_mgs(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
+                       double2* logO);
+
+// K9 epilogue: E_L = E1 + 1/2 sum X^2 + sum_sigma 1/2 theta^T Yx theta.
+template <typename T>
+cudaError_t launch_energy_reduce(cudaStream_t st, int W, int M, int n_up, int n_dn,
+                                 int n_chol, const T* X, long ldx, const T* Theta,
+                                 const T* Z, double2* eloc);
+
+// Weighted mixed estimate sum W Re E / sum W (walkers with W > 0) into
+// hist[slot] = (step, value).
+cudaError_t launch_mixed_energy(cudaStream_t st, int W, const double* weight,
+                                const double2* eloc, double step, double2* hist,
+                                int slot, double* out_scalar);
+
+// K11: blocked FP64 prefix sum and comb; parent[j] per new walker, the new
+// common weight in *wnew; on zero total weight sets bit 1 of *status and
+// leaves parent = identity.
+cudaError_t launch_comb(cudaStream_t st, int W, const double* weight, uint64_t seed,
+                        int run_id, long step, int* parent, double* scratch,
+                        double* wnew, int* status);
+
+// Walker copies after the comb.
+template <typename T>
+cudaError_t launch_gather(cudaStream_t st, int W, long phi_elems, long theta_elems,
+                          const int* parent, const T* Phi, T* Phi_out,
+                          const T* Theta, T* Theta_out, const double2* logO,
+                          double2* logO_out, const double* wnew, double* weight);
+
+// Setup helpers (FP64).
+cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,
+                                const double* L, double* h1p);
+cudaError_t launch_scale_identity(cudaStream_t st, int M, const double* A, double s,
+                                  double* out_I_plus, double* out_scaled);
+cudaError_t launch_yx_permute(cudaStream_t st, int n, int M, const double* gram,
+                              double* yx);
+template <typename T>
+cudaError_t launch_convert(cudaStream_t st, long n, const double* in, T* out);
+template <typename T>
+cudaError_t launch_init_walkers(cudaStream_t st, int W, int M, int N, const T* PsiT,
+                                T* Phi, double* weight);
+cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x,
+                          double* y);
+
+}  // namespace afqmc

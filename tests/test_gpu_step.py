@@ -1,0 +1,216 @@
+"""Parity of the CUDA walker step (through the C ABI) with the FP64 oracle.
+
+FP64 path: per-walker weights, log-overlaps, orbitals, Green's functions and
+local energies agree with the oracle to 1e-10 relative over the first 20
+shared-draw steps. Reduced-precision path: 1e-4 relative. Sizes span several
+GEMM tiles with ragged tails; full-size workloads are checked on sampled
+walkers, which the oracle can follow one by one until the first comb.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from gpu_helpers import compare_energy, compare_green, compare_state
+from oracle import afqmc as O
+from synth import config_c1, config_c2, config_c3, make_system, small_system
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built():
+    from paper_1804_03310_gb300 import build
+    build.build()
+
+
+def gpu_ctx(system, **kw):
+    from paper_1804_03310_gb300 import Afqmc
+    return Afqmc.from_system(system, **kw)
+
+
+def side_by_side(system, precision, n_steps, rtol, walkers=None, energy_at=(),
+                 green_every=0):
+    gpu = gpu_ctx(system, precision=precision)
+    orc = O.OracleRun(system, walker_ids=walkers)
+    e0, _ = gpu.afqmc_local_energy()
+    assert abs(e0[0].real - orc.e_shift) <= rtol * max(1.0, abs(orc.e_shift))
+    worst = {}
+    for s in range(1, n_steps + 1):
+        gpu.afqmc_propagate(1)
+        orc.step()
+        r = compare_state(gpu, orc, rtol=rtol, walkers=walkers, label=f"step {s}")
+        for k, v in r.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+        if s in energy_at:
+            worst["energy"] = max(worst.get("energy", 0.0),
+                                  compare_energy(gpu, orc, rtol=rtol, walkers=walkers,
+                                                 label=f"step {s}"))
+        if green_every and s % green_every == 0:
+            wid = orc.walker_ids[-1]
+            compare_green(gpu, orc, len(orc.walker_ids) - 1, wid, rtol=rtol * 10,
+                          label=f"step {s}")
+    gpu.close()
+    return worst
+
+
+def test_force_bias_first_step_fp64():
+    s = config_c1()
+    gpu = gpu_ctx(s, precision="fp64")
+    orc = O.OracleRun(s)
+    gpu.afqmc_propagate(1)
+    orc.step()
+    xb = gpu.afqmc_force_bias()
+    err = np.max(np.abs(xb - orc.last["xbar"])) / np.max(np.abs(orc.last["xbar"]))
+    assert err < 1e-12
+    gpu.close()
+
+
+def test_c1_twenty_steps_fp64():
+    """Config 1 in full: 64 walkers, orthonormalisation every 5 steps, energy
+    and comb every 10 steps, all 20 first steps compared."""
+    w = side_by_side(config_c1(), "fp64", 20, 1e-10, energy_at=(5, 10, 20),
+                     green_every=5)
+    print("c1 fp64 worst", w)
+
+
+@pytest.mark.parametrize("M,nu,nd,G,W", [
+    (7, 3, 2, 5, 5),        # odd everything
+    (33, 17, 16, 67, 67),   # more than one 64-wide tile, ragged tails
+    (12, 4, 0, 9, 3),       # no down electrons
+    (3, 1, 1, 1, 1),        # one field, one walker
+    (70, 5, 9, 130, 40),    # unequal spins, long contraction
+])
+def test_ragged_sizes_fp64(M, nu, nd, G, W):
+    s = small_system(M=M, n_up=nu, n_dn=nd, n_chol=G, seed=M + G, l_sigma=0.08,
+                     n_walkers=W, dtau=0.02, ortho_every=3, measure_every=4,
+                     pc_every=4, trial="random")
+    side_by_side(s, "fp64", 8, 1e-10, energy_at=(4, 8), green_every=4)
+
+
+@pytest.mark.parametrize("order", [1, 3, 9])
+def test_taylor_orders_fp64(order):
+    s = small_system(M=9, n_up=3, n_dn=3, n_chol=11, seed=5, n_walkers=6,
+                     ortho_every=2, measure_every=0, pc_every=0, taylor_order=order)
+    side_by_side(s, "fp64", 4, 1e-10)
+
+
+def test_c2_full_size_sampled_fp64():
+    """H-chain-shaped workload at full size (1024 walkers); the oracle follows
+    three of them through the 19 steps before the first comb."""
+    s = config_c2()
+    walkers = [0, 513, 1023]
+    w = side_by_side(s, "fp64", 19, 1e-10, walkers=walkers, energy_at=(2, 19),
+                     green_every=19)
+    print("c2 fp64 worst", w)
+
+
+def test_c3_full_size_sampled_fp64():
+    s = config_c3()
+    walkers = [0, 2047]
+    side_by_side(s, "fp64", 4, 1e-10, walkers=walkers, energy_at=(4,))
+
+
+def test_c1_twenty_steps_fp32():
+    w = side_by_side(config_c1(), "fp32", 20, 1e-4, energy_at=(10, 20))
+    print("c1 fp32 worst", w)
+
+
+def test_c2_full_size_sampled_fp32():
+    s = config_c2()
+    w = side_by_side(s, "fp32", 19, 1e-4, walkers=[0, 1023], energy_at=(19,))
+    print("c2 fp32 worst", w)
+
+
+def test_checkpoint_resume_is_bitwise():
+    s = config_c1()
+    gpu = gpu_ctx(s, precision="fp64")
+    gpu.afqmc_propagate(7)
+    state = gpu.afqmc_get_state()
+    gpu.afqmc_propagate(9)
+    a = gpu.walkers()
+    ea, _ = gpu.afqmc_local_energy()
+    gpu.afqmc_set_state(state)
+    gpu.afqmc_propagate(9)
+    b = gpu.walkers()
+    eb, _ = gpu.afqmc_local_energy()
+    assert a["step"] == b["step"] == 16
+    for k in ("Phi_up", "Phi_dn", "weight", "logO"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(ea, eb)
+    gpu.close()
+
+
+def test_free_propagation_closed_form():
+    """All L_g = 0: walkers follow exp(-n dt h1) Psi_0 exactly; with an
+    eigenvector trial weights stay 1 and E_L stays the trial energy."""
+    s = make_system("free", M=16, n_up=5, n_dn=4, n_chol=3, ham_seed=3,
+                    l_kind="zero", trial="eig", dtau=0.02, n_walkers=4,
+                    n_steps=10, seed=1, ortho_every=0, measure_every=0, pc_every=0)
+    gpu = gpu_ctx(s, precision="fp64")
+    gpu.afqmc_propagate(10)
+    st = gpu.walkers()
+    U = expm(-10 * 0.02 * s.h1)
+    assert np.max(np.abs(st["Phi_up"][2] - U @ s.trial_up())) < 1e-12
+    assert np.max(np.abs(st["weight"] - 1.0)) < 1e-12
+    eps = np.linalg.eigvalsh(s.h1)
+    e, em = gpu.afqmc_local_energy()
+    assert np.max(np.abs(e - (eps[:5].sum() + eps[:4].sum()))) < 1e-12
+    gpu.close()
+
+
+def test_all_zero_weights_report_population_error():
+    from paper_1804_03310_gb300 import AfqmcError
+    from paper_1804_03310_gb300.afqmc import decode_state, encode_state
+    s = small_system(M=6, n_up=2, n_dn=2, n_chol=4, n_walkers=5)
+    gpu = gpu_ctx(s)
+    st = gpu.afqmc_get_state()
+    d = decode_state(st)
+    gpu.afqmc_set_state(encode_state(st, d["Phi_up"], d["Phi_dn"],
+                                     np.zeros(5), d["logO"]))
+    with pytest.raises(AfqmcError) as e:
+        gpu.afqmc_population_control()
+    assert e.value.status == 4
+    gpu.close()
+
+
+def test_comb_matches_oracle_on_given_weights():
+    """The comb's integer decisions: parents equal the oracle's comb on the
+    same weights and offset (same FP64 prefix-sum order on both sides)."""
+    from paper_1804_03310_gb300.afqmc import decode_state, encode_state
+    from oracle.philox import comb_uniform
+    rng = np.random.default_rng(11)
+    for W in (1, 31, 32, 33, 100, 1000):
+        s = small_system(M=5, n_up=1, n_dn=1, n_chol=2, n_walkers=W, seed=W,
+                         ortho_every=0, measure_every=0, pc_every=0)
+        gpu = gpu_ctx(s)
+        st = gpu.afqmc_get_state()
+        d = decode_state(st)
+        w = rng.uniform(0.0, 2.0, size=W)
+        w[rng.uniform(size=W) < 0.2] = 0.0
+        w[0] = max(w[0], 0.1)
+        # tag each walker by a distinct orbital phase to identify parents
+        tag = np.exp(1j * np.arange(W) / W)
+        Pu = d["Phi_up"] * tag[:, None, None]
+        gpu.afqmc_set_state(encode_state(st, Pu, d["Phi_dn"], w, d["logO"]))
+        gpu.afqmc_population_control()
+        out = gpu.walkers()
+        got = np.argmin(np.abs(out["Phi_up"][:, 0, 0][:, None]
+                               - Pu[:, 0, 0][None, :]), axis=1)
+        parent, wn = O.comb(w, comb_uniform(s.seed, s.run_id, 0))
+        assert np.array_equal(got, parent)
+        assert np.all(out["weight"] == wn)
+        gpu.close()
+
+
+def test_kernel_timing_and_launch_counter():
+    s = config_c1()
+    gpu = gpu_ctx(s)
+    gpu.afqmc_set_kernel_timing(True)
+    n0 = gpu.afqmc_launch_count()
+    gpu.afqmc_propagate(10)
+    gpu.afqmc_synchronize()
+    assert gpu.afqmc_launch_count() > n0 + 10 * 8
+    st = gpu.afqmc_kernel_stats("propagate")
+    assert st["launches"] == 10 and st["total_ms"] > 0 and st["work"] > 0
+    assert gpu.afqmc_kernel_stats("comb")["launches"] == 1
+    gpu.close()
