@@ -12,11 +12,22 @@ namespace afqmc {
 
 namespace {
 
-constexpr int kSmemMax = 227 * 1024;
 
+// Opt the kernel in to the largest dynamic shared memory the device allows
+// beside its static shared memory; returns that limit in bytes. Errors of
+// these queries are cleared so they cannot surface at a later launch check.
 template <typename K>
-void allow_big_smem(K kernel) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+size_t allow_big_smem(K kernel) {
+  int dev = 0, optin = 48 * 1024;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  size_t stat = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+  size_t dyn = (size_t)optin > stat ? (size_t)optin - stat : 0;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  cudaGetLastError();
+  return dyn;
 }
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
@@ -625,14 +636,13 @@ cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long l
 template <typename T>
 cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
                           const T* V, const T* Phi_in, T* Phi_out) {
-  static bool init = false;
-  if (!init) { allow_big_smem(taylor_kernel<T>); init = true; }
+  static const size_t smem_cap = allow_big_smem(taylor_kernel<T>);
   int NC = 4096 / M;
   if (NC > 16) NC = 16;
   if (NC < 1) return cudaErrorInvalidValue;
   if (NC > N) NC = N;
   size_t smem = sizeof(T) * ((size_t)NC * 2 * M + 2 * (size_t)kTaylorKC * M);
-  if (smem > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  if (smem > smem_cap) return cudaErrorInvalidValue;
   dim3 grid(W, (N + NC - 1) / NC);
   taylor_kernel<T><<<grid, kTaylorThreads, smem, st>>>(M, N, NC, order, V, Phi_in, Phi_out);
   return cudaGetLastError();
@@ -642,11 +652,10 @@ template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, double2* logdet,
                            double2* Ainv) {
-  static bool init = false;
-  if (!init) { allow_big_smem(overlap_kernel<T>); init = true; }
+  static const size_t smem_cap = allow_big_smem(overlap_kernel<T>);
   int nmax = n_up > n_dn ? n_up : n_dn;
   size_t smem = sizeof(double2) * ((size_t)nmax * 2 * nmax + nmax);
-  if (smem > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  if (smem > smem_cap) return cudaErrorInvalidValue;
   dim3 grid(W, 2);
   overlap_kernel<T><<<grid, 256, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta, logdet,
                                             Ainv, nmax);
@@ -670,11 +679,10 @@ cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
 template <typename T>
 cudaError_t launch_mgs(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
                        double2* logO) {
-  static bool init = false;
-  if (!init) { allow_big_smem(mgs_kernel<T>); init = true; }
+  static const size_t smem_cap = allow_big_smem(mgs_kernel<T>);
   int nmax = n_up > n_dn ? n_up : n_dn;
   size_t smem = sizeof(double2) * (size_t)nmax * M;
-  if (smem > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  if (smem > smem_cap) return cudaErrorInvalidValue;
   mgs_kernel<T><<<W, 256, smem, st>>>(M, n_up, n_dn, Phi, logO);
   return cudaGetLastError();
 }
@@ -698,11 +706,10 @@ cudaError_t launch_mixed_energy(cudaStream_t st, int W, const double* weight,
 cudaError_t launch_comb(cudaStream_t st, int W, const double* weight, uint64_t seed,
                         int run_id, long step, int* parent, double* scratch,
                         double* wnew, int* status) {
-  static bool init = false;
-  if (!init) { allow_big_smem(comb_kernel); init = true; }
+  static const size_t smem_cap = allow_big_smem(comb_kernel);
   int nb = (W + kScanBlock - 1) / kScanBlock;
   size_t smem = sizeof(double) * 2 * (size_t)nb;
-  if (smem > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  if (smem > smem_cap) return cudaErrorInvalidValue;
   comb_kernel<<<1, 1024, smem, st>>>(W, weight, (uint32_t)seed, (uint32_t)(seed >> 32),
                                      run_id, (uint32_t)step, parent, scratch, wnew,
                                      status);
