@@ -56,8 +56,10 @@ typedef enum {
  * TF32:    complex64 walkers, dense contractions on tcgen05 tensor cores with
  *          TF32 operands and FP32 accumulation.
  * TF32X3:  as TF32 with split (hi + lo) operands, three products per term.
- * The mixed modes keep FP64 for log-determinants, orthonormalisation, weights
- * and population-control sums. */
+ * The reduced modes keep FP64 for walker weights, the accumulation of
+ * log-determinants and ln det R, and the population-control prefix sums;
+ * params.fp64_islands moves the small inverse and Gram-Schmidt arithmetic
+ * to FP64 as well. */
 typedef enum {
   AFQMC_FP64 = 0,
   AFQMC_FP32 = 1,
@@ -81,7 +83,11 @@ typedef struct {
   int32_t taylor_order;  /* terms of the exponential's Taylor series, 1..12 */
   double fb_cap;         /* cap on |xbar_g|; <= 0 disables the cap */
   double e_shift;        /* energy shift E_T; NaN: local energy of the reference determinant */
-  int32_t reserved[8];   /* must be zero */
+  int32_t fp64_islands;  /* reduced-precision modes: 1 = Gauss-Jordan inverse and
+                            Gram-Schmidt arithmetic in FP64; 0 (default) = FP32
+                            arithmetic there, with the log-determinant and
+                            ln det R sums still accumulated in FP64 */
+  int32_t reserved[7];   /* must be zero */
 } afqmc_params;
 
 /* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,

@@ -32,7 +32,8 @@ class afqmc_params(C.Structure):
                 ("precision", C.c_int32), ("ortho_every", C.c_int32),
                 ("measure_every", C.c_int32), ("pc_every", C.c_int32),
                 ("taylor_order", C.c_int32), ("fb_cap", C.c_double),
-                ("e_shift", C.c_double), ("reserved", C.c_int32 * 8)]
+                ("e_shift", C.c_double), ("fp64_islands", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class AfqmcError(RuntimeError):
@@ -105,7 +106,7 @@ class Afqmc:
     def __init__(self, h1, L, C_up, C_dn, occ_up, occ_dn, ci, *, dtau,
                  n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
                  measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
-                 e_shift=None, stream=None):
+                 e_shift=None, fp64_islands=False, stream=None):
         lib = load_library()
         self._lib = lib
         h1 = np.ascontiguousarray(h1, dtype=np.float64)
@@ -133,6 +134,7 @@ class Afqmc:
         p.taylor_order = taylor_order
         p.fb_cap = fb_cap
         p.e_shift = math.nan if e_shift is None else e_shift
+        p.fp64_islands = int(bool(fp64_islands))
         self.params = p
         self.M, self.n_up, self.n_dn = M, p.n_up, p.n_dn
         self.n_chol, self.n_walkers = p.n_chol, n_walkers

@@ -35,6 +35,7 @@ struct afqmc_ctx {
   afqmc_params p;
   int M, nu, nd, N, G, W, ndet;
   bool fp64;
+  bool fp64_islands;   // Gauss-Jordan and Gram-Schmidt arithmetic in FP64
   cudaStream_t st;
   bool own_stream;
   long step;
@@ -226,7 +227,7 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
 template <typename T>
 afqmc_status mgs_T(afqmc_ctx* c) {
   KTimer t(c, 6);
-  LK(launch_mgs<T>(c->st, c->W, c->M, c->nu, c->nd, (T*)c->Phi, c->logO));
+  LK(launch_mgs<T>(c->st, c->W, c->M, c->nu, c->nd, (T*)c->Phi, c->logO, c->fp64_islands));
   return AFQMC_OK;
 }
 
@@ -249,7 +250,8 @@ afqmc_status comb_T(afqmc_ctx* c) {
 template <typename T>
 afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
   LK(launch_overlap<T>(c->st, c->W, c->M, c->nu, c->nd, (const T*)c->Phi,
-                       (const T*)c->PsiT, (T*)c->Theta, c->logdet, nullptr));
+                       (const T*)c->PsiT, (T*)c->Theta, c->logdet, nullptr,
+                       c->fp64_islands));
   LK(launch_logdet_sum(c->st, c->W, c->logdet, logO_out));
   return AFQMC_OK;
 }
@@ -325,7 +327,7 @@ afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
   afqmc_ctx* c = nullptr;
   if (!p || !h1 || !L || !Cu || !Cd || !ou || !od || !ci)
     return fail(c, AFQMC_E_INVALID, "null argument");
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 7; ++i)
     if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
   const int M = p->M;
   if (M < 1 || M > 256) return fail(c, AFQMC_E_INVALID, "M must be in 1..256");
@@ -601,6 +603,7 @@ afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const do
   c->W = params->n_walkers;
   c->ndet = params->n_det;
   c->fp64 = params->precision == AFQMC_FP64;
+  c->fp64_islands = c->fp64 || params->fp64_islands != 0;
   c->step = 0;
   c->n_meas = 0;
   c->poisoned = false;

@@ -33,14 +33,15 @@ template <typename T>
 cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
                           const T* V, const T* Phi_in, T* Phi_out);
 
-// K6: A = D^H Phi per spin in FP64, Gauss-Jordan inverse with partial
-// pivoting, ln det A, Theta = Phi A^-1. PsiT [N][M] holds the reference
-// determinant's orbitals as rows (up orbitals then down orbitals).
-// Ainv (optional) [W][2][nmax][nmax] double2 receives A^-1 per spin.
+// K6: A = D^H Phi per spin, Gauss-Jordan inverse with partial pivoting
+// (FP64 arithmetic when fp64_compute, else FP32), ln det A accumulated in
+// FP64, Theta = Phi A^-1. PsiT [N][M] holds the reference determinant's
+// orbitals as rows (up orbitals then down orbitals). Ainv (optional)
+// [W][2][nmax][nmax] double2 receives A^-1 per spin.
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta,
-                           double2* logdet, double2* Ainv);
+                           double2* logdet, double2* Ainv, bool fp64_compute);
 
 // K7: hybrid weight and phaseless cut from the new log-overlap.
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
@@ -51,10 +52,11 @@ cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
 cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
                               double2* out);
 
-// K10: modified Gram-Schmidt in FP64 per walker and spin; logO -= ln det R.
+// K10: modified Gram-Schmidt per walker and spin (FP64 arithmetic when
+// fp64_compute, else FP32); logO -= ln det R accumulated in FP64.
 template <typename T>
 cudaError_t launch_mgs(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
-                       double2* logO);
+                       double2* logO, bool fp64_compute);
 
 // K9 epilogue: E_L = E1 + 1/2 sum X^2 + sum_sigma 1/2 theta^T Yx theta.
 template <typename T>

@@ -190,7 +190,28 @@ taylor_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
 }
 
 // --------------------------------------------------------------- K6
-template <typename T>
+// Complex value of the elimination's compute type R (double or float).
+template <typename R>
+struct cx {
+  R x, y;
+};
+template <typename R>
+__device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> r; r.x = a; r.y = b; return r; }
+template <typename R>
+__device__ __forceinline__ cx<R> sub_mul(cx<R> a, cx<R> f, cx<R> b) {   // a - f b
+  return mk<R>(a.x - (f.x * b.x - f.y * b.y), a.y - (f.x * b.y + f.y * b.x));
+}
+template <typename R>
+__device__ __forceinline__ cx<R> div_c(cx<R> a, cx<R> b) {
+  R d = b.x * b.x + b.y * b.y;
+  return mk<R>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// One block per (walker, spin). A = D^T Phi (real trial orbitals) is formed
+// and inverted by Gauss-Jordan elimination with partial pivoting in the
+// compute type R; the log-determinant (sum of the pivots' logarithms plus
+// i pi per row swap) is accumulated in FP64 in every precision.
+template <typename T, typename R>
 __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
                                const T* __restrict__ PsiT, T* __restrict__ Theta,
                                double2* __restrict__ logdet,
@@ -205,50 +226,48 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     if (tid == 0) logdet[2 * w + sig] = make_double2(0.0, 0.0);
     return;
   }
-  double2* aug = reinterpret_cast<double2*>(smem_raw);   // [ns][2 ns]
-  double2* fac = aug + (long)ns * 2 * ns;                 // [ns]
+  cx<R>* aug = reinterpret_cast<cx<R>*>(smem_raw);   // [ns][2 ns]
+  cx<R>* fac = aug + (long)ns * 2 * ns;               // [ns]
   __shared__ int piv;
   __shared__ int singular;
   __shared__ double2 ld;
   __shared__ int nswap;
   const int ld2 = 2 * ns;
   const T* Pw = Phi + (long)w * N * 2 * M;
-  // A[a][b] = sum_k D_ka Phi_kb (real trial orbitals)
   for (int e = tid; e < ns * ns; e += nt) {
     int a = e / ns, b = e - a * ns;
     const T* d = PsiT + (long)(j0 + a) * M;
     const T* pr = Pw + ((long)(j0 + b) * 2 + 0) * M;
     const T* pi = pr + M;
-    double sr = 0.0, si = 0.0;
+    R sr = 0, si = 0;
     for (int k = 0; k < M; ++k) {
-      double dk = (double)d[k];
-      sr = fma(dk, (double)pr[k], sr);
-      si = fma(dk, (double)pi[k], si);
+      R dk = (R)d[k];
+      sr = fma(dk, (R)pr[k], sr);
+      si = fma(dk, (R)pi[k], si);
     }
-    aug[a * ld2 + b] = make_double2(sr, si);
-    aug[a * ld2 + ns + b] = make_double2(a == b ? 1.0 : 0.0, 0.0);
+    aug[a * ld2 + b] = mk<R>(sr, si);
+    aug[a * ld2 + ns + b] = mk<R>(a == b ? R(1) : R(0), R(0));
   }
   if (tid == 0) { ld = make_double2(0.0, 0.0); nswap = 0; singular = 0; }
   __syncthreads();
-  // Gauss-Jordan with partial pivoting
   for (int k = 0; k < ns; ++k) {
     if (tid < 32) {
-      double best = -1.0;
+      R best = R(-1);
       int bi = k;
       for (int i = k + tid; i < ns; i += 32) {
-        double2 v = aug[i * ld2 + k];
-        double m = v.x * v.x + v.y * v.y;
+        cx<R> v = aug[i * ld2 + k];
+        R m = v.x * v.x + v.y * v.y;
         if (m > best) { best = m; bi = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
         piv = bi;
-        if (!(best > 0.0)) singular = 1;
+        if (!(best > R(0))) singular = 1;
       }
     }
     __syncthreads();
@@ -256,26 +275,27 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     const int p = piv;
     if (p != k) {
       for (int c = tid; c < ld2; c += nt) {
-        double2 t = aug[k * ld2 + c];
+        cx<R> t = aug[k * ld2 + c];
         aug[k * ld2 + c] = aug[p * ld2 + c];
         aug[p * ld2 + c] = t;
       }
       if (tid == 0) nswap ^= 1;
     }
     __syncthreads();
-    const double2 pv = aug[k * ld2 + k];
+    const cx<R> pv = aug[k * ld2 + k];
     if (tid == 0) {
-      ld.x += log(sqrt(pv.x * pv.x + pv.y * pv.y));
-      ld.y += atan2(pv.y, pv.x);
+      double px = (double)pv.x, py = (double)pv.y;
+      ld.x += 0.5 * log(px * px + py * py);
+      ld.y += atan2(py, px);
     }
     __syncthreads();
-    for (int c = tid; c < ld2; c += nt) aug[k * ld2 + c] = cdiv(aug[k * ld2 + c], pv);
-    for (int i = tid; i < ns; i += nt) fac[i] = (i == k) ? make_double2(0.0, 0.0) : aug[i * ld2 + k];
+    for (int c = tid; c < ld2; c += nt) aug[k * ld2 + c] = div_c(aug[k * ld2 + c], pv);
+    for (int i = tid; i < ns; i += nt) fac[i] = (i == k) ? mk<R>(R(0), R(0)) : aug[i * ld2 + k];
     __syncthreads();
     for (int e = tid; e < ns * ld2; e += nt) {
       int i = e / ld2, c = e - i * ld2;
       if (i == k) continue;
-      aug[e] = csub(aug[e], cmul(fac[i], aug[k * ld2 + c]));
+      aug[e] = sub_mul(aug[e], fac[i], aug[k * ld2 + c]);
     }
     __syncthreads();
   }
@@ -290,7 +310,8 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     double2* Ao = Ainv_out + ((long)w * 2 + sig) * nmax * nmax;
     for (int e = tid; e < ns * ns; e += nt) {
       int a = e / ns, b = e - a * ns;
-      Ao[a * nmax + b] = sing ? make_double2(0.0, 0.0) : aug[a * ld2 + ns + b];
+      cx<R> v = aug[a * ld2 + ns + b];
+      Ao[a * nmax + b] = sing ? make_double2(0.0, 0.0) : make_double2((double)v.x, (double)v.y);
     }
   }
   // Theta[:, a] = sum_b Phi[:, b] Ainv[b][a]
@@ -298,12 +319,12 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
   T* Ti = Theta + ((long)w * 2 + 1) * N * M + (long)j0 * M;
   for (int e = tid; e < M * ns; e += nt) {
     int a = e / M, k = e - a * M;
-    double sr = 0.0, si = 0.0;
+    R sr = 0, si = 0;
     if (!sing) {
       for (int b = 0; b < ns; ++b) {
         const T* pr = Pw + ((long)(j0 + b) * 2 + 0) * M;
-        double xr = (double)pr[k], xi = (double)pr[M + k];
-        double2 iv = aug[b * ld2 + ns + a];
+        R xr = (R)pr[k], xi = (R)pr[M + k];
+        cx<R> iv = aug[b * ld2 + ns + a];
         sr += xr * iv.x - xi * iv.y;
         si += xr * iv.y + xi * iv.x;
       }
@@ -342,12 +363,15 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
 }
 
 // --------------------------------------------------------------- K10
-template <typename T>
+// Modified Gram-Schmidt per walker (both spins in turn), right-looking: once
+// column j is normalised it is projected out of every later column, one warp
+// per column. Arithmetic in R; ln det R = sum_j ln r_jj accumulated in FP64.
+template <typename T, typename R>
 __global__ void mgs_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
                            double2* __restrict__ logO) {
   extern __shared__ unsigned char smem_raw[];
-  double2* Q = reinterpret_cast<double2*>(smem_raw);    // [ns][M]
-  __shared__ double rjj;
+  cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);    // [ns][M]
+  __shared__ R rjj;
   const int w = blockIdx.x;
   const int N = n_up + n_dn;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -361,39 +385,39 @@ __global__ void mgs_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
     __syncthreads();
     for (int e = tid; e < ns * M; e += nt) {
       int b = e / M, k = e - b * M;
-      Q[e] = make_double2((double)Pw[(b * 2 + 0) * M + k], (double)Pw[(b * 2 + 1) * M + k]);
+      Q[e] = mk<R>((R)Pw[(b * 2 + 0) * M + k], (R)Pw[(b * 2 + 1) * M + k]);
     }
     __syncthreads();
     for (int j = 0; j < ns; ++j) {
       if (wid == 0) {
-        double s = 0.0;
+        R s = 0;
         for (int k = lane; k < M; k += 32) {
-          double2 q = Q[j * M + k];
+          cx<R> q = Q[j * M + k];
           s += q.x * q.x + q.y * q.y;
         }
         s = warp_sum(s);
         if (lane == 0) rjj = sqrt(s);
       }
       __syncthreads();
-      const double r = rjj;
-      if (tid == 0) logr += log(r);
+      const R r = rjj;
+      if (tid == 0) logr += log((double)r);
       for (int k = tid; k < M; k += nt) {
-        double2 q = Q[j * M + k];
-        Q[j * M + k] = make_double2(q.x / r, q.y / r);
+        cx<R> q = Q[j * M + k];
+        Q[j * M + k] = mk<R>(q.x / r, q.y / r);
       }
       __syncthreads();
       for (int c = j + 1 + wid; c < ns; c += nw) {
-        double sr = 0.0, si = 0.0;   // r_jc = q_j^H a_c
+        R sr = 0, si = 0;   // r_jc = q_j^H a_c
         for (int k = lane; k < M; k += 32) {
-          double2 q = Q[j * M + k], a = Q[c * M + k];
+          cx<R> q = Q[j * M + k], a = Q[c * M + k];
           sr += q.x * a.x + q.y * a.y;
           si += q.x * a.y - q.y * a.x;
         }
         sr = warp_sum(sr);
         si = warp_sum(si);
         for (int k = lane; k < M; k += 32) {
-          double2 q = Q[j * M + k], a = Q[c * M + k];
-          Q[c * M + k] = make_double2(a.x - (sr * q.x - si * q.y), a.y - (sr * q.y + si * q.x));
+          cx<R> q = Q[j * M + k], a = Q[c * M + k];
+          Q[c * M + k] = mk<R>(a.x - (sr * q.x - si * q.y), a.y - (sr * q.y + si * q.x));
         }
       }
       __syncthreads();
@@ -651,14 +675,22 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, double2* logdet,
-                           double2* Ainv) {
-  static const size_t smem_cap = allow_big_smem(overlap_kernel<T>);
+                           double2* Ainv, bool fp64_compute) {
   int nmax = n_up > n_dn ? n_up : n_dn;
-  size_t smem = sizeof(double2) * ((size_t)nmax * 2 * nmax + nmax);
-  if (smem > smem_cap) return cudaErrorInvalidValue;
   dim3 grid(W, 2);
-  overlap_kernel<T><<<grid, 256, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta, logdet,
-                                            Ainv, nmax);
+  if (fp64_compute) {
+    static const size_t cap = allow_big_smem(overlap_kernel<T, double>);
+    size_t smem = sizeof(double2) * ((size_t)nmax * 2 * nmax + nmax);
+    if (smem > cap) return cudaErrorInvalidValue;
+    overlap_kernel<T, double><<<grid, 256, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
+                                                      logdet, Ainv, nmax);
+  } else {
+    static const size_t cap = allow_big_smem(overlap_kernel<T, float>);
+    size_t smem = sizeof(float2) * ((size_t)nmax * 2 * nmax + nmax);
+    if (smem > cap) return cudaErrorInvalidValue;
+    overlap_kernel<T, float><<<grid, 256, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
+                                                     logdet, Ainv, nmax);
+  }
   return cudaGetLastError();
 }
 
@@ -678,12 +710,19 @@ cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
 
 template <typename T>
 cudaError_t launch_mgs(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
-                       double2* logO) {
-  static const size_t smem_cap = allow_big_smem(mgs_kernel<T>);
+                       double2* logO, bool fp64_compute) {
   int nmax = n_up > n_dn ? n_up : n_dn;
-  size_t smem = sizeof(double2) * (size_t)nmax * M;
-  if (smem > smem_cap) return cudaErrorInvalidValue;
-  mgs_kernel<T><<<W, 256, smem, st>>>(M, n_up, n_dn, Phi, logO);
+  if (fp64_compute) {
+    static const size_t cap = allow_big_smem(mgs_kernel<T, double>);
+    size_t smem = sizeof(double2) * (size_t)nmax * M;
+    if (smem > cap) return cudaErrorInvalidValue;
+    mgs_kernel<T, double><<<W, 256, smem, st>>>(M, n_up, n_dn, Phi, logO);
+  } else {
+    static const size_t cap = allow_big_smem(mgs_kernel<T, float>);
+    size_t smem = sizeof(float2) * (size_t)nmax * M;
+    if (smem > cap) return cudaErrorInvalidValue;
+    mgs_kernel<T, float><<<W, 256, smem, st>>>(M, n_up, n_dn, Phi, logO);
+  }
   return cudaGetLastError();
 }
 
@@ -771,8 +810,9 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
   template cudaError_t launch_taylor<T>(cudaStream_t, int, int, int, int, const T*,     \
                                         const T*, T*);                                  \
   template cudaError_t launch_overlap<T>(cudaStream_t, int, int, int, int, const T*,    \
-                                         const T*, T*, double2*, double2*);             \
-  template cudaError_t launch_mgs<T>(cudaStream_t, int, int, int, int, T*, double2*);   \
+                                         const T*, T*, double2*, double2*, bool);       \
+  template cudaError_t launch_mgs<T>(cudaStream_t, int, int, int, int, T*, double2*,    \
+                                     bool);                                             \
   template cudaError_t launch_energy_reduce<T>(cudaStream_t, int, int, int, int, int,   \
                                                const T*, long, const T*, const T*,      \
                                                double2*);                               \

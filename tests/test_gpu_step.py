@@ -29,8 +29,8 @@ def gpu_ctx(system, **kw):
 
 
 def side_by_side(system, precision, n_steps, rtol, walkers=None, energy_at=(),
-                 green_every=0):
-    gpu = gpu_ctx(system, precision=precision)
+                 green_every=0, **kw):
+    gpu = gpu_ctx(system, precision=precision, **kw)
     orc = O.OracleRun(system, walker_ids=walkers)
     e0, _ = gpu.afqmc_local_energy()
     assert abs(e0[0].real - orc.e_shift) <= rtol * max(1.0, abs(orc.e_shift))
@@ -115,10 +115,12 @@ def test_c1_twenty_steps_fp32():
     print("c1 fp32 worst", w)
 
 
-def test_c2_full_size_sampled_fp32():
+@pytest.mark.parametrize("islands", [False, True])
+def test_c2_full_size_sampled_fp32(islands):
     s = config_c2()
-    w = side_by_side(s, "fp32", 19, 1e-4, walkers=[0, 1023], energy_at=(19,))
-    print("c2 fp32 worst", w)
+    w = side_by_side(s, "fp32", 19, 1e-4, walkers=[0, 1023], energy_at=(19,),
+                     fp64_islands=islands)
+    print(f"c2 fp32 islands={islands} worst", w)
 
 
 def test_checkpoint_resume_is_bitwise():
