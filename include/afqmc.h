@@ -190,8 +190,42 @@ afqmc_status afqmc_kernel_stats(afqmc_ctx* ctx, int32_t kernel_id,
 /* Number of kernel launches issued since creation (all of this library's). */
 int64_t afqmc_launch_count(const afqmc_ctx* ctx);
 
+/* Comb population control that allocates no device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc: applications whose device memory is all owned by
+ * another memory manager (a framework's caching allocator or a pool reserved
+ * at start-up) and real-time or certified hosts that forbid device
+ * allocation after initialisation. It runs the same blocked FP64 prefix sum
+ * and comb as afqmc_population_control, but on the caller's device buffers,
+ * with its scratch in a file-scope device array of
+ * AFQMC_COMB_STATIC_MAX_WALKERS + 1 doubles (512 KB) that every GPU loading
+ * the library holds until the process exits.
+ *
+ *  d_weight  [n_walkers] device, walker weights (read only)
+ *  n_walkers 1 .. AFQMC_COMB_STATIC_MAX_WALKERS, else AFQMC_E_INVALID
+ *  seed, run_id, step   Philox key, stream tag and step counter of the comb
+ *            offset (stream 1), as in afqmc_population_control
+ *  d_parent  [n_walkers] device, receives the parent index of each new walker
+ *  d_wnew    [1] device, receives the common new weight sum(W)/n_walkers, or
+ *            -1 (with d_parent the identity) when every weight is zero
+ *  stream    cudaStream_t to run on (NULL: the legacy default stream)
+ *
+ * Asynchronous on `stream`; it calls no cudaMalloc, cudaFree or allocating
+ * library routine. The first call on each device looks up the scratch
+ * array's device address (with that device current) and should come before
+ * any stream capture. All calls share the one array, which keeps the last
+ * call's contents (the call clears what must start at zero), so calls that
+ * overlap on the GPU race: serialise them, e.g. on one stream. Errors are
+ * described by afqmc_last_error(NULL). */
+#define AFQMC_COMB_STATIC_MAX_WALKERS 65536
+afqmc_status afqmc_comb_static(const double* d_weight, int32_t n_walkers,
+                               uint64_t seed, int32_t run_id, int64_t step,
+                               int32_t* d_parent, double* d_wnew, void* stream);
+
 /* Text of the last error on this context ("" if none); valid until the next
- * call on the context. ctx may be NULL for errors of afqmc_create. */
+ * call on the context. ctx may be NULL for errors of afqmc_create and of the
+ * context-free calls. */
 const char* afqmc_last_error(const afqmc_ctx* ctx);
 
 /* Free all device memory of the context and the stream it owns. */

@@ -77,6 +77,8 @@ def load_library(path: str = LIB_PATH):
         "afqmc_launch_count": (C.c_int64, [vp]),
         "afqmc_last_error": (C.c_char_p, [vp]),
         "afqmc_destroy": (None, [vp]),
+        "afqmc_comb_static": (C.c_int, [vp, C.c_int32, C.c_uint64, C.c_int32,
+                                        C.c_int64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -291,3 +293,18 @@ def encode_state(template: bytes, Phi_up, Phi_dn, weight, logO, step=None) -> by
     z = np.ascontiguousarray(np.swapaxes(z, 1, 2), dtype=np.complex128)
     return (h.tobytes() + z.tobytes() + np.asarray(weight, np.float64).tobytes()
             + np.asarray(logO, np.complex128).tobytes())
+
+
+COMB_STATIC_MAX_WALKERS = 65536
+
+
+def afqmc_comb_static(d_weight: int, n_walkers: int, seed: int, run_id: int,
+                      step: int, d_parent: int, d_wnew: int, stream: int = 0):
+    """Comb population control on caller-owned device buffers (raw device
+    pointers), allocating no device memory; see include/afqmc.h."""
+    lib = load_library()
+    s = lib.afqmc_comb_static(C.c_void_p(d_weight), n_walkers, seed, run_id, step,
+                              C.c_void_p(d_parent), C.c_void_p(d_wnew),
+                              C.c_void_p(stream) if stream else None)
+    if s != 0:
+        raise AfqmcError(s, lib.afqmc_last_error(None).decode())

@@ -69,6 +69,14 @@ namespace {
 
 const int kHist = 4096;
 thread_local std::string g_create_err;
+}  // namespace
+
+namespace afqmc {
+// Error text of calls that have no context (read by afqmc_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace afqmc
+
+namespace {
 
 afqmc_status fail(afqmc_ctx* c, afqmc_status s, const std::string& msg) {
   if (c) {
