@@ -50,13 +50,26 @@ struct afqmc_ctx {
   // precomputed operators in the step precision
   void *L, *Ltil, *Bhalf, *PsiT, *Yx_up, *Yx_dn;
   double* PsiT64;
-  double *weight, *scan, *wnew, *escalar;
+  double *weight, *scan, *wnew, *escalar, *lr;
   double2 *logO, *logO2, *logO_new, *logdet, *lw, *eloc, *hist;
   int *parent, *status;
   std::vector<void*> allocs;
 
-  // tensor-core operand copies (TF32 modes)
-  TcPlan* tc;
+  // padded strides (TMA needs 16-byte-aligned rows)
+  long ldS;          // S row stride: n_chol rounded up to 4
+  long ldx;          // X row stride: n_chol + 1
+  long dn_off, ldt;  // Theta: down block offset and row stride
+  long Jp[2];        // Yx / Z row strides per spin
+  int xsplit;        // K splits of the force-bias contraction
+  void* LT;          // L transposed [M*M][ldS] (tensor-core operand)
+  void* dB;          // B_half - I (tensor-core operand)
+  void* bimg;        // (B_half - I) operand image for the fused tensor-core Taylor kernel
+
+  // tensor-core resources (TF32 modes)
+  TcCtx* tc;
+  bool tc_taylor_ok;  // M <= 64: on-chip tensor-core Taylor kernel
+  bool tc_bhalf_ok;   // M % 4 == 0: B_half on the tensor cores
+  bool split3;
 
   bool timing;
   std::vector<TimedPair> pending;
@@ -174,6 +187,10 @@ afqmc_status check_status(afqmc_ctx* c) {
   int s = 0;
   CK(cudaMemcpyAsync(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (s & 4) {
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+    return fail(c, AFQMC_E_TIMEOUT, "a tensor-core pipeline wait timed out");
+  }
   if (s & 2) {
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
     return fail(c, AFQMC_E_POPULATION, "population control found every walker weight zero");
@@ -187,21 +204,22 @@ afqmc_status check_status(afqmc_ctx* c) {
 
 template <typename T>
 afqmc_status force_bias_contraction(afqmc_ctx* c) {
-  const int W = c->W, N = c->N, M = c->M, G = c->G;
+  const int W = c->W, G = c->G;
   KTimer t(c, 0);
   if (c->tc) {
-    LK(tc_force_bias(c->tc, c->st, (const float*)c->Theta, (float*)c->X));
+    LK(tc_gemm(c->tc, c->st, 2 * W, G + 1, (int)c->ldt, (const float*)c->Theta, c->ldt,
+               (const float*)c->Ltil, c->ldt, (float*)c->X, c->ldx, 1.0f, 0.0f, nullptr, 0,
+               c->split3, c->xsplit, 2L * W * c->ldx, c->status));
   } else {
-    LK(gemm<T>(c->st, false, true, 2 * W, G + 1, N * M, T(1), (const T*)c->Theta,
-               (long)N * M, 0, (const T*)c->Ltil, (long)N * M, 0, T(0), (T*)c->X,
-               G + 1, 0, 1));
+    LK(gemm<T>(c->st, false, true, 2 * W, G + 1, (int)c->ldt, T(1), (const T*)c->Theta,
+               c->ldt, 0, (const T*)c->Ltil, c->ldt, 0, T(0), (T*)c->X, c->ldx, 0, 1));
   }
   return AFQMC_OK;
 }
 
 template <typename T>
 afqmc_status measure_T(afqmc_ctx* c, bool record) {
-  const int W = c->W, N = c->N, M = c->M, G = c->G;
+  const int W = c->W, M = c->M, G = c->G;
   afqmc_status s = force_bias_contraction<T>(c);
   if (s != AFQMC_OK) return s;
   {
@@ -209,21 +227,25 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
     long zoff = 0;
     for (int sig = 0; sig < 2; ++sig) {
       const int ns = sig ? c->nd : c->nu;
-      const int j0 = sig ? c->nu : 0;
+      const long off = sig ? c->dn_off : 0;
+      const long ldz = c->Jp[sig];
       if (ns == 0) continue;
       const long J = (long)ns * M;
       const T* Y = (const T*)(sig ? c->Yx_dn : c->Yx_up);
       if (c->tc) {
-        LK(tc_exchange(c->tc, c->st, sig, (const float*)c->Theta, (float*)c->Z + zoff));
+        LK(tc_gemm(c->tc, c->st, 2 * W, (int)J, (int)J, (const float*)c->Theta + off, c->ldt,
+                   (const float*)Y, ldz, (float*)c->Z + zoff, ldz, 1.0f, 0.0f, nullptr, 0,
+                   c->split3, 1, 0, c->status));
       } else {
         LK(gemm<T>(c->st, false, false, 2 * W, (int)J, (int)J, T(1),
-                   (const T*)c->Theta + (long)j0 * M, (long)N * M, 0, Y, J, 0, T(0),
-                   (T*)c->Z + zoff, J, 0, 1));
+                   (const T*)c->Theta + off, c->ldt, 0, Y, ldz, 0, T(0), (T*)c->Z + zoff,
+                   ldz, 0, 1));
       }
-      zoff += 2L * W * J;
+      zoff += 2L * W * ldz;
     }
-    LK(launch_energy_reduce<T>(c->st, W, M, c->nu, c->nd, G, (const T*)c->X, G + 1,
-                               (const T*)c->Theta, (const T*)c->Z, c->eloc));
+    LK(launch_energy_reduce<T>(c->st, W, M, c->nu, c->nd, G, (const T*)c->X, c->ldx,
+                               c->xsplit, 2L * W * c->ldx, (const T*)c->Theta, c->ldt,
+                               c->dn_off, (const T*)c->Z, c->Jp[0], c->Jp[1], c->eloc));
   }
   LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, (double)c->step,
                          record ? c->hist : nullptr, (int)(c->n_meas % kHist),
@@ -235,7 +257,8 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
 template <typename T>
 afqmc_status mgs_T(afqmc_ctx* c) {
   KTimer t(c, 6);
-  LK(launch_mgs<T>(c->st, c->W, c->M, c->nu, c->nd, (T*)c->Phi, c->logO, c->fp64_islands));
+  LK(launch_qr<T>(c->st, c->W, c->M, c->nu, c->nd, (T*)c->Phi, c->logO, c->lr,
+                  c->fp64_islands));
   return AFQMC_OK;
 }
 
@@ -246,7 +269,7 @@ afqmc_status comb_T(afqmc_ctx* c) {
   LK(launch_comb(c->st, W, c->weight, c->p.seed, c->p.run_id, c->step, c->parent, c->scan,
                  c->wnew, c->status));
   const long pe = (long)c->N * 2 * c->M;
-  LK(launch_gather<T>(c->st, W, pe, pe, c->parent, (const T*)c->Phi, (T*)c->Phi2,
+  LK(launch_gather<T>(c->st, W, pe, 2 * c->ldt, c->parent, (const T*)c->Phi, (T*)c->Phi2,
                       (const T*)c->Theta, (T*)c->Theta2, c->logO, c->logO2, c->wnew,
                       c->weight));
   std::swap(c->Phi, c->Phi2);
@@ -258,8 +281,8 @@ afqmc_status comb_T(afqmc_ctx* c) {
 template <typename T>
 afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
   LK(launch_overlap<T>(c->st, c->W, c->M, c->nu, c->nd, (const T*)c->Phi,
-                       (const T*)c->PsiT, (T*)c->Theta, c->logdet, nullptr,
-                       c->fp64_islands));
+                       (const T*)c->PsiT, (T*)c->Theta, c->ldt, c->dn_off, c->logdet,
+                       nullptr, c->fp64_islands));
   LK(launch_logdet_sum(c->st, c->W, c->logdet, logO_out));
   return AFQMC_OK;
 }
@@ -272,31 +295,51 @@ afqmc_status step_T(afqmc_ctx* c) {
   if (s != AFQMC_OK) return s;
   {
     KTimer t(c, 1);
-    LK(launch_fields<T>(c->st, W, G, (const T*)c->X, G + 1, sqrt(dt), c->p.fb_cap,
-                        c->p.seed, c->p.run_id, c->step, (T*)c->S, (T*)c->xbar, c->lw));
+    LK(launch_fields<T>(c->st, W, G, (const T*)c->X, c->ldx, c->xsplit, 2L * W * c->ldx,
+                        sqrt(dt), c->p.fb_cap, c->p.seed, c->p.run_id, c->step, (T*)c->S,
+                        c->ldS, (T*)c->xbar, c->lw));
   }
   {
     KTimer t(c, 2);
     if (c->tc) {
-      LK(tc_one_body(c->tc, c->st, (const float*)c->S, (float*)c->V));
+      LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
+                 (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
+                 nullptr, 0, c->split3, 1, 0, c->status));
     } else {
-      LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, G, 0,
+      LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, c->ldS, 0,
                  (const T*)c->L, (long)M * M, 0, T(0), (T*)c->V, (long)M * M, 0, 1));
     }
   }
   {
     KTimer t(c, 3);
-    if (c->tc) {
-      LK(tc_propagate(c->tc, c->st, (const float*)c->V, (float*)c->Phi, (float*)c->Phi2,
-                      (float*)c->Phi3));
+    const int rows = W * N * 2;
+    if (c->tc && c->tc_taylor_ok) {   // B_half exp(V) B_half in one tensor-core kernel
+      LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
+                   (const float*)c->Phi, (float*)c->Phi3, (const float*)c->bimg, c->split3,
+                   c->status));
+      std::swap(c->Phi, c->Phi3);
     } else {
-      const int rows = W * N * 2;
+    // Phi2 = B_half Phi
+    if (c->tc && c->tc_bhalf_ok) {
+      LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi, M, (const float*)c->dB, M,
+                 (float*)c->Phi2, M, 1.0f, 1.0f, (const float*)c->Phi, M, c->split3, 1, 0,
+                 c->status));
+    } else {
       LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi, M, 0,
                  (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi2, M, 0, 1));
-      LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V,
-                          (const T*)c->Phi2, (T*)c->Phi3));
+    }
+    // Phi3 = exp_T(V) Phi2
+    LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V,
+                        (const T*)c->Phi2, (T*)c->Phi3));
+    // Phi = B_half Phi3
+    if (c->tc && c->tc_bhalf_ok) {
+      LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi3, M, (const float*)c->dB, M,
+                 (float*)c->Phi, M, 1.0f, 1.0f, (const float*)c->Phi3, M, c->split3, 1, 0,
+                 c->status));
+    } else {
       LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi3, M, 0,
                  (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi, M, 0, 1));
+    }
     }
   }
   {
@@ -355,10 +398,11 @@ afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
   if (p->ortho_every < 0 || p->measure_every < 0 || p->pc_every < 0)
     return fail(c, AFQMC_E_INVALID, "cadences must be >= 0");
   const int nmax = p->n_up > p->n_dn ? p->n_up : p->n_dn;
-  if ((size_t)nmax * 2 * nmax * 16 + nmax * 16 > 227 * 1024)
-    return fail(c, AFQMC_E_INVALID, "electrons per spin too large for the on-chip inverse");
-  if ((size_t)nmax * M * 16 > 227 * 1024)
-    return fail(c, AFQMC_E_INVALID, "M x electrons per spin too large for on-chip Gram-Schmidt");
+  const bool f64 = p->precision == AFQMC_FP64 || p->fp64_islands;
+  if (afqmc::overlap_smem(M, nmax, f64 ? 16 : 8) > 227 * 1024)
+    return fail(c, AFQMC_E_INVALID,
+                "M x electrons per spin too large for the on-chip overlap and QR in this "
+                "precision");
   // symmetry of h1 and L
   double scale = 0.0;
   for (long e = 0; e < (long)M * M; ++e) scale = fmax(scale, fabs(h1[e]));
@@ -425,8 +469,10 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     return AFQMC_OK;
   };
 #define TM(p, n) do { afqmc_status s_ = tmalloc(&p, (n)); if (s_ != AFQMC_OK) return s_; } while (0)
+  double *Ltil_pad;
   TM(h1, MM); TM(L, (size_t)G * MM); TM(PsiT, (size_t)N * M); TM(h1p, MM); TM(Bh, MM);
   TM(Ltil, (size_t)(G + 1) * N * M); TM(ta, MM); TM(tb, MM); TM(tcur, MM); TM(tnext, MM);
+  TM(Ltil_pad, (size_t)(G + 1) * c->ldt);
   std::vector<double> psiT_h((size_t)N * M);
   for (int a = 0; a < N; ++a) {
     const bool up = a < c->nu;
@@ -480,12 +526,28 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     TM(yx, (size_t)J * J);
     LK(gemm<double>(st, true, false, (int)J, (int)J, G, 1.0, Ltil + (size_t)j0 * M,
                     (long)N * M, 0, Ltil + (size_t)j0 * M, (long)N * M, 0, 0.0, gram, J, 0, 1));
-    LK(launch_yx_permute(st, ns, M, gram, yx));
+    CK(cudaMemsetAsync(yx, 0, (size_t)J * J * sizeof(double), st));
+    LK(launch_yx_permute(st, ns, M, gram, yx, c->Jp[sig]));
     void* dst = sig ? c->Yx_dn : c->Yx_up;
-    LK(launch_convert<T>(st, J * J, yx, (T*)dst));
+    LK(launch_convert<T>(st, J * c->Jp[sig], yx, (T*)dst));
   }
   LK(launch_convert<T>(st, (long)G * MM, L, (T*)c->L));
-  LK(launch_convert<T>(st, (long)(G + 1) * N * M, Ltil, (T*)c->Ltil));
+  CK(cudaMemsetAsync(Ltil_pad, 0, (size_t)(G + 1) * c->ldt * sizeof(double), st));
+  LK(launch_pad_rows(st, G + 1, (long)c->nu * M, (long)c->nd * M, Ltil, Ltil_pad, c->ldt,
+                     c->dn_off));
+  LK(launch_convert<T>(st, (long)(G + 1) * c->ldt, Ltil_pad, (T*)c->Ltil));
+  if (c->LT) {   // L transposed [M*M][ldS] and B_half - I for the tensor cores
+    double *lt;
+    TM(lt, MM * c->ldS);
+    CK(cudaMemsetAsync(lt, 0, MM * c->ldS * sizeof(double), st));
+    LK(launch_transpose(st, G, (long)MM, L, lt, c->ldS));
+    LK(launch_convert<T>(st, (long)MM * c->ldS, lt, (T*)c->LT));
+    CK(cudaMemcpyAsync(tb, Bh, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    LK(launch_add_diag(st, M, tb, -1.0));                  // B_half - I
+    LK(launch_convert<T>(st, MM, tb, (T*)c->dB));
+    if (c->bimg)
+      LK(tc_bhalf_image(st, M, (const float*)c->dB, (float*)c->bimg, c->split3));
+  }
   LK(launch_convert<T>(st, MM, Bh, (T*)c->Bhalf));
   LK(launch_convert<T>(st, (long)N * M, PsiT, (T*)c->PsiT));
   CK(cudaStreamSynchronize(st));
@@ -509,6 +571,8 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   return AFQMC_OK;
 }
 
+long round4(long x) { return (x + 3) / 4 * 4; }
+
 afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
                          const double* Cu, const double* Cd, const int32_t* ou,
                          const int32_t* od) {
@@ -516,27 +580,54 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   const size_t es = esize(c);
   const size_t MM = (size_t)M * M;
   const size_t phi = (size_t)W * N * 2 * M;
+  const bool tcmode = c->p.precision == AFQMC_TF32 || c->p.precision == AFQMC_TF32X3;
+  c->ldS = round4(G);
+  c->ldx = G + 1;
+  c->dn_off = round4((long)c->nu * M);
+  c->ldt = c->dn_off + round4((long)c->nd * M);
+  c->Jp[0] = round4((long)c->nu * M);
+  c->Jp[1] = round4((long)c->nd * M);
+  c->xsplit = 1;
+  c->split3 = c->p.precision == AFQMC_TF32X3;
+  c->tc_taylor_ok = tcmode && M <= 64;
+  c->tc_bhalf_ok = tcmode && M % 4 == 0;
+  if (tcmode) {
+    // split K of the force-bias contraction so that its few output tiles
+    // still fill the GPU; partial sums are added in order by the consumers
+    const long tiles = ((2L * W + 127) / 128) * ((G + 1 + 127) / 128);
+    const long ktiles = (c->ldt + 31) / 32;
+    int ks = 1;
+    while (tiles * ks * 2 <= 2 * 152 && ks * 2 <= 8 && ktiles / (ks * 2) >= 4) ks *= 2;
+    c->xsplit = ks;
+  }
   DALLOC(c->Phi, phi * es);
   DALLOC(c->Phi2, phi * es);
   DALLOC(c->Phi3, phi * es);
-  DALLOC(c->Theta, phi * es);
-  DALLOC(c->Theta2, phi * es);
+  DALLOC(c->Theta, (size_t)W * 2 * c->ldt * es);
+  DALLOC(c->Theta2, (size_t)W * 2 * c->ldt * es);
   DALLOC(c->V, (size_t)W * 2 * MM * es);
-  DALLOC(c->X, (size_t)W * 2 * (G + 1) * es);
-  DALLOC(c->S, (size_t)W * 2 * G * es);
+  DALLOC(c->X, (size_t)c->xsplit * W * 2 * c->ldx * es);
+  DALLOC(c->S, (size_t)W * 2 * c->ldS * es);
   DALLOC(c->xbar, (size_t)W * 2 * G * es);
-  const size_t Jt = (size_t)c->nu * c->nu * MM + (size_t)c->nd * c->nd * MM;
-  DALLOC(c->Z, (size_t)2 * W * ((size_t)c->nu * M + (size_t)c->nd * M) * es);
+  DALLOC(c->Z, (size_t)2 * W * (c->Jp[0] + c->Jp[1]) * es);
   DALLOC(c->L, (size_t)G * MM * es);
-  DALLOC(c->Ltil, (size_t)(G + 1) * N * M * es);
+  DALLOC(c->Ltil, (size_t)(G + 1) * c->ldt * es);
   DALLOC(c->Bhalf, MM * es);
   DALLOC(c->PsiT, (size_t)N * M * es);
   DALLOC(c->PsiT64, (size_t)N * M * sizeof(double));
-  DALLOC(c->Yx_up, (size_t)c->nu * c->nu * MM * es);
-  DALLOC(c->Yx_dn, (size_t)c->nd * c->nd * MM * es);
-  (void)Jt;
+  DALLOC(c->Yx_up, (size_t)c->nu * M * c->Jp[0] * es);
+  DALLOC(c->Yx_dn, (size_t)c->nd * M * c->Jp[1] * es);
+  c->LT = nullptr;
+  c->dB = nullptr;
+  c->bimg = nullptr;
+  if (tcmode) {
+    DALLOC(c->LT, MM * c->ldS * es);
+    DALLOC(c->dB, MM * es);
+    if (c->tc_taylor_ok) DALLOC(c->bimg, tc_bhalf_image_floats(c->split3) * sizeof(float));
+  }
   DALLOC(c->weight, W * sizeof(double));
   DALLOC(c->scan, W * sizeof(double));
+  DALLOC(c->lr, 2 * W * sizeof(double));
   DALLOC(c->wnew, sizeof(double));
   DALLOC(c->escalar, sizeof(double));
   DALLOC(c->logO, W * sizeof(double2));
@@ -551,23 +642,21 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
   CK(cudaMemsetAsync(c->lw, 0, W * sizeof(double2), c->st));
   CK(cudaMemsetAsync(c->xbar, 0, (size_t)W * 2 * G * es, c->st));
+  CK(cudaMemsetAsync(c->S, 0, (size_t)W * 2 * c->ldS * es, c->st));
+  CK(cudaMemsetAsync(c->Theta, 0, (size_t)W * 2 * c->ldt * es, c->st));
+  CK(cudaMemsetAsync(c->Theta2, 0, (size_t)W * 2 * c->ldt * es, c->st));
+  CK(cudaMemsetAsync(c->X, 0, (size_t)c->xsplit * W * 2 * c->ldx * es, c->st));
+  if (tcmode) {
+    cudaError_t e = tc_create(&c->tc);
+    if (e != cudaSuccess)
+      return fail(c, AFQMC_E_CUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
+  }
   afqmc_status s = c->fp64 ? setup_T<double>(c, h1, L, Cu, Cd, ou, od)
                            : setup_T<float>(c, h1, L, Cu, Cd, ou, od);
   if (s != AFQMC_OK) return s;
-  if (c->p.precision == AFQMC_TF32 || c->p.precision == AFQMC_TF32X3) {
-    TcShape sh{c->W, c->M, c->nu, c->nd, c->G, c->p.taylor_order,
-               c->p.precision == AFQMC_TF32X3};
-    cudaError_t e = tc_plan_create(&c->tc, sh, c->st, (const float*)c->L,
-                                   (const float*)c->Ltil, (const float*)c->Bhalf,
-                                   (const float*)c->Yx_up, (const float*)c->Yx_dn);
-    if (e != cudaSuccess)
-      return fail(c, e == cudaErrorMemoryAllocation ? AFQMC_E_OOM : AFQMC_E_CUDA,
-                  std::string("tensor-core plan: ") + cudaGetErrorString(e));
-  }
   CK(cudaStreamSynchronize(c->st));
   return AFQMC_OK;
 }
-
 
 #define GUARD(c)                                                        \
   do {                                                                  \
@@ -689,15 +778,16 @@ afqmc_status afqmc_green(afqmc_ctx* c, int32_t walker, double* G_up, double* G_d
   if (walker < 0 || walker >= c->W) return fail(c, AFQMC_E_INVALID, "walker out of range");
   const int M = c->M, N = c->N;
   const size_t es = esize(c);
-  std::vector<unsigned char> th(2 * (size_t)N * M * es);
-  CK(cudaMemcpyAsync(th.data(), (const unsigned char*)c->Theta + (size_t)walker * 2 * N * M * es,
+  std::vector<unsigned char> th(2 * (size_t)c->ldt * es);
+  CK(cudaMemcpyAsync(th.data(), (const unsigned char*)c->Theta + (size_t)walker * 2 * c->ldt * es,
                      th.size(), cudaMemcpyDeviceToHost, c->st));
   std::vector<double> psi((size_t)N * M);
   CK(cudaMemcpyAsync(psi.data(), c->PsiT64, psi.size() * sizeof(double),
                      cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   auto theta = [&](int cc, int a, int k) -> double {
-    size_t idx = ((size_t)cc * N + a) * M + k;
+    size_t idx = (size_t)cc * c->ldt + (a < c->nu ? (size_t)a * M
+                                                  : c->dn_off + (size_t)(a - c->nu) * M) + k;
     return c->fp64 ? ((const double*)th.data())[idx] : (double)((const float*)th.data())[idx];
   };
   // G_ij = sum_a Theta_ja D_ia (G^T = Theta D^H, real trial orbitals)
@@ -907,7 +997,7 @@ void afqmc_destroy(afqmc_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (auto& t : c->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   for (auto e : c->free_events) cudaEventDestroy(e);
-  if (c->tc) tc_plan_destroy(c->tc);
+  if (c->tc) tc_destroy(c->tc);
   for (void* p : c->allocs) cudaFree(p);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;

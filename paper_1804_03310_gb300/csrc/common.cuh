@@ -57,6 +57,19 @@ __device__ __forceinline__ void box_muller(uint32_t ra, uint32_t rb, double& z0,
   z1 = rad * s;
 }
 
+// The same pair in single precision: u = (r + 1/2) 2^-32 rounded to FP32
+// (never 0 or 1 after rounding for r < 2^32 - 128; the top values map to
+// 1 - 2^-24 by clamping).
+__device__ __forceinline__ void box_muller_f(uint32_t ra, uint32_t rb, float& z0, float& z1) {
+  float ua = fminf(((float)ra + 0.5f) * 2.3283064365386963e-10f, 0.99999994f);
+  float ub = ((float)rb + 0.5f) * 2.3283064365386963e-10f;
+  float rad = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
 enum { kStreamFields = 0, kStreamComb = 1 };
 
 // ----------------------------------------------------------------------------

@@ -4,11 +4,15 @@
 // Walker layouts (T = double on the FP64 path, float otherwise):
 //   Phi    [W][N][2][M]   column j of walker w (j < n_up: spin up), re plane
 //                         then im plane, M basis coefficients each
-//   Theta  [W][2][N][M]   Theta = Phi (D^H Phi)^-1, re block then im block,
-//                         so row (w, c) is one contiguous N*M vector
+//   Theta  [W][2][ldt]    Theta = Phi (D^H Phi)^-1, re row then im row; each
+//                         row holds the up block (n_up*M, column a at a*M)
+//                         at 0 and the down block at dn_off, both 16-byte
+//                         aligned, zeros in the padding
 //   V      [W][2][M][M]   one-body operator per walker (complex symmetric)
-//   X      [W][2][ldx]    force-bias contraction per walker, re row, im row
-//   S      [W][2][n_chol] i sqrt(dt) (x - xbar) per walker
+//   X      [nsplit][W][2][ldx]  force-bias contraction partial sums, ldx =
+//                         n_chol + 1 (last column: tr(h~ Theta))
+//   S      [W][2][ldS]    i sqrt(dt) (x - xbar) per walker, ldS = n_chol
+//                         rounded up to a multiple of 4
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,11 +26,13 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, T alpha
                  T beta, T* C, long ldc, long sC, int batch);
 
 // K1 + K3: Philox fields, capped force bias, shifted fields and the log of
-// the importance factor sum_g (x xbar - xbar^2/2) per walker.
+// the importance factor sum_g (x xbar - xbar^2/2) per walker. X holds
+// `nsplit` partial sums (split_stride elements apart) that are added in order.
 template <typename T>
 cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
-                          double sqdt, double cap, uint64_t seed, int run_id,
-                          long step, T* S, T* xbar, double2* lw);
+                          int nsplit, long split_stride, double sqdt, double cap,
+                          uint64_t seed, int run_id, long step, T* S, long ldS, T* xbar,
+                          double2* lw);
 
 // K5 on the CUDA cores: Phi_out = sum_{n<=order} V^n Phi_in / n!.
 template <typename T>
@@ -40,7 +46,7 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
 // [W][2][nmax][nmax] double2 receives A^-1 per spin.
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
-                           const T* Phi, const T* PsiT, T* Theta,
+                           const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
                            double2* logdet, double2* Ainv, bool fp64_compute);
 
 // K7: hybrid weight and phaseless cut from the new log-overlap.
@@ -52,17 +58,22 @@ cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
 cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
                               double2* out);
 
-// K10: modified Gram-Schmidt per walker and spin (FP64 arithmetic when
-// fp64_compute, else FP32); logO -= ln det R accumulated in FP64.
+// K10: QR orthonormalisation per walker and spin, Phi <- Q with R's
+// diagonal real and positive (FP64 arithmetic when fp64_compute, else FP32);
+// logO -= ln det R accumulated in FP64. lr [W][2] is scratch.
 template <typename T>
-cudaError_t launch_mgs(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
-                       double2* logO, bool fp64_compute);
+cudaError_t launch_qr(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
+                      double2* logO, double* lr, bool fp64_compute);
+size_t overlap_smem(int M, int nmax, size_t csize);
 
-// K9 epilogue: E_L = E1 + 1/2 sum X^2 + sum_sigma 1/2 theta^T Yx theta.
+// K9 epilogue: E_L = E1 + 1/2 sum X^2 + sum_sigma 1/2 theta^T Yx theta, with
+// X split as for launch_fields and Z^sigma = Theta^sigma Yx^sigma per spin
+// ([2W][ldz] each, up block first).
 template <typename T>
 cudaError_t launch_energy_reduce(cudaStream_t st, int W, int M, int n_up, int n_dn,
-                                 int n_chol, const T* X, long ldx, const T* Theta,
-                                 const T* Z, double2* eloc);
+                                 int n_chol, const T* X, long ldx, int nsplit,
+                                 long split_stride, const T* Theta, long ldt, long dn_off,
+                                 const T* Z, long ldz_up, long ldz_dn, double2* eloc);
 
 // Weighted mixed estimate sum W Re E / sum W (walkers with W > 0) into
 // hist[slot] = (step, value).
@@ -90,7 +101,11 @@ cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double
 cudaError_t launch_scale_identity(cudaStream_t st, int M, const double* A, double s,
                                   double* out_I_plus, double* out_scaled);
 cudaError_t launch_yx_permute(cudaStream_t st, int n, int M, const double* gram,
-                              double* yx);
+                              double* yx, long ldy);
+cudaError_t launch_pad_rows(cudaStream_t st, long rows, long Jup, long Jdn,
+                            const double* in, double* out, long ld, long dn_off);
+cudaError_t launch_transpose(cudaStream_t st, long rows, long cols, const double* in,
+                             double* out, long ldo);
 template <typename T>
 cudaError_t launch_convert(cudaStream_t st, long n, const double* in, T* out);
 template <typename T>
@@ -98,5 +113,6 @@ cudaError_t launch_init_walkers(cudaStream_t st, int W, int M, int N, const T* P
                                 T* Phi, double* weight);
 cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x,
                           double* y);
+cudaError_t launch_add_diag(cudaStream_t st, int M, double* A, double a);
 
 }  // namespace afqmc

@@ -1,27 +1,603 @@
-// Tensor-core plan: not yet built; the TF32 modes report "not supported".
+// Tensor-core kernels (tcgen05 MMA, TMEM accumulators, TMA operand loads)
+// for the dense contractions of the walker step in the TF32 modes:
+//
+//  * tc_gemm_kernel: C = alpha A B^T + beta R with both operands K-major,
+//    128 x BN output tiles, a multi-stage TMA -> MMA pipeline and one
+//    accumulator tile in TMEM. Used for the force bias (Theta . L~^T, Sec. II),
+//    the one-body operator (S . L, Eq. 3), the exchange-energy contraction
+//    (Theta . Yx, Eq. 5) and the half-step propagator (Phi + Phi (B_half - I)).
+//  * tc_taylor_kernel: per walker, the Taylor series of exp(V) applied to
+//    the orbitals (Sec. II, Thouless propagation by matrix products), with V
+//    held on-chip as the real 2M x 2M form [[Vr, -Vi], [Vi, Vr]] and each term
+//    t_n = V t_{n-1} / n fed back from TMEM into shared memory.
+//
+// TF32X3 mode splits each operand x into hi = x rounded to TF32 and
+// lo = x - hi (exact), and accumulates hi.hi + hi.lo + lo.hi.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "tc.h"
+#include "umma.cuh"
 
 namespace afqmc {
 
-struct TcPlan {};
+using namespace umma;
 
-cudaError_t tc_plan_create(TcPlan** out, const TcShape&, cudaStream_t, const float*,
-                           const float*, const float*, const float*, const float*) {
+struct TcCtx {
+  PFN_cuTensorMapEncodeTiled_v12000 encode;
+  int num_sms;
+};
+
+namespace {
+
+constexpr int BM = 128, BK = 32;
+
+// x rounded to the nearest TF32 value (10 explicit mantissa bits, ties to
+// even), so that x - tf32_hi(x) is exact in FP32 and at most 2^-11 |x|.
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t u = __float_as_uint(x);
+  u += 0x0FFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void flag_timeout(int* status) {
+  if (status) atomicOr(status, 4);
+}
+
+// ------------------------------------------------------------------ GEMM
+template <int BN, bool SPLIT3>
+struct GemmCfg {
+  static constexpr int STAGES = SPLIT3 ? (BN == 128 ? 3 : 4) : 4;
+  static constexpr int A_BYTES = BM * BK * 4;
+  static constexpr int B_BYTES = BN * BK * 4;
+  static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT3 ? 2 : 1);
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int BN, bool SPLIT3>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+               const __grid_constant__ CUtensorMap mapB, int m, int n, int ktiles_total,
+               int ktiles_per_split, float* __restrict__ C, long ldc, float alpha,
+               float beta, const float* __restrict__ R, long ldr, long split_stride,
+               int* status) {
+  using Cfg = GemmCfg<BN, SPLIT3>;
+  constexpr int S = Cfg::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  auto a_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES; };
+  auto b_hi = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
+  auto a_lo = [&](int s) { return base + s * Cfg::STAGE_BYTES + Cfg::A_BYTES + Cfg::B_BYTES; };
+  auto b_lo = [&](int s) {
+    return base + s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES + Cfg::B_BYTES;
+  };
+  uint64_t* bars = (uint64_t*)(base + S * Cfg::STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + S;
+  uint64_t* empty = bars + 2 * S;
+  uint64_t* done = bars + 3 * S;
+  uint32_t* tslot = (uint32_t*)(bars + 3 * S + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, z = blockIdx.z;
+  const int kt0 = z * ktiles_per_split;
+  const int nkt = max(0, min(ktiles_total, kt0 + ktiles_per_split) - kt0);
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&conv[s]), 128);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tslot), BN);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < nkt; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
+        if (i >= S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
+          flag_timeout(status);
+          s_fail = 1;
+          break;
+        }
+        mbar_arrive_expect_tx(smem_u32(&full[s]), Cfg::A_BYTES + Cfg::B_BYTES);
+        tma_load_2d(smem_u32(a_hi(s)), &mapA, (kt0 + i) * BK, m0, smem_u32(&full[s]));
+        tma_load_2d(smem_u32(b_hi(s)), &mapB, (kt0 + i) * BK, n0, smem_u32(&full[s]));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nkt > 0) {
+      const uint32_t id = idesc_tf32(BM, BN);
+      for (int i = 0; i < nkt; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
+        if (!mbar_wait(smem_u32(SPLIT3 ? &conv[s] : &full[s]), ph)) {
+          flag_timeout(status);
+          s_fail = 1;
+          break;
+        }
+        fence_after_sync();
+#pragma unroll
+        for (int ks = 0; ks < BK / 8; ++ks) {
+          const uint64_t ad = desc_sw128(smem_u32(a_hi(s)) + ks * 32);
+          const uint64_t bd = desc_sw128(smem_u32(b_hi(s)) + ks * 32);
+          mma_tf32(tmem, ad, bd, id, (i > 0 || ks > 0) ? 1u : 0u);
+          if (SPLIT3) {
+            mma_tf32(tmem, ad, desc_sw128(smem_u32(b_lo(s)) + ks * 32), id, 1u);
+            mma_tf32(tmem, desc_sw128(smem_u32(a_lo(s)) + ks * 32), bd, id, 1u);
+          }
+        }
+        mma_commit(smem_u32(&empty[s]));
+      }
+      mma_commit(smem_u32(done));
+    }
+  } else {
+    // warps 2..5: operand split (TF32X3), then the epilogue
+    const int t = threadIdx.x - 64;
+    if (SPLIT3) {
+      for (int i = 0; i < nkt; ++i) {
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
+        if (!mbar_wait(smem_u32(&full[s]), ph)) {
+          flag_timeout(status);
+          s_fail = 1;
+          break;
+        }
+        float4* ah = (float4*)a_hi(s);
+        float4* al = (float4*)a_lo(s);
+        for (int e = t; e < Cfg::A_BYTES / 16; e += 128) {
+          float4 x = ah[e], h, l;
+          h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
+          l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+          ah[e] = h;
+          al[e] = l;
+        }
+        float4* bh = (float4*)b_hi(s);
+        float4* bl = (float4*)b_lo(s);
+        for (int e = t; e < Cfg::B_BYTES / 16; e += 128) {
+          float4 x = bh[e], h, l;
+          h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
+          l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+          bh[e] = h;
+          bl[e] = l;
+        }
+        fence_proxy_async();
+        mbar_arrive(smem_u32(&conv[s]));
+      }
+    }
+    bool ok = true;
+    if (nkt > 0) {
+      ok = mbar_wait(smem_u32(done), 0);
+      if (!ok) flag_timeout(status);
+    }
+    fence_after_sync();
+    const int q = warp & 3;
+    const int row = m0 + 32 * q + lane;
+    float* crow = C + (long)z * split_stride + (long)row * ldc;
+    const float* rrow = R ? R + (long)row * ldr : nullptr;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      if (nkt > 0 && ok) {
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      }
+      if (row < m) {
+        const int cb = n0 + c0;
+        if (cb + 32 <= n && (ldc & 3) == 0 && (!rrow || (ldr & 3) == 0) &&
+            ((uintptr_t)(crow + cb) & 15) == 0 && (!rrow || ((uintptr_t)(rrow + cb) & 15) == 0)) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            float4 o;
+            o.x = alpha * v[j]; o.y = alpha * v[j + 1]; o.z = alpha * v[j + 2]; o.w = alpha * v[j + 3];
+            if (rrow) {
+              float4 r = *(const float4*)(rrow + cb + j);
+              o.x += beta * r.x; o.y += beta * r.y; o.z += beta * r.z; o.w += beta * r.w;
+            }
+            *(float4*)(crow + cb + j) = o;
+          }
+        } else {
+          for (int j = 0; j < 32; ++j) {
+            const int col = cb + j;
+            if (col < n) {
+              float o = alpha * v[j];
+              if (rrow) o += beta * rrow[col];
+              crow[col] = o;
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, BN);
+}
+
+// ------------------------------------------------------------------ Taylor
+// One CTA of 128 threads per (walker, 64-column chunk) work item, looping
+// over items. Thread r owns row r of the real 2M-row form (r < 64: real part
+// of orbital row r; r >= 64: imaginary part of row r - 64) and the matching
+// TMEM lane; it keeps the running sum of the series for its row in
+// registers.
+//
+// With a half-step image (FUSE_B), the symmetric Trotter factors are applied
+// on the tensor cores too: t0 = Phi + (B_half - I) Phi before the series and
+// out = s + (B_half - I) s after it, the identity part added exactly in FP32
+// and (B_half - I) in its real 2M-row form [[dB, 0], [0, dB]] bulk-copied
+// into the operand buffer from a pre-swizzled (and pre-split) image.
+constexpr int TY_A_BYTES = 128 * 128 * 4;     // [[Vr, -Vi], [Vi, Vr]], 4 K-blocks
+constexpr int TY_B_BYTES = 64 * 128 * 4;      // current term t, 64 columns
+template <bool SPLIT3>
+constexpr int taylor_smem() {
+  return (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1) + 1024 + 64;
+}
+
+// (B_half - I) as the operand image the Taylor kernel copies in: hi tile,
+// then (TF32X3) lo tile, each 128 x 128 fp32 in the K-major SW128 layout.
+__global__ void bhalf_image_kernel(int M, const float* __restrict__ dB, float* __restrict__ img,
+                                   int split3) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 128 * 128) return;
+  const int r = e / 128, k = e % 128;
+  const int rc = r >> 6, rr = r & 63, kc = k >> 6, kk = k & 63;
+  float x = 0.f;
+  if (rc == kc && rr < M && kk < M) x = dB[rr * M + kk];
+  const uint32_t off = sw128_offset(r, k, 128) / 4;
+  if (split3) {
+    const float h = tf32_hi(x);
+    img[off] = h;
+    img[128 * 128 + off] = x - h;
+  } else {
+    img[off] = x;
+  }
+}
+
+template <bool SPLIT3>
+__device__ __forceinline__ void put_operand(unsigned char* hi, unsigned char* lo, uint32_t off,
+                                            float x) {
+  if (SPLIT3) {
+    const float h = tf32_hi(x);
+    *(float*)(hi + off) = h;
+    *(float*)(lo + off) = x - h;
+  } else {
+    *(float*)(hi + off) = x;
+  }
+}
+
+template <bool SPLIT3>
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint32_t Alo,
+                                               uint32_t Bhi, uint32_t Blo, uint32_t id) {
+#pragma unroll
+  for (int ks = 0; ks < 16; ++ks) {
+    const int kb = ks >> 2, koff = (ks & 3) * 32;
+    const uint64_t ad = desc_sw128(Ahi + kb * 16384 + koff);
+    const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
+    mma_tf32(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
+    if (SPLIT3) {
+      mma_tf32(tmem, ad, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
+      mma_tf32(tmem, desc_sw128(Alo + kb * 16384 + koff), bd, id, 1u);
+    }
+  }
+}
+
+template <bool SPLIT3>
+__global__ void __launch_bounds__(128, 1)
+tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
+                 const float* __restrict__ Pin, float* __restrict__ Pout,
+                 const float* __restrict__ dB_img, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // A hi and lo are adjacent so one bulk copy fills both
+  unsigned char* Ahi = base;
+  unsigned char* Alo = base + TY_A_BYTES;
+  unsigned char* Bhi = base + TY_A_BYTES * (SPLIT3 ? 2 : 1);
+  unsigned char* Blo = Bhi + TY_B_BYTES;
+  uint64_t* bar = (uint64_t*)(base + (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1));
+  uint64_t* lbar = bar + 1;
+  uint32_t* tslot = (uint32_t*)(bar + 2);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int nchunk = (N + 63) / 64;
+  const int items = W * nchunk;
+  const bool fuse_b = dB_img != nullptr;
+  const uint32_t img_bytes = (uint32_t)TY_A_BYTES * (SPLIT3 ? 2u : 1u);
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(smem_u32(bar), 1);
+    mbar_init(smem_u32(lbar), 1);
+    mbar_fence_init();
+  }
+  // The V operand's padding (rows and K beyond M in each half) stays zero for
+  // every walker: the V build writes only the M x M blocks, and the half-step
+  // image is zero there too.
+  for (int e = tid; e < TY_A_BYTES / 4 * (SPLIT3 ? 2 : 1); e += 128) ((float*)Ahi)[e] = 0.f;
+  fence_proxy_async();
+  if (warp == 0) tmem_alloc(smem_u32(tslot), 64);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t id = idesc_tf32(128, 64);
+  uint32_t phase = 0, lphase = 0;
+  const int r = tid;                       // embedded row / K index owned
+  const int rc = r >> 6, rr = r & 63;      // component (0 re, 1 im), orbital row
+  const uint32_t sAhi = smem_u32(Ahi), sAlo = smem_u32(Alo);
+  const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+  const int MM = M * M;
+
+  // wait for the MMAs just issued; flags a timeout
+  auto wait_mma = [&]() {
+    const bool ok = mbar_wait(smem_u32(bar), phase);
+    phase ^= 1u;
+    if (!ok) {
+      flag_timeout(status);
+      s_fail = 1;
+    }
+    fence_after_sync();
+  };
+  auto sync_for_mma = [&]() {
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  };
+  auto load_bhalf = [&]() {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(smem_u32(lbar), img_bytes);
+      bulk_load(sAhi, dB_img, img_bytes, smem_u32(lbar));
+    }
+  };
+  auto wait_bhalf = [&]() {
+    if (!mbar_wait(smem_u32(lbar), lphase)) {
+      flag_timeout(status);
+      s_fail = 1;
+    }
+    lphase ^= 1u;
+  };
+
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int w = item / nchunk;
+    const int j0 = (item - w * nchunk) * 64;
+    const int nc = min(64, N - j0);
+    const float* Vw = V + (long)w * 2 * MM;
+    if (fuse_b) load_bhalf();
+    // ---- t0 = the chunk's columns; this thread's row of it seeds the sum
+    float acc[64];
+    const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
+#pragma unroll
+    for (int j = 0; j < 64; ++j)
+      acc[j] = (j < nc && rr < M) ? Pw[((long)j * 2 + rc) * M + rr] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) put_operand<SPLIT3>(Bhi, Blo, sw128_offset(j, r, 64), acc[j]);
+    if (fuse_b) {                          // t0 = Phi + dB Phi
+      wait_bhalf();
+      sync_for_mma();
+      if (tid == 0) {
+        issue_products<SPLIT3>(tmem, sAhi, sAlo, sBhi, sBlo, id);
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          acc[c0 + j] += v[j];
+          put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64), acc[c0 + j]);
+        }
+      }
+    }
+    // ---- A = [[Vr, -Vi], [Vi, Vr]]: each V element lands in two quadrants
+    for (int e0 = tid; e0 < 2 * MM; e0 += 128 * 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * 128;
+        v[u] = e < 2 * MM ? Vw[e] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * 128;
+        if (e >= 2 * MM) break;
+        const int plane = e >= MM;
+        const int rem = e - plane * MM;
+        const int i = rem / M, j = rem - i * M;
+        if (plane == 0) {          // Vr on both diagonal blocks
+          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(i, j, 128), v[u]);
+          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(64 + i, 64 + j, 128), v[u]);
+        } else {                   // Vi below, -Vi above the diagonal
+          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(64 + i, j, 128), v[u]);
+          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(i, 64 + j, 128), -v[u]);
+        }
+      }
+    }
+    for (int term = 1; term <= order; ++term) {
+      sync_for_mma();
+      if (tid == 0) {
+        issue_products<SPLIT3>(tmem, sAhi, sAlo, sBhi, sBlo, id);
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
+      const float inv = 1.0f / (float)term;
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float x = v[j] * inv;
+          acc[c0 + j] += x;
+          if (term < order || fuse_b)
+            put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64),
+                                term < order ? x : acc[c0 + j]);
+        }
+      }
+    }
+    if (fuse_b) {                          // out = s + dB s
+      fence_before_sync();
+      __syncthreads();
+      load_bhalf();
+      wait_bhalf();
+      sync_for_mma();
+      if (tid == 0) {
+        issue_products<SPLIT3>(tmem, sAhi, sAlo, sBhi, sBlo, id);
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[c0 + j] += v[j];
+      }
+    }
+    float* Ow = Pout + ((long)w * N + j0) * 2 * M;
+    if (rr < M) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j)
+        if (j < nc) Ow[((long)j * 2 + rc) * M + rr] = acc[j];
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (s_fail) break;
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
+}
+
+cudaError_t make_map(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, long k,
+                     long ld, int box_rows) {
+  if (((uintptr_t)ptr & 15) != 0 || (ld & 3) != 0 || k < 1 || rows < 1)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = t->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, bool SPLIT3>
+cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
+                        long lda, const float* B, long ldb, float* C, long ldc, float alpha,
+                        float beta, const float* R, long ldr, int ksplit, long split_stride,
+                        int* status) {
+  using Cfg = GemmCfg<BN, SPLIT3>;
+  static const cudaError_t attr = set_smem(tc_gemm_kernel<BN, SPLIT3>, Cfg::SMEM);
+  if (attr != cudaSuccess) return attr;
+  CUtensorMap ma, mb;
+  cudaError_t e = make_map(t, &ma, A, m, k, lda, BM);
+  if (e != cudaSuccess) return e;
+  e = make_map(t, &mb, B, n, k, ldb, BN);
+  if (e != cudaSuccess) return e;
+  const int kt = (k + BK - 1) / BK;
+  const int per = (kt + ksplit - 1) / ksplit;
+  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, ksplit);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  tc_gemm_kernel<BN, SPLIT3><<<grid, 192, Cfg::SMEM, st>>>(ma, mb, m, n, kt, per, C, ldc,
+                                                           alpha, beta, R, ldr,
+                                                           split_stride, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_create(TcCtx** out) {
   *out = nullptr;
-  return cudaErrorNotSupported;
+  TcCtx* t = new TcCtx();
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled",
+                                                   (void**)&t->encode, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !t->encode) {
+    delete t;
+    cudaGetLastError();
+    return e != cudaSuccess ? e : cudaErrorNotSupported;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  *out = t;
+  return cudaSuccess;
 }
-void tc_plan_destroy(TcPlan* p) { delete p; }
-cudaError_t tc_force_bias(TcPlan*, cudaStream_t, const float*, float*) {
-  return cudaErrorNotSupported;
+
+void tc_destroy(TcCtx* t) { delete t; }
+
+cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A, long lda,
+                    const float* B, long ldb, float* C, long ldc, float alpha, float beta,
+                    const float* R, long ldr, bool split3, int ksplit, long split_stride,
+                    int* status) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (ksplit < 1 || (ksplit > 1 && (R || beta != 0.f))) return cudaErrorInvalidValue;
+  if (n <= 64) {
+    return split3 ? launch_gemm<64, true>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
+                                          R, ldr, ksplit, split_stride, status)
+                  : launch_gemm<64, false>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha,
+                                           beta, R, ldr, ksplit, split_stride, status);
+  }
+  return split3 ? launch_gemm<128, true>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
+                                         R, ldr, ksplit, split_stride, status)
+                : launch_gemm<128, false>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
+                                          R, ldr, ksplit, split_stride, status);
 }
-cudaError_t tc_one_body(TcPlan*, cudaStream_t, const float*, float*) {
-  return cudaErrorNotSupported;
+
+cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
+                      const float* V, const float* Pin, float* Pout, const float* bhalf_img,
+                      bool split3, int* status) {
+  if (M > 64 || M < 1 || N < 1) return cudaErrorInvalidValue;
+  if (bhalf_img && ((uintptr_t)bhalf_img & 15)) return cudaErrorInvalidValue;
+  const int items = W * ((N + 63) / 64);
+  if (split3) {
+    static const cudaError_t attr = set_smem(tc_taylor_kernel<true>, taylor_smem<true>());
+    if (attr != cudaSuccess) return attr;
+    int grid = items < t->num_sms ? items : t->num_sms;
+    tc_taylor_kernel<true><<<grid, 128, taylor_smem<true>(), st>>>(W, M, N, order, V, Pin,
+                                                                  Pout, bhalf_img, status);
+  } else {
+    static const cudaError_t attr = set_smem(tc_taylor_kernel<false>, taylor_smem<false>());
+    if (attr != cudaSuccess) return attr;
+    int grid = items < 2 * t->num_sms ? items : 2 * t->num_sms;
+    tc_taylor_kernel<false><<<grid, 128, taylor_smem<false>(), st>>>(W, M, N, order, V, Pin,
+                                                                    Pout, bhalf_img, status);
+  }
+  return cudaGetLastError();
 }
-cudaError_t tc_propagate(TcPlan*, cudaStream_t, const float*, float*, float*, float*) {
-  return cudaErrorNotSupported;
-}
-cudaError_t tc_exchange(TcPlan*, cudaStream_t, int, const float*, float*) {
-  return cudaErrorNotSupported;
+
+size_t tc_bhalf_image_floats(bool split3) { return (size_t)128 * 128 * (split3 ? 2 : 1); }
+
+cudaError_t tc_bhalf_image(cudaStream_t st, int M, const float* dB, float* img, bool split3) {
+  if (M > 64) return cudaErrorInvalidValue;
+  bhalf_image_kernel<<<(128 * 128 + 255) / 256, 256, 0, st>>>(M, dB, img, split3 ? 1 : 0);
+  return cudaGetLastError();
 }
 
 }  // namespace afqmc

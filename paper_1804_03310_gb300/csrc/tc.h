@@ -1,26 +1,38 @@
-// Tensor-core (tcgen05) plan for the dense contractions of the TF32 modes.
+// Tensor-core (tcgen05 + TMA) kernels for the dense contractions of the
+// TF32 modes.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace afqmc {
 
-struct TcShape {
-  int W, M, n_up, n_dn, n_chol, taylor_order;
-  bool split;   // TF32x3: hi + lo operands
-};
+struct TcCtx;
 
-struct TcPlan;
+cudaError_t tc_create(TcCtx** out);
+void tc_destroy(TcCtx* t);
 
-cudaError_t tc_plan_create(TcPlan** out, const TcShape& s, cudaStream_t st,
-                           const float* L, const float* Ltil, const float* Bhalf,
-                           const float* Yx_up, const float* Yx_dn);
-void tc_plan_destroy(TcPlan* p);
-cudaError_t tc_force_bias(TcPlan* p, cudaStream_t st, const float* Theta, float* X);
-cudaError_t tc_one_body(TcPlan* p, cudaStream_t st, const float* S, float* V);
-cudaError_t tc_propagate(TcPlan* p, cudaStream_t st, const float* V, float* Phi,
-                         float* tmp1, float* tmp2);
-cudaError_t tc_exchange(TcPlan* p, cudaStream_t st, int spin, const float* Theta,
-                        float* Z);
+// C[m][n] (row stride ldc) = alpha * sum_k A[m][k] B[n][k] + beta * R[m][n].
+// A and B are row-major fp32 (K contiguous) with lda, ldb multiples of 4 and
+// 16-byte-aligned bases. split3: three TF32 products (hi*hi + hi*lo + lo*hi)
+// instead of one. ksplit > 1 splits K into that many ranges and writes
+// partial sums to C + s * split_stride (beta must then be 0). A device-side
+// wait that times out sets bit 4 of *status.
+cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
+                    long lda, const float* B, long ldb, float* C, long ldc, float alpha,
+                    float beta, const float* R, long ldr, bool split3, int ksplit,
+                    long split_stride, int* status);
+
+// Taylor propagation of W walkers (M <= 64): Pout = sum_{n<=order} V^n Pin / n!
+// with V [W][2][M][M] and Pin, Pout [W][N][2][M], on the tensor cores. With a
+// half-step image (see tc_bhalf_image) the two half-step factors are applied
+// around the series: Pout = B_half exp_T(V) B_half Pin.
+cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
+                      const float* V, const float* Pin, float* Pout, const float* bhalf_img,
+                      bool split3, int* status);
+
+// Operand image of (B_half - I) (M x M, row-major fp32 in dB) for tc_taylor:
+// tc_bhalf_image_floats(split3) floats, 16-byte aligned.
+size_t tc_bhalf_image_floats(bool split3);
+cudaError_t tc_bhalf_image(cudaStream_t st, int M, const float* dB, float* img, bool split3);
 
 }  // namespace afqmc

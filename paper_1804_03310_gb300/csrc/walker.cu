@@ -45,52 +45,77 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 
 // --------------------------------------------------------------- K1 + K3
+// Arithmetic type of the field draw: FP64 on the FP64 path, FP32 on the
+// reduced paths (the Philox words are the same; only the transform's
+// precision differs). The per-walker sum of the importance exponent is
+// reduced across the block in FP64.
 template <typename T>
-__global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx,
-                              double sqdt, double cap, uint32_t k0, uint32_t k1,
-                              int run_id, uint32_t step, T* __restrict__ S,
-                              T* __restrict__ xbar, double2* __restrict__ lw) {
+struct FieldMath { using type = float; };
+template <>
+struct FieldMath<double> { using type = double; };
+
+template <typename T>
+__global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int nsplit,
+                              long split_stride, double sqdt_d, double cap_d, uint32_t k0,
+                              uint32_t k1, int run_id, uint32_t step, T* __restrict__ S,
+                              long ldS, T* __restrict__ xbar, double2* __restrict__ lw) {
+  using C = typename FieldMath<T>::type;
   __shared__ double red[32];
   const int w = blockIdx.x;
   const T* Xr = X + (2L * w) * ldx;
   const T* Xi = Xr + ldx;
-  T* Sr = S + (2L * w) * n_chol;
-  T* Si = Sr + n_chol;
+  T* Sr = S + (2L * w) * ldS;
+  T* Si = Sr + ldS;
   T* Br = xbar + (2L * w) * n_chol;
   T* Bi = Br + n_chol;
-  double lre = 0.0, lim = 0.0;
+  const C sqdt = (C)sqdt_d, cap = (C)cap_d;
+  C lre = 0, lim = 0;
   const int nq = (n_chol + 3) >> 2;
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     U4 c = {(uint32_t)q, (uint32_t)w, step, (uint32_t)(4 * run_id + kStreamFields)};
     U4 r = philox4x32_10(c, k0, k1);
-    double z[4];
-    box_muller(r.x, r.y, z[0], z[1]);
-    box_muller(r.z, r.w, z[2], z[3]);
+    C z[4];
+    if (sizeof(C) == 8) {
+      double a0, a1, a2, a3;
+      box_muller(r.x, r.y, a0, a1);
+      box_muller(r.z, r.w, a2, a3);
+      z[0] = (C)a0; z[1] = (C)a1; z[2] = (C)a2; z[3] = (C)a3;
+    } else {
+      float a0, a1, a2, a3;
+      box_muller_f(r.x, r.y, a0, a1);
+      box_muller_f(r.z, r.w, a2, a3);
+      z[0] = (C)a0; z[1] = (C)a1; z[2] = (C)a2; z[3] = (C)a3;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int g = 4 * q + j;
+      const int g = 4 * q + j;
       if (g >= n_chol) break;
-      // xbar = -i sqrt(dt) X
-      double br = sqdt * (double)Xi[g];
-      double bi = -sqdt * (double)Xr[g];
-      if (!isfinite(br) || !isfinite(bi)) { br = 0.0; bi = 0.0; }
-      if (cap > 0.0) {
-        double a = sqrt(br * br + bi * bi);
-        if (a > cap) { double f = cap / a; br *= f; bi *= f; }
+      C xr = 0, xi = 0;   // X summed over the K-split partials, in order
+      for (int sp = 0; sp < nsplit; ++sp) {
+        xr += (C)Xr[sp * split_stride + g];
+        xi += (C)Xi[sp * split_stride + g];
       }
-      double x = z[j];
-      double sr = x - br, si = -bi;          // s = x - xbar
+      // xbar = -i sqrt(dt) X
+      C br = sqdt * xi;
+      C bi = -sqdt * xr;
+      if (!isfinite(br) || !isfinite(bi)) { br = 0; bi = 0; }
+      if (cap > 0) {
+        const C a = sqrt(br * br + bi * bi);
+        if (a > cap) { const C f = cap / a; br *= f; bi *= f; }
+      }
+      const C x = z[j];
+      const C sr = x - br, si = -bi;          // s = x - xbar
       Sr[g] = (T)(-sqdt * si);               // i sqrt(dt) s
       Si[g] = (T)(sqdt * sr);
       Br[g] = (T)br;
       Bi[g] = (T)bi;
-      lre += x * br - 0.5 * (br * br - bi * bi);
+      lre += x * br - C(0.5) * (br * br - bi * bi);
       lim += x * bi - br * bi;
     }
   }
-  lre = block_sum(lre, red);
-  lim = block_sum(lim, red);
-  if (threadIdx.x == 0) lw[w] = make_double2(lre, lim);
+  const double tre = block_sum((double)lre, red);
+  const double tim = block_sum((double)lim, red);
+  if (threadIdx.x == 0) lw[w] = make_double2(tre, tim);
 }
 
 // --------------------------------------------------------------- K5 (SIMT)
@@ -207,14 +232,28 @@ __device__ __forceinline__ cx<R> div_c(cx<R> a, cx<R> b) {
   return mk<R>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// One block per (walker, spin). A = D^T Phi (real trial orbitals) is formed
-// and inverted by Gauss-Jordan elimination with partial pivoting in the
-// compute type R; the log-determinant (sum of the pivots' logarithms plus
-// i pi per row swap) is accumulated in FP64 in every precision.
+template <typename R>
+__device__ __forceinline__ cx<R> mul_c(cx<R> a, cx<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Row stride (in complex values) of a walker block staged as [column][row]:
+// odd, so that lanes reading the same row of consecutive columns hit
+// distinct banks.
+__host__ __device__ __forceinline__ int staged_ld(int M) { return M | 1; }
+
+// One block per (walker, spin), with the walker's columns of that spin
+// staged in shared memory as Q[b][k] (orbital column b, basis row k).
+//  1. A = D^T Phi (real trial orbitals), ns x ns.
+//  2. LU with partial pivoting, P A = L U, in the compute type R; the
+//     log-determinant sum_k ln U_kk (+ i pi per odd row-swap count) is
+//     accumulated in FP64.
+//  3. Theta = Phi A^-1 = Phi U^-1 L^-1 P row by row: thread k solves
+//     z U = phi_k, then y L = z, and scatters theta_k[perm[i]] = y_i.
 template <typename T, typename R>
 __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
                                const T* __restrict__ PsiT, T* __restrict__ Theta,
-                               double2* __restrict__ logdet,
+                               long ldt, long dn_off, double2* __restrict__ logdet,
                                double2* __restrict__ Ainv_out, int nmax) {
   extern __shared__ unsigned char smem_raw[];
   const int w = blockIdx.x, sig = blockIdx.y;
@@ -226,43 +265,45 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     if (tid == 0) logdet[2 * w + sig] = make_double2(0.0, 0.0);
     return;
   }
-  cx<R>* aug = reinterpret_cast<cx<R>*>(smem_raw);   // [ns][2 ns]
-  cx<R>* fac = aug + (long)ns * 2 * ns;               // [ns]
-  __shared__ int piv;
-  __shared__ int singular;
-  __shared__ double2 ld;
-  __shared__ int nswap;
-  const int ld2 = 2 * ns;
-  const T* Pw = Phi + (long)w * N * 2 * M;
+  const int ldq = staged_ld(M);
+  cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);      // [ns][ldq]
+  cx<R>* A = Q + (long)ns * ldq;                      // [ns][ns], L and U in place
+  int* perm = reinterpret_cast<int*>(A + (long)ns * ns);
+  __shared__ int piv, singular, nswap;
+  const T* Pw = Phi + ((long)w * N + j0) * 2 * M;
+  for (int e = tid; e < ns * M; e += nt) {
+    const int b = e / M, k = e - b * M;
+    Q[b * ldq + k] = mk<R>((R)Pw[(long)b * 2 * M + k], (R)Pw[(long)b * 2 * M + M + k]);
+  }
+  if (tid == 0) { nswap = 0; singular = 0; }
+  for (int i = tid; i < ns; i += nt) perm[i] = i;
+  __syncthreads();
   for (int e = tid; e < ns * ns; e += nt) {
-    int a = e / ns, b = e - a * ns;
+    const int a = e / ns, b = e - a * ns;
     const T* d = PsiT + (long)(j0 + a) * M;
-    const T* pr = Pw + ((long)(j0 + b) * 2 + 0) * M;
-    const T* pi = pr + M;
     R sr = 0, si = 0;
     for (int k = 0; k < M; ++k) {
-      R dk = (R)d[k];
-      sr = fma(dk, (R)pr[k], sr);
-      si = fma(dk, (R)pi[k], si);
+      const R dk = (R)d[k];
+      const cx<R> q = Q[b * ldq + k];
+      sr = fma(dk, q.x, sr);
+      si = fma(dk, q.y, si);
     }
-    aug[a * ld2 + b] = mk<R>(sr, si);
-    aug[a * ld2 + ns + b] = mk<R>(a == b ? R(1) : R(0), R(0));
+    A[a * ns + b] = mk<R>(sr, si);
   }
-  if (tid == 0) { ld = make_double2(0.0, 0.0); nswap = 0; singular = 0; }
   __syncthreads();
   for (int k = 0; k < ns; ++k) {
     if (tid < 32) {
       R best = R(-1);
       int bi = k;
       for (int i = k + tid; i < ns; i += 32) {
-        cx<R> v = aug[i * ld2 + k];
-        R m = v.x * v.x + v.y * v.y;
+        const cx<R> v = A[i * ns + k];
+        const R m = v.x * v.x + v.y * v.y;
         if (m > best) { best = m; bi = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
@@ -274,63 +315,94 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     if (singular) break;
     const int p = piv;
     if (p != k) {
-      for (int c = tid; c < ld2; c += nt) {
-        cx<R> t = aug[k * ld2 + c];
-        aug[k * ld2 + c] = aug[p * ld2 + c];
-        aug[p * ld2 + c] = t;
+      for (int c = tid; c < ns; c += nt) {
+        const cx<R> t = A[k * ns + c];
+        A[k * ns + c] = A[p * ns + c];
+        A[p * ns + c] = t;
       }
-      if (tid == 0) nswap ^= 1;
+      if (tid == 0) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+        nswap ^= 1;
+      }
+      __syncthreads();
     }
+    const cx<R> pv = A[k * ns + k];
+    for (int i = k + 1 + tid; i < ns; i += nt) A[i * ns + k] = div_c(A[i * ns + k], pv);
     __syncthreads();
-    const cx<R> pv = aug[k * ld2 + k];
-    if (tid == 0) {
-      double px = (double)pv.x, py = (double)pv.y;
-      ld.x += 0.5 * log(px * px + py * py);
-      ld.y += atan2(py, px);
-    }
-    __syncthreads();
-    for (int c = tid; c < ld2; c += nt) aug[k * ld2 + c] = div_c(aug[k * ld2 + c], pv);
-    for (int i = tid; i < ns; i += nt) fac[i] = (i == k) ? mk<R>(R(0), R(0)) : aug[i * ld2 + k];
-    __syncthreads();
-    for (int e = tid; e < ns * ld2; e += nt) {
-      int i = e / ld2, c = e - i * ld2;
-      if (i == k) continue;
-      aug[e] = sub_mul(aug[e], fac[i], aug[k * ld2 + c]);
+    const int rem = ns - k - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      A[i * ns + j] = sub_mul(A[i * ns + j], A[i * ns + k], A[k * ns + j]);
     }
     __syncthreads();
   }
   const int sing = singular;
-  if (tid == 0) {
-    double2 out = ld;
-    if (sing) out = make_double2(-INFINITY, 0.0);
-    else if (nswap) out.y += 3.141592653589793;
-    logdet[2 * w + sig] = out;
-  }
-  if (Ainv_out) {
-    double2* Ao = Ainv_out + ((long)w * 2 + sig) * nmax * nmax;
-    for (int e = tid; e < ns * ns; e += nt) {
-      int a = e / ns, b = e - a * ns;
-      cx<R> v = aug[a * ld2 + ns + b];
-      Ao[a * nmax + b] = sing ? make_double2(0.0, 0.0) : make_double2((double)v.x, (double)v.y);
-    }
-  }
-  // Theta[:, a] = sum_b Phi[:, b] Ainv[b][a]
-  T* Tr = Theta + ((long)w * 2 + 0) * N * M + (long)j0 * M;
-  T* Ti = Theta + ((long)w * 2 + 1) * N * M + (long)j0 * M;
-  for (int e = tid; e < M * ns; e += nt) {
-    int a = e / M, k = e - a * M;
-    R sr = 0, si = 0;
+  if (tid < 32) {
+    double lre = 0.0, lim = 0.0;
     if (!sing) {
-      for (int b = 0; b < ns; ++b) {
-        const T* pr = Pw + ((long)(j0 + b) * 2 + 0) * M;
-        R xr = (R)pr[k], xi = (R)pr[M + k];
-        cx<R> iv = aug[b * ld2 + ns + a];
-        sr += xr * iv.x - xi * iv.y;
-        si += xr * iv.y + xi * iv.x;
+      for (int k = tid; k < ns; k += 32) {
+        const double px = (double)A[k * ns + k].x, py = (double)A[k * ns + k].y;
+        lre += 0.5 * log(px * px + py * py);
+        lim += atan2(py, px);
       }
     }
-    Tr[(long)a * M + k] = (T)sr;
-    Ti[(long)a * M + k] = (T)si;
+    lre = warp_sum(lre);
+    lim = warp_sum(lim);
+    if (tid == 0) {
+      double2 out = make_double2(lre, lim);
+      if (sing) out = make_double2(-INFINITY, 0.0);
+      else if (nswap) out.y += 3.141592653589793;
+      logdet[2 * w + sig] = out;
+    }
+  }
+  T* Tr = Theta + ((long)w * 2 + 0) * ldt + (sig ? dn_off : 0);
+  T* Ti = Theta + ((long)w * 2 + 1) * ldt + (sig ? dn_off : 0);
+  for (int k = tid; k < M; k += nt) {
+    if (sing) {
+      for (int a = 0; a < ns; ++a) {
+        Tr[(long)a * M + k] = T(0);
+        Ti[(long)a * M + k] = T(0);
+      }
+      continue;
+    }
+    for (int j = 0; j < ns; ++j) {              // z U = phi_k
+      cx<R> s = Q[j * ldq + k];
+      for (int i = 0; i < j; ++i) s = sub_mul(s, Q[i * ldq + k], A[i * ns + j]);
+      Q[j * ldq + k] = div_c(s, A[j * ns + j]);
+    }
+    for (int j = ns - 2; j >= 0; --j) {         // y L = z (unit lower L)
+      cx<R> s = Q[j * ldq + k];
+      for (int i = j + 1; i < ns; ++i) s = sub_mul(s, Q[i * ldq + k], A[i * ns + j]);
+      Q[j * ldq + k] = s;
+    }
+    for (int i = 0; i < ns; ++i) {              // theta_k[perm[i]] = y_i
+      const cx<R> y = Q[i * ldq + k];
+      Tr[(long)perm[i] * M + k] = (T)y.x;
+      Ti[(long)perm[i] * M + k] = (T)y.y;
+    }
+  }
+  if (Ainv_out) {                               // rows of A^-1 = e_r U^-1 L^-1 P
+    __syncthreads();
+    double2* Ao = Ainv_out + ((long)w * 2 + sig) * nmax * nmax;
+    cx<R>* rowbuf = Q;                          // reuse: [ns][ldq] as [i][r]
+    for (int r = tid; r < ns; r += nt) {
+      for (int j = 0; j < ns; ++j) {
+        cx<R> s = mk<R>(j == r ? R(1) : R(0), R(0));
+        for (int i = 0; i < j; ++i) s = sub_mul(s, rowbuf[i * ldq + r], A[i * ns + j]);
+        rowbuf[j * ldq + r] = sing ? mk<R>(R(0), R(0)) : div_c(s, A[j * ns + j]);
+      }
+      for (int j = ns - 2; j >= 0; --j) {
+        cx<R> s = rowbuf[j * ldq + r];
+        for (int i = j + 1; i < ns; ++i) s = sub_mul(s, rowbuf[i * ldq + r], A[i * ns + j]);
+        rowbuf[j * ldq + r] = s;
+      }
+      for (int i = 0; i < ns; ++i) {
+        const cx<R> y = rowbuf[i * ldq + r];
+        Ao[(long)r * nmax + perm[i]] = make_double2((double)y.x, (double)y.y);
+      }
+    }
   }
 }
 
@@ -363,113 +435,139 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
 }
 
 // --------------------------------------------------------------- K10
-// Modified Gram-Schmidt per walker (both spins in turn), right-looking: once
-// column j is normalised it is projected out of every later column, one warp
-// per column. Arithmetic in R; ln det R = sum_j ln r_jj accumulated in FP64.
+// QR of each walker's spin block, Phi = Q R with R upper triangular and its
+// diagonal real and positive (the factorisation modified Gram-Schmidt
+// produces), computed through the Gram matrix: S = Phi^H Phi = R^H R
+// (Cholesky), then Q = Phi R^-1 row by row. The walkers are re-orthonormalised
+// every few steps, so S stays close to the identity and the Cholesky route is
+// as accurate as Gram-Schmidt. One block per (walker, spin); ln det R =
+// sum_j ln R_jj is accumulated in FP64 into lr[w][spin].
 template <typename T, typename R>
-__global__ void mgs_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
-                           double2* __restrict__ logO) {
+__global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
+                          double* __restrict__ lr) {
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);    // [ns][M]
-  __shared__ R rjj;
-  const int w = blockIdx.x;
+  const int w = blockIdx.x, sig = blockIdx.y;
   const int N = n_up + n_dn;
+  const int ns = sig ? n_dn : n_up;
+  const int j0 = sig ? n_up : 0;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  double logr = 0.0;
-  for (int sig = 0; sig < 2; ++sig) {
-    const int ns = sig ? n_dn : n_up;
-    const int j0 = sig ? n_up : 0;
-    if (ns == 0) continue;
-    T* Pw = Phi + ((long)w * N + j0) * 2 * M;
+  if (ns == 0) {
+    if (tid == 0) lr[2 * w + sig] = 0.0;
+    return;
+  }
+  const int ldq = staged_ld(M);
+  cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);      // [ns][ldq]
+  cx<R>* S = Q + (long)ns * ldq;                      // [ns][ns], R in the upper part
+  T* Pw = Phi + ((long)w * N + j0) * 2 * M;
+  for (int e = tid; e < ns * M; e += nt) {
+    const int b = e / M, k = e - b * M;
+    Q[b * ldq + k] = mk<R>((R)Pw[(long)b * 2 * M + k], (R)Pw[(long)b * 2 * M + M + k]);
+  }
+  __syncthreads();
+  for (int e = tid; e < ns * ns; e += nt) {           // S_ab = q_a^H q_b, a <= b
+    const int a = e / ns, b = e - a * ns;
+    if (a > b) continue;
+    R sr = 0, si = 0;
+    for (int k = 0; k < M; ++k) {
+      const cx<R> x = Q[a * ldq + k], y = Q[b * ldq + k];
+      sr += x.x * y.x + x.y * y.y;
+      si += x.x * y.y - x.y * y.x;
+    }
+    S[a * ns + b] = mk<R>(sr, si);
+  }
+  __syncthreads();
+  for (int j = 0; j < ns; ++j) {                      // right-looking Cholesky
+    const R d = sqrt(S[j * ns + j].x);
     __syncthreads();
-    for (int e = tid; e < ns * M; e += nt) {
-      int b = e / M, k = e - b * M;
-      Q[e] = mk<R>((R)Pw[(b * 2 + 0) * M + k], (R)Pw[(b * 2 + 1) * M + k]);
+    for (int c = j + tid; c < ns; c += nt) {
+      const cx<R> v = S[j * ns + c];
+      S[j * ns + c] = (c == j) ? mk<R>(d, R(0)) : mk<R>(v.x / d, v.y / d);
     }
     __syncthreads();
+    const int rem = ns - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int a = j + 1 + e / rem, c = j + 1 + e % rem;
+      if (c < a) continue;
+      const cx<R> x = S[j * ns + a], y = S[j * ns + c];   // S_ac -= conj(R_ja) R_jc
+      S[a * ns + c] = mk<R>(S[a * ns + c].x - (x.x * y.x + x.y * y.y),
+                            S[a * ns + c].y - (x.x * y.y - x.y * y.x));
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < M; k += nt) {                 // q_k R = phi_k
     for (int j = 0; j < ns; ++j) {
-      if (wid == 0) {
-        R s = 0;
-        for (int k = lane; k < M; k += 32) {
-          cx<R> q = Q[j * M + k];
-          s += q.x * q.x + q.y * q.y;
-        }
-        s = warp_sum(s);
-        if (lane == 0) rjj = sqrt(s);
-      }
-      __syncthreads();
-      const R r = rjj;
-      if (tid == 0) logr += log((double)r);
-      for (int k = tid; k < M; k += nt) {
-        cx<R> q = Q[j * M + k];
-        Q[j * M + k] = mk<R>(q.x / r, q.y / r);
-      }
-      __syncthreads();
-      for (int c = j + 1 + wid; c < ns; c += nw) {
-        R sr = 0, si = 0;   // r_jc = q_j^H a_c
-        for (int k = lane; k < M; k += 32) {
-          cx<R> q = Q[j * M + k], a = Q[c * M + k];
-          sr += q.x * a.x + q.y * a.y;
-          si += q.x * a.y - q.y * a.x;
-        }
-        sr = warp_sum(sr);
-        si = warp_sum(si);
-        for (int k = lane; k < M; k += 32) {
-          cx<R> q = Q[j * M + k], a = Q[c * M + k];
-          Q[c * M + k] = mk<R>(a.x - (sr * q.x - si * q.y), a.y - (sr * q.y + si * q.x));
-        }
-      }
-      __syncthreads();
+      cx<R> s = Q[j * ldq + k];
+      for (int i = 0; i < j; ++i) s = sub_mul(s, Q[i * ldq + k], S[i * ns + j]);
+      const R d = S[j * ns + j].x;
+      Q[j * ldq + k] = mk<R>(s.x / d, s.y / d);
     }
-    for (int e = tid; e < ns * M; e += nt) {
-      int b = e / M, k = e - b * M;
-      Pw[(b * 2 + 0) * M + k] = (T)Q[e].x;
-      Pw[(b * 2 + 1) * M + k] = (T)Q[e].y;
+    for (int j = 0; j < ns; ++j) {
+      const cx<R> q = Q[j * ldq + k];
+      Pw[(long)j * 2 * M + k] = (T)q.x;
+      Pw[(long)j * 2 * M + M + k] = (T)q.y;
     }
   }
-  if (tid == 0) logO[w].x -= logr;
+  if (tid < 32) {
+    double l = 0.0;
+    for (int j = tid; j < ns; j += 32) l += log((double)S[j * ns + j].x);
+    l = warp_sum(l);
+    if (tid == 0) lr[2 * w + sig] = l;
+  }
+}
+
+__global__ void sub_logdet_r_kernel(int W, const double* __restrict__ lr,
+                                    double2* __restrict__ logO) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < W) logO[w].x -= lr[2 * w] + lr[2 * w + 1];
 }
 
 // --------------------------------------------------------------- K9 epilogue
 template <typename T>
 __global__ void energy_reduce_kernel(int M, int n_up, int n_dn, int n_chol,
-                                     const T* __restrict__ X, long ldx,
-                                     const T* __restrict__ Theta,
-                                     const T* __restrict__ Z, int W,
+                                     const T* __restrict__ X, long ldx, int nsplit,
+                                     long split_stride, const T* __restrict__ Theta,
+                                     long ldt, long dn_off, const T* __restrict__ Z,
+                                     long ldz_up, long ldz_dn, int W,
                                      double2* __restrict__ eloc) {
   __shared__ double red[32];
   const int w = blockIdx.x;
-  const int N = n_up + n_dn;
   const T* Xr = X + (2L * w) * ldx;
   const T* Xi = Xr + ldx;
   double cr = 0.0, ci = 0.0;
-  for (int g = threadIdx.x; g < n_chol; g += blockDim.x) {
-    double a = Xr[g], b = Xi[g];
-    cr += 0.5 * (a * a - b * b);
-    ci += a * b;
+  for (int g = threadIdx.x; g <= n_chol; g += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) {
+      a += (double)Xr[sp * split_stride + g];
+      b += (double)Xi[sp * split_stride + g];
+    }
+    if (g == n_chol) {          // the one-body column tr(h~ Theta)
+      cr += a;
+      ci += b;
+    } else {
+      cr += 0.5 * (a * a - b * b);
+      ci += a * b;
+    }
   }
   double er = 0.0, ei = 0.0;
   long zoff = 0;
   for (int sig = 0; sig < 2; ++sig) {
     const int ns = sig ? n_dn : n_up;
-    const int j0 = sig ? n_up : 0;
     const long J = (long)ns * M;
-    const T* tr = Theta + (2L * w) * N * M + (long)j0 * M;
-    const T* ti = tr + (long)N * M;
-    const T* zr = Z + zoff + (2L * w) * J;
-    const T* zi = zr + J;
+    const long ldz = sig ? ldz_dn : ldz_up;
+    const T* tr = Theta + (2L * w) * ldt + (sig ? dn_off : 0);
+    const T* ti = tr + ldt;
+    const T* zr = Z + zoff + (2L * w) * ldz;
+    const T* zi = zr + ldz;
     for (long e = threadIdx.x; e < J; e += blockDim.x) {
       double a = tr[e], b = ti[e], p = zr[e], q = zi[e];
       er += 0.5 * (a * p - b * q);
       ei += 0.5 * (a * q + b * p);
     }
-    zoff += 2L * W * J;
+    zoff += 2L * W * ldz;
   }
   double tr_ = block_sum(cr + er, red);
   double ti_ = block_sum(ci + ei, red);
-  if (threadIdx.x == 0)
-    eloc[w] = make_double2(tr_ + (double)Xr[n_chol], ti_ + (double)Xi[n_chol]);
+  if (threadIdx.x == 0) eloc[w] = make_double2(tr_, ti_);
 }
 
 __global__ void mixed_energy_kernel(int W, const double* __restrict__ weight,
@@ -606,7 +704,7 @@ __global__ void scale_identity_kernel(int M, const double* __restrict__ A, doubl
 }
 
 __global__ void yx_permute_kernel(int n, int M, const double* __restrict__ gram,
-                                  double* __restrict__ yx) {
+                                  double* __restrict__ yx, long ldy) {
   // Yx[(a,k)][(b,l)] = -Gram[(b,k)][(a,l)],  J = n * M
   long J = (long)n * M;
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -614,7 +712,26 @@ __global__ void yx_permute_kernel(int n, int M, const double* __restrict__ gram,
   long row = e / J, col = e - row * J;
   int a = (int)(row / M), k = (int)(row - (long)a * M);
   int b = (int)(col / M), l = (int)(col - (long)b * M);
-  yx[e] = -gram[((long)b * M + k) * J + (long)a * M + l];
+  yx[row * ldy + col] = -gram[((long)b * M + k) * J + (long)a * M + l];
+}
+
+// Rows of [rows][Jup + Jdn] into [rows][ld] with the down block at dn_off.
+__global__ void pad_rows_kernel(long rows, long Jup, long Jdn, const double* __restrict__ in,
+                                double* __restrict__ out, long ld, long dn_off) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long J = Jup + Jdn;
+  if (e >= rows * J) return;
+  long r = e / J, c = e - r * J;
+  out[r * ld + (c < Jup ? c : dn_off + (c - Jup))] = in[e];
+}
+
+// out[i][j] = in[j][i] for an rows x cols matrix, into leading dimension ldo.
+__global__ void transpose_kernel(long rows, long cols, const double* __restrict__ in,
+                                 double* __restrict__ out, long ldo) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  long r = e / cols, c = e - r * cols;
+  out[c * ldo + r] = in[e];
 }
 
 template <typename T>
@@ -636,6 +753,11 @@ __global__ void init_walkers_kernel(int M, int N, const T* __restrict__ PsiT,
   if (threadIdx.x == 0) weight[w] = 1.0;
 }
 
+__global__ void add_diag_kernel(int M, double* __restrict__ A, double a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) A[(long)i * M + i] += a;
+}
+
 __global__ void axpy_d_kernel(long n, double a, const double* __restrict__ x,
                               double* __restrict__ y) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -649,11 +771,12 @@ inline unsigned blocks_for(long n, int t) { return (unsigned)((n + t - 1) / t); 
 // =============================================================== launchers
 template <typename T>
 cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
-                          double sqdt, double cap, uint64_t seed, int run_id,
-                          long step, T* S, T* xbar, double2* lw) {
-  fields_kernel<T><<<W, 128, 0, st>>>(n_chol, X, ldx, sqdt, cap, (uint32_t)seed,
-                                      (uint32_t)(seed >> 32), run_id, (uint32_t)step,
-                                      S, xbar, lw);
+                          int nsplit, long split_stride, double sqdt, double cap,
+                          uint64_t seed, int run_id, long step, T* S, long ldS, T* xbar,
+                          double2* lw) {
+  fields_kernel<T><<<W, 128, 0, st>>>(n_chol, X, ldx, nsplit, split_stride, sqdt, cap,
+                                      (uint32_t)seed, (uint32_t)(seed >> 32), run_id,
+                                      (uint32_t)step, S, ldS, xbar, lw);
   return cudaGetLastError();
 }
 
@@ -672,24 +795,29 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
   return cudaGetLastError();
 }
 
+size_t overlap_smem(int M, int nmax, size_t csize) {
+  return csize * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax) + sizeof(int) * nmax;
+}
+
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
-                           const T* Phi, const T* PsiT, T* Theta, double2* logdet,
-                           double2* Ainv, bool fp64_compute) {
-  int nmax = n_up > n_dn ? n_up : n_dn;
+                           const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
+                           double2* logdet, double2* Ainv, bool fp64_compute) {
+  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int threads = M > 96 ? 256 : 128;
   dim3 grid(W, 2);
   if (fp64_compute) {
     static const size_t cap = allow_big_smem(overlap_kernel<T, double>);
-    size_t smem = sizeof(double2) * ((size_t)nmax * 2 * nmax + nmax);
+    const size_t smem = overlap_smem(M, nmax, sizeof(double2));
     if (smem > cap) return cudaErrorInvalidValue;
-    overlap_kernel<T, double><<<grid, 256, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                      logdet, Ainv, nmax);
+    overlap_kernel<T, double><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
+                                                          ldt, dn_off, logdet, Ainv, nmax);
   } else {
     static const size_t cap = allow_big_smem(overlap_kernel<T, float>);
-    size_t smem = sizeof(float2) * ((size_t)nmax * 2 * nmax + nmax);
+    const size_t smem = overlap_smem(M, nmax, sizeof(float2));
     if (smem > cap) return cudaErrorInvalidValue;
-    overlap_kernel<T, float><<<grid, 256, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                     logdet, Ainv, nmax);
+    overlap_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
+                                                         ldt, dn_off, logdet, Ainv, nmax);
   }
   return cudaGetLastError();
 }
@@ -709,29 +837,36 @@ cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
 }
 
 template <typename T>
-cudaError_t launch_mgs(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
-                       double2* logO, bool fp64_compute) {
-  int nmax = n_up > n_dn ? n_up : n_dn;
+cudaError_t launch_qr(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
+                      double2* logO, double* lr, bool fp64_compute) {
+  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int threads = M > 96 ? 256 : 128;
+  dim3 grid(W, 2);
   if (fp64_compute) {
-    static const size_t cap = allow_big_smem(mgs_kernel<T, double>);
-    size_t smem = sizeof(double2) * (size_t)nmax * M;
+    static const size_t cap = allow_big_smem(qr_kernel<T, double>);
+    const size_t smem = sizeof(double2) * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
     if (smem > cap) return cudaErrorInvalidValue;
-    mgs_kernel<T, double><<<W, 256, smem, st>>>(M, n_up, n_dn, Phi, logO);
+    qr_kernel<T, double><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   } else {
-    static const size_t cap = allow_big_smem(mgs_kernel<T, float>);
-    size_t smem = sizeof(float2) * (size_t)nmax * M;
+    static const size_t cap = allow_big_smem(qr_kernel<T, float>);
+    const size_t smem = sizeof(float2) * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
     if (smem > cap) return cudaErrorInvalidValue;
-    mgs_kernel<T, float><<<W, 256, smem, st>>>(M, n_up, n_dn, Phi, logO);
+    qr_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sub_logdet_r_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, lr, logO);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_energy_reduce(cudaStream_t st, int W, int M, int n_up, int n_dn,
-                                 int n_chol, const T* X, long ldx, const T* Theta,
-                                 const T* Z, double2* eloc) {
-  energy_reduce_kernel<T><<<W, 256, 0, st>>>(M, n_up, n_dn, n_chol, X, ldx, Theta, Z,
-                                             W, eloc);
+                                 int n_chol, const T* X, long ldx, int nsplit,
+                                 long split_stride, const T* Theta, long ldt, long dn_off,
+                                 const T* Z, long ldz_up, long ldz_dn, double2* eloc) {
+  energy_reduce_kernel<T><<<W, 256, 0, st>>>(M, n_up, n_dn, n_chol, X, ldx, nsplit,
+                                             split_stride, Theta, ldt, dn_off, Z, ldz_up,
+                                             ldz_dn, W, eloc);
   return cudaGetLastError();
 }
 
@@ -779,9 +914,22 @@ cudaError_t launch_scale_identity(cudaStream_t st, int M, const double* A, doubl
 }
 
 cudaError_t launch_yx_permute(cudaStream_t st, int n, int M, const double* gram,
-                              double* yx) {
+                              double* yx, long ldy) {
   long J = (long)n * M;
-  yx_permute_kernel<<<blocks_for(J * J, 256), 256, 0, st>>>(n, M, gram, yx);
+  yx_permute_kernel<<<blocks_for(J * J, 256), 256, 0, st>>>(n, M, gram, yx, ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_rows(cudaStream_t st, long rows, long Jup, long Jdn,
+                            const double* in, double* out, long ld, long dn_off) {
+  pad_rows_kernel<<<blocks_for(rows * (Jup + Jdn), 256), 256, 0, st>>>(rows, Jup, Jdn, in,
+                                                                     out, ld, dn_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(cudaStream_t st, long rows, long cols, const double* in,
+                             double* out, long ldo) {
+  transpose_kernel<<<blocks_for(rows * cols, 256), 256, 0, st>>>(rows, cols, in, out, ldo);
   return cudaGetLastError();
 }
 
@@ -799,22 +947,30 @@ cudaError_t launch_init_walkers(cudaStream_t st, int W, int M, int N, const T* P
   return cudaGetLastError();
 }
 
+cudaError_t launch_add_diag(cudaStream_t st, int M, double* A, double a) {
+  add_diag_kernel<<<blocks_for(M, 128), 128, 0, st>>>(M, A, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, double* y) {
   axpy_d_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, a, x, y);
   return cudaGetLastError();
 }
 
 #define AFQMC_INST(T)                                                                    \
-  template cudaError_t launch_fields<T>(cudaStream_t, int, int, const T*, long, double, \
-                                        double, uint64_t, int, long, T*, T*, double2*); \
+  template cudaError_t launch_fields<T>(cudaStream_t, int, int, const T*, long, int,    \
+                                        long, double, double, uint64_t, int, long, T*,  \
+                                        long, T*, double2*);                            \
   template cudaError_t launch_taylor<T>(cudaStream_t, int, int, int, int, const T*,     \
                                         const T*, T*);                                  \
   template cudaError_t launch_overlap<T>(cudaStream_t, int, int, int, int, const T*,    \
-                                         const T*, T*, double2*, double2*, bool);       \
-  template cudaError_t launch_mgs<T>(cudaStream_t, int, int, int, int, T*, double2*,    \
-                                     bool);                                             \
+                                         const T*, T*, long, long, double2*, double2*,  \
+                                         bool);                                         \
+  template cudaError_t launch_qr<T>(cudaStream_t, int, int, int, int, T*, double2*,     \
+                                    double*, bool);                                     \
   template cudaError_t launch_energy_reduce<T>(cudaStream_t, int, int, int, int, int,   \
-                                               const T*, long, const T*, const T*,      \
+                                               const T*, long, int, long, const T*,     \
+                                               long, long, const T*, long, long,        \
                                                double2*);                               \
   template cudaError_t launch_gather<T>(cudaStream_t, int, long, long, const int*,      \
                                         const T*, T*, const T*, T*, const double2*,     \
