@@ -306,6 +306,16 @@ def local_energy(h1, L, trial, Phi_up, Phi_dn):
     return E
 
 
+def reference_energy(h1, L, trial):
+    """E_T: the energy of the reference determinant alone, <D_0|H|D_0>
+    (for a one-determinant trial, the trial's variational energy). At
+    phi = D_0 the excited determinants have zero overlap, so the
+    multi-determinant local energy there is a 0/0 limit; the reference
+    energy is the well-defined shift used instead."""
+    Du, Dd = trial.D_up[0], trial.D_dn[0]
+    return float(local_energy_rotated(h1, L, Du, Dd, Du[None], Dd[None])[0].real)
+
+
 # ---------------------------------------------------------------------------
 # Population control (simple comb)
 # ---------------------------------------------------------------------------
@@ -390,8 +400,7 @@ class OracleRun:
         self.weight = np.ones(W)
         self.logO, _ = trial_overlap(self.trial, self.Phi_up, self.Phi_dn)
         if e_shift is None:
-            e_shift = float(local_energy(self.h1, self.L, self.trial,
-                                         self.Phi_up[:1], self.Phi_dn[:1])[0].real)
+            e_shift = reference_energy(self.h1, self.L, self.trial)
         self.e_shift = e_shift
         self.step_count = 0
         self.energies = []          # (step, mixed energy, E_L per walker)

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libafqmc.so")
-SOURCES = ["capi.cu", "walker.cu", "gemm_simt.cu", "tc.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "walker.cu", "gemm_simt.cu", "tc.cu", "noalloc.cu",
+           "multidet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "--expt-relaxed-constexpr"]

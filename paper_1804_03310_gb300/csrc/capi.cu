@@ -5,11 +5,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
 #include "../../include/afqmc.h"
 #include "kernels.h"
+#include "multidet.h"
 #include "tc.h"
 
 using namespace afqmc;
@@ -51,7 +53,7 @@ struct afqmc_ctx {
   void *L, *Ltil, *Bhalf, *PsiT, *Yx_up, *Yx_dn;
   double* PsiT64;
   double *weight, *scan, *wnew, *escalar, *lr;
-  double2 *logO, *logO2, *logO_new, *logdet, *lw, *eloc, *hist;
+  double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
   int *parent, *status;
   std::vector<void*> allocs;
 
@@ -64,6 +66,17 @@ struct afqmc_ctx {
   void* LT;          // L transposed [M*M][ldS] (tensor-core operand)
   void* dB;          // B_half - I (tensor-core operand)
   void* bimg;        // (B_half - I) operand image for the fused tensor-core Taylor kernel
+
+  // multi-determinant trial (Sherman-Morrison-Woodbury), unused for one determinant
+  bool md;
+  bool ref_only;            // evaluate with the reference determinant alone (E_T)
+  const double* ci_h;       // caller's CI coefficients (valid during create only)
+  MdTables mdt;
+  int nact[2];
+  long ldg, gdn_off;        // Gamma / LtilA row layout: up block at 0, down at gdn_off
+  void *Gamma, *Gamma2, *LtilA;
+  std::vector<int> act_h[2];       // host: active orbital indices per spin
+  double* CactT64;                 // [nact_up + nact_dn][M] (read-outs)
 
   // tensor-core resources (TF32 modes)
   TcCtx* tc;
@@ -206,13 +219,18 @@ template <typename T>
 afqmc_status force_bias_contraction(afqmc_ctx* c) {
   const int W = c->W, G = c->G;
   KTimer t(c, 0);
+  // single determinant: X = Theta . L~^T; multi-determinant: X = Gamma . L~act^T
+  const bool md = c->md && !c->ref_only;
+  const void* A = md ? c->Gamma : c->Theta;
+  const void* B = md ? c->LtilA : c->Ltil;
+  const long ld = md ? c->ldg : c->ldt;
   if (c->tc) {
-    LK(tc_gemm(c->tc, c->st, 2 * W, G + 1, (int)c->ldt, (const float*)c->Theta, c->ldt,
-               (const float*)c->Ltil, c->ldt, (float*)c->X, c->ldx, 1.0f, 0.0f, nullptr, 0,
-               c->split3, c->xsplit, 2L * W * c->ldx, c->status));
+    LK(tc_gemm(c->tc, c->st, 2 * W, G + 1, (int)ld, (const float*)A, ld, (const float*)B, ld,
+               (float*)c->X, c->ldx, 1.0f, 0.0f, nullptr, 0, c->split3, c->xsplit,
+               2L * W * c->ldx, c->status));
   } else {
-    LK(gemm<T>(c->st, false, true, 2 * W, G + 1, (int)c->ldt, T(1), (const T*)c->Theta,
-               c->ldt, 0, (const T*)c->Ltil, c->ldt, 0, T(0), (T*)c->X, c->ldx, 0, 1));
+    LK(gemm<T>(c->st, false, true, 2 * W, G + 1, (int)ld, T(1), (const T*)A, ld, 0,
+               (const T*)B, ld, 0, T(0), (T*)c->X, c->ldx, 0, 1));
   }
   return AFQMC_OK;
 }
@@ -220,6 +238,17 @@ afqmc_status force_bias_contraction(afqmc_ctx* c) {
 template <typename T>
 afqmc_status measure_T(afqmc_ctx* c, bool record) {
   const int W = c->W, M = c->M, G = c->G;
+  if (c->md && !c->ref_only) {
+    KTimer t(c, 7);
+    LK(launch_md_energy<T>(c->st, c->mdt, W, M, c->nu, c->nd, G, (const T*)c->Theta, c->ldt,
+                           c->dn_off, c->logdet, (const T*)c->LtilA, c->ldg, c->gdn_off,
+                           c->eloc, c->fp64_islands));
+    LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, (double)c->step,
+                           record ? c->hist : nullptr, (int)(c->n_meas % kHist),
+                           c->escalar));
+    if (record) c->n_meas += 1;
+    return AFQMC_OK;
+  }
   afqmc_status s = force_bias_contraction<T>(c);
   if (s != AFQMC_OK) return s;
   {
@@ -275,6 +304,13 @@ afqmc_status comb_T(afqmc_ctx* c) {
   std::swap(c->Phi, c->Phi2);
   std::swap(c->Theta, c->Theta2);
   std::swap(c->logO, c->logO2);
+  if (c->md) {
+    LK(launch_gather_rows<T>(c->st, W, 2 * c->ldg, c->parent, (const T*)c->Gamma,
+                             (T*)c->Gamma2));
+    LK(launch_gather_rows<double2>(c->st, W, 2, c->parent, c->logdet, c->logdet2));
+    std::swap(c->Gamma, c->Gamma2);
+    std::swap(c->logdet, c->logdet2);
+  }
   return AFQMC_OK;
 }
 
@@ -283,7 +319,13 @@ afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
   LK(launch_overlap<T>(c->st, c->W, c->M, c->nu, c->nd, (const T*)c->Phi,
                        (const T*)c->PsiT, (T*)c->Theta, c->ldt, c->dn_off, c->logdet,
                        nullptr, c->fp64_islands));
-  LK(launch_logdet_sum(c->st, c->W, c->logdet, logO_out));
+  if (c->md) {   // ratios by Sherman-Morrison-Woodbury, ln O_T and Gamma
+    LK(launch_md_step<T>(c->st, c->mdt, c->W, c->M, c->nu, c->nd, (const T*)c->Theta, c->ldt,
+                         c->dn_off, c->logdet, logO_out, (T*)c->Gamma, c->ldg, c->gdn_off,
+                         c->fp64_islands));
+  } else {
+    LK(launch_logdet_sum(c->st, c->W, c->logdet, logO_out));
+  }
   return AFQMC_OK;
 }
 
@@ -385,8 +427,8 @@ afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
   if (p->n_up < 0 || p->n_dn < 0 || p->n_up > M || p->n_dn > M || p->n_up + p->n_dn < 1)
     return fail(c, AFQMC_E_INVALID, "electron counts out of range");
   if (p->n_chol < 1) return fail(c, AFQMC_E_INVALID, "n_chol must be >= 1");
-  if (p->n_det != 1)
-    return fail(c, AFQMC_E_INVALID, "multi-determinant trials are not available in this build");
+  if (p->n_det < 1 || p->n_det > 256 * MD_MAX_DET_PER_THREAD)
+    return fail(c, AFQMC_E_INVALID, "n_det must be in 1..2048");
   if (p->n_walkers < 1 || p->n_walkers > 32768)
     return fail(c, AFQMC_E_INVALID, "n_walkers must be in 1..32768");
   if (!(p->dtau > 0.0)) return fail(c, AFQMC_E_INVALID, "dtau must be > 0");
@@ -550,6 +592,23 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   }
   LK(launch_convert<T>(st, MM, Bh, (T*)c->Bhalf));
   LK(launch_convert<T>(st, (long)N * M, PsiT, (T*)c->PsiT));
+  if (c->md) {   // C_act^T L_g and C_act^T h1 per spin, [G+1][ldg]
+    double* la;
+    TM(la, (size_t)(G + 1) * c->ldg);
+    CK(cudaMemsetAsync(la, 0, (size_t)(G + 1) * c->ldg * sizeof(double), st));
+    for (int sg = 0; sg < 2; ++sg) {
+      const int na = c->nact[sg];
+      if (na == 0) continue;
+      const double* ct = c->CactT64 + (sg ? (size_t)c->nact[0] * M : 0);
+      double* dst = la + (sg ? c->gdn_off : 0);
+      LK(gemm<double>(st, false, false, na, M, M, 1.0, ct, M, 0, L, M, MM, 0.0, dst, M,
+                      c->ldg, G));
+      LK(gemm<double>(st, false, false, na, M, M, 1.0, ct, M, 0, h1, M, 0, 0.0,
+                      dst + (size_t)G * c->ldg, M, 0, 1));
+      LK(launch_convert<T>(st, (long)na * M, ct, (T*)c->mdt.CactT[sg]));
+    }
+    LK(launch_convert<T>(st, (long)(G + 1) * c->ldg, la, (T*)c->LtilA));
+  }
   CK(cudaStreamSynchronize(st));
   for (void* q : tmp) cudaFree(q);
 #undef TM
@@ -558,7 +617,10 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   afqmc_status s = overlap_T<T>(c, c->logO);
   if (s != AFQMC_OK) return s;
   if (isnan(c->p.e_shift)) {
+    // E_T: energy of the reference determinant, <D_0|H|D_0>
+    c->ref_only = true;
     s = measure_T<T>(c, false);
+    c->ref_only = false;
     if (s != AFQMC_OK) return s;
     double2 e0;
     CK(cudaMemcpyAsync(&e0, c->eloc, sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -572,6 +634,85 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
 }
 
 long round4(long x) { return (x + 3) / 4 * 4; }
+
+// Parity (+1 / -1) of the permutation taking list `from` to list `to`
+// (same elements).
+int perm_sign(const std::vector<int>& from, const std::vector<int>& to) {
+  const int n = (int)from.size();
+  std::vector<int> pos(n), seen(n, 0);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i)
+      if (from[i] == to[j]) { pos[j] = i; break; }
+  int sign = 1;
+  for (int j = 0; j < n; ++j) {
+    if (seen[j]) continue;
+    int len = 0, k = j;
+    while (!seen[k]) { seen[k] = 1; k = pos[k]; ++len; }
+    if (len % 2 == 0) sign = -sign;
+  }
+  return sign;
+}
+
+// Multi-determinant trial: each determinant as in-place excitations of the
+// reference (holes at reference positions, filled by particles in ascending
+// order), the column-order sign folded into its coefficient; active orbitals
+// per spin are the reference orbitals (in position order) then the others
+// occupied anywhere (ascending).
+afqmc_status prepare_multidet(afqmc_ctx* c, const int32_t* ou, const int32_t* od,
+                              const double* ci, std::vector<MdDet>& dets,
+                              std::vector<double2>& cconj) {
+  const int nd_ = c->ndet;
+  dets.assign(nd_, MdDet());
+  cconj.assign(nd_, make_double2(0, 0));
+  std::vector<int> sign(nd_, 1);
+  for (int sg = 0; sg < 2; ++sg) {
+    const int ns = sg ? c->nd : c->nu;
+    const int32_t* occ = sg ? od : ou;
+    std::vector<int> ref(occ, occ + ns);
+    std::vector<int> refpos(c->M, -1);
+    for (int a = 0; a < ns; ++a) refpos[ref[a]] = a;
+    std::vector<char> used(c->M, 0);
+    for (int i = 0; i < nd_; ++i)
+      for (int a = 0; a < ns; ++a) used[occ[(size_t)i * ns + a]] = 1;
+    std::vector<int>& act = c->act_h[sg];
+    act = ref;
+    for (int o = 0; o < c->M; ++o)
+      if (used[o] && refpos[o] < 0) act.push_back(o);
+    std::vector<int> actidx(c->M, -1);
+    for (size_t q = 0; q < act.size(); ++q) actidx[act[q]] = (int)q;
+    c->nact[sg] = (int)act.size();
+    for (int i = 0; i < nd_; ++i) {
+      std::vector<int> oi(occ + (size_t)i * ns, occ + (size_t)(i + 1) * ns);
+      std::vector<char> in_i(c->M, 0);
+      for (int o : oi) in_i[o] = 1;
+      std::vector<int> holes, parts;
+      for (int a = 0; a < ns; ++a)
+        if (!in_i[ref[a]]) holes.push_back(a);
+      std::vector<int> sorted_oi = oi;
+      std::sort(sorted_oi.begin(), sorted_oi.end());
+      for (int o : sorted_oi)
+        if (refpos[o] < 0) parts.push_back(o);
+      if ((int)holes.size() > MD_EMAX)
+        return fail(c, AFQMC_E_INVALID,
+                    "a determinant has more than " + std::to_string(MD_EMAX) +
+                        " excitations in one spin");
+      std::vector<int> t = ref;
+      for (size_t l = 0; l < holes.size(); ++l) t[holes[l]] = parts[l];
+      sign[i] *= perm_sign(oi, t);
+      MdDet& d = dets[i];
+      d.E[sg] = (int)holes.size();
+      for (int l = 0; l < MD_EMAX; ++l) {
+        d.h[sg][l] = l < (int)holes.size() ? holes[l] : 0;
+        d.p[sg][l] = l < (int)holes.size() ? actidx[parts[l]] : 0;
+      }
+    }
+  }
+  if (dets[0].E[0] != 0 || dets[0].E[1] != 0)
+    return fail(c, AFQMC_E_INVALID, "determinant 0 must be the reference");
+  for (int i = 0; i < nd_; ++i)
+    cconj[i] = make_double2(sign[i] * ci[2 * i], -sign[i] * ci[2 * i + 1]);
+  return AFQMC_OK;
+}
 
 afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
                          const double* Cu, const double* Cd, const int32_t* ou,
@@ -596,9 +737,68 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     // still fill the GPU; partial sums are added in order by the consumers
     const long tiles = ((2L * W + 127) / 128) * ((G + 1 + 127) / 128);
     const long ktiles = (c->ldt + 31) / 32;
-    int ks = 1;
-    while (tiles * ks * 2 <= 2 * 152 && ks * 2 <= 8 && ktiles / (ks * 2) >= 4) ks *= 2;
-    c->xsplit = ks;
+    int ks = (int)(152 / (tiles > 0 ? tiles : 1));
+    if (ks > 8) ks = 8;
+    while (ks > 1 && ktiles / ks < 4) --ks;
+    c->xsplit = ks < 1 ? 1 : ks;
+  }
+  c->md = c->ndet > 1;
+  c->ref_only = false;
+  std::vector<MdDet> dets_h;
+  std::vector<double2> cconj_h;
+  c->nact[0] = c->nu;
+  c->nact[1] = c->nd;
+  c->Gamma = c->Gamma2 = c->LtilA = nullptr;
+  c->CactT64 = nullptr;
+  if (c->md) {
+    afqmc_status s0 = prepare_multidet(c, ou, od, c->ci_h, dets_h, cconj_h);
+    if (s0 != AFQMC_OK) return s0;
+  }
+  c->gdn_off = round4((long)c->nact[0] * M);
+  c->ldg = c->gdn_off + round4((long)c->nact[1] * M);
+  if (c->md) {
+    const bool f64c = c->fp64_islands;
+    if (md_energy_smem(M, c->nu, c->nd, c->nact[0], c->nact[1], c->ndet, f64c) > 227 * 1024)
+      return fail(c, AFQMC_E_INVALID,
+                  "multi-determinant trial too large for the on-chip energy kernel");
+    DALLOC(c->Gamma, (size_t)W * 2 * c->ldg * es);
+    DALLOC(c->Gamma2, (size_t)W * 2 * c->ldg * es);
+    DALLOC(c->LtilA, (size_t)(G + 1) * c->ldg * es);
+    DALLOC(c->CactT64, (size_t)(c->nact[0] + c->nact[1]) * M * sizeof(double));
+    void *ct0, *ct1, *dt, *cc, *r0, *r1;
+    DALLOC(ct0, (size_t)c->nact[0] * M * es);
+    DALLOC(ct1, (size_t)c->nact[1] * M * es);
+    DALLOC(dt, sizeof(MdDet) * c->ndet);
+    DALLOC(cc, sizeof(double2) * c->ndet);
+    DALLOC(r0, sizeof(int) * (c->nu + 1));
+    DALLOC(r1, sizeof(int) * (c->nd + 1));
+    std::vector<int> ract_u(c->nu + 1), ract_d(c->nd + 1);
+    for (int a = 0; a <= c->nu; ++a) ract_u[a] = a;
+    for (int a = 0; a <= c->nd; ++a) ract_d[a] = a;
+    CK(cudaMemcpyAsync(dt, dets_h.data(), sizeof(MdDet) * c->ndet, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(cc, cconj_h.data(), sizeof(double2) * c->ndet, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(r0, ract_u.data(), sizeof(int) * (c->nu + 1), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(r1, ract_d.data(), sizeof(int) * (c->nd + 1), cudaMemcpyHostToDevice, c->st));
+    // active orbitals as rows, FP64 copy for read-outs
+    std::vector<double> cact((size_t)(c->nact[0] + c->nact[1]) * M);
+    for (int sg = 0; sg < 2; ++sg) {
+      const double* C = sg ? Cd : Cu;
+      const size_t off = sg ? (size_t)c->nact[0] * M : 0;
+      for (int q = 0; q < c->nact[sg]; ++q)
+        for (int k = 0; k < M; ++k) cact[off + (size_t)q * M + k] = C[(size_t)k * M + c->act_h[sg][q]];
+    }
+    CK(cudaMemcpyAsync(c->CactT64, cact.data(), cact.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->mdt.ndet = c->ndet;
+    c->mdt.nact[0] = c->nact[0];
+    c->mdt.nact[1] = c->nact[1];
+    c->mdt.dets = (const MdDet*)dt;
+    c->mdt.cconj = (const double2*)cc;
+    c->mdt.ract[0] = (const int*)r0;
+    c->mdt.ract[1] = (const int*)r1;
+    c->mdt.CactT[0] = ct0;
+    c->mdt.CactT[1] = ct1;
   }
   DALLOC(c->Phi, phi * es);
   DALLOC(c->Phi2, phi * es);
@@ -634,6 +834,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   DALLOC(c->logO2, W * sizeof(double2));
   DALLOC(c->logO_new, W * sizeof(double2));
   DALLOC(c->logdet, 2 * W * sizeof(double2));
+  DALLOC(c->logdet2, 2 * W * sizeof(double2));
   DALLOC(c->lw, W * sizeof(double2));
   DALLOC(c->eloc, W * sizeof(double2));
   DALLOC(c->hist, kHist * sizeof(double2));
@@ -719,7 +920,9 @@ afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const do
     }
     c->own_stream = true;
   }
+  c->ci_h = ci;
   s = create_impl(c, h1, L, C_up, C_dn, occ_up, occ_dn);
+  c->ci_h = nullptr;
   if (s != AFQMC_OK) {
     g_create_err = c->err;
     afqmc_destroy(c);
@@ -790,6 +993,37 @@ afqmc_status afqmc_green(afqmc_ctx* c, int32_t walker, double* G_up, double* G_d
                                                   : c->dn_off + (size_t)(a - c->nu) * M) + k;
     return c->fp64 ? ((const double*)th.data())[idx] : (double)((const float*)th.data())[idx];
   };
+  if (c->md) {   // G_ij = sum_q Gamma[q][j] C_act[i][q]
+    std::vector<unsigned char> gb(2 * (size_t)c->ldg * es);
+    CK(cudaMemcpyAsync(gb.data(), (const unsigned char*)c->Gamma + (size_t)walker * 2 * c->ldg * es,
+                       gb.size(), cudaMemcpyDeviceToHost, c->st));
+    std::vector<double> ca((size_t)(c->nact[0] + c->nact[1]) * M);
+    CK(cudaMemcpyAsync(ca.data(), c->CactT64, ca.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    auto gam = [&](int cc, size_t idx) -> double {
+      idx += (size_t)cc * c->ldg;
+      return c->fp64 ? ((const double*)gb.data())[idx] : (double)((const float*)gb.data())[idx];
+    };
+    for (int sig = 0; sig < 2; ++sig) {
+      double* G = sig ? G_dn : G_up;
+      if (!G) continue;
+      const int na = c->nact[sig];
+      const size_t goff = sig ? c->gdn_off : 0, coff = sig ? (size_t)c->nact[0] * M : 0;
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+          double re = 0.0, im = 0.0;
+          for (int q = 0; q < na; ++q) {
+            const double cv = ca[coff + (size_t)q * M + i];
+            re += gam(0, goff + (size_t)q * M + j) * cv;
+            im += gam(1, goff + (size_t)q * M + j) * cv;
+          }
+          G[2 * ((size_t)i * M + j)] = re;
+          G[2 * ((size_t)i * M + j) + 1] = im;
+        }
+    }
+    return AFQMC_OK;
+  }
   // G_ij = sum_a Theta_ja D_ia (G^T = Theta D^H, real trial orbitals)
   for (int sig = 0; sig < 2; ++sig) {
     double* G = sig ? G_dn : G_up;

@@ -95,6 +95,11 @@ cudaError_t launch_gather(cudaStream_t st, int W, long phi_elems, long theta_ele
                           const T* Theta, T* Theta_out, const double2* logO,
                           double2* logO_out, const double* wnew, double* weight);
 
+// Row copies out[j] = in[parent[j]] ([W][elems]).
+template <typename T>
+cudaError_t launch_gather_rows(cudaStream_t st, int W, long elems, const int* parent,
+                               const T* in, T* out);
+
 // Setup helpers (FP64).
 cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,
                                 const double* L, double* h1p);

@@ -217,7 +217,7 @@ taylor_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
 // --------------------------------------------------------------- K6
 // Complex value of the elimination's compute type R (double or float).
 template <typename R>
-struct cx {
+struct __align__(2 * sizeof(R)) cx {
   R x, y;
 };
 template <typename R>
@@ -679,6 +679,15 @@ __global__ void gather_kernel(long phi_elems, long theta_elems,
 }
 
 // --------------------------------------------------------------- setup
+template <typename T>
+__global__ void gather_rows_kernel(long elems, const int* __restrict__ parent,
+                                   const T* __restrict__ in, T* __restrict__ out) {
+  const int j = blockIdx.x;
+  const int p = parent[j];
+  for (long e = threadIdx.x; e < elems; e += blockDim.x)
+    out[(long)j * elems + e] = in[(long)p * elems + e];
+}
+
 __global__ void h1_remainder_kernel(int M, int n_chol, const double* __restrict__ h1,
                                     const double* __restrict__ L,
                                     double* __restrict__ h1p) {
@@ -899,6 +908,19 @@ cudaError_t launch_gather(cudaStream_t st, int W, long phi_elems, long theta_ele
                                       Theta, Theta_out, logO, logO_out, wnew, weight);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_gather_rows(cudaStream_t st, int W, long elems, const int* parent,
+                               const T* in, T* out) {
+  gather_rows_kernel<T><<<W, 256, 0, st>>>(elems, parent, in, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gather_rows<float>(cudaStream_t, int, long, const int*,
+                                               const float*, float*);
+template cudaError_t launch_gather_rows<double>(cudaStream_t, int, long, const int*,
+                                                const double*, double*);
+template cudaError_t launch_gather_rows<double2>(cudaStream_t, int, long, const int*,
+                                                 const double2*, double2*);
 
 cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,
                                 const double* L, double* h1p) {
