@@ -87,11 +87,19 @@ typedef struct {
                             Gram-Schmidt arithmetic in FP64; 0 (default) = FP32
                             arithmetic there, with the log-determinant and
                             ln det R sums still accumulated in FP64 */
-  int32_t reserved[7];   /* must be zero */
+  int32_t graphs;        /* 1: afqmc_propagate replays whole periods of the
+                            ortho / measure / comb cadence as CUDA graphs
+                            (same kernels, same results); 0: plain launches */
+  int32_t autotune;      /* tensor-core modes: 1 = time the launch shapes
+                            (afqmc_tuning) on this system at creation and keep
+                            the fastest, cached per shape for the process;
+                            0 = fixed heuristics */
+  int32_t reserved[5];   /* must be zero */
 } afqmc_params;
 
 /* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,
- * ortho_every 2, measure_every 20, pc_every 20, everything else zero. */
+ * ortho_every 2, measure_every 20, pc_every 20, graphs 1, autotune 1,
+ * everything else zero. */
 void afqmc_params_default(afqmc_params* p);
 
 /* Create a context: copy the Hamiltonian and trial to the device, precompute
@@ -127,8 +135,10 @@ afqmc_status afqmc_create(const afqmc_params* params, const double* h1,
  * returns host data reports AFQMC_E_POPULATION if a comb found all weights 0. */
 afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t n_steps);
 
-/* Orthonormalise every walker now (modified Gram-Schmidt in FP64); the
- * log-overlap drops by ln det R (Sec. IV.A). */
+/* Orthonormalise every walker now: the QR factor Q with R's diagonal real
+ * and positive (the factorisation modified Gram-Schmidt produces), computed
+ * from the Cholesky factor of the Gram matrix; ln det R is accumulated in
+ * FP64 and the log-overlap drops by it (Sec. IV.A). */
 afqmc_status afqmc_orthonormalize(afqmc_ctx* ctx);
 
 /* Comb population control now (Sec. V final comments); offset drawn from
@@ -187,8 +197,153 @@ afqmc_status afqmc_kernel_stats(afqmc_ctx* ctx, int32_t kernel_id,
                                 double* work_per_launch, int32_t* is_bytes);
 #define AFQMC_N_KERNEL_IDS 9
 
-/* Number of kernel launches issued since creation (all of this library's). */
+/* Number of kernel launches issued since creation (all of this library's),
+ * counting each kernel of a replayed graph. */
 int64_t afqmc_launch_count(const afqmc_ctx* ctx);
+
+/* Launch shapes of the tensor-core modes (TF32, TF32X3). Shapes change the
+ * numerics only through the order of FP32 sums (split K) and through the
+ * Taylor path (one fused tensor-core kernel for B_half exp_T(V) B_half, or
+ * the half steps on the tensor cores around the series on the CUDA cores);
+ * every choice meets the same tolerance against the FP64 path. In the FP64
+ * and FP32 modes get returns xsplit 1 and zeros, and set accepts only that. */
+typedef struct {
+  int32_t xsplit;         /* K ranges of the force-bias contraction, 1..8 */
+  int32_t bn_force_bias;  /* output tile width (64 or 128) of the force-bias, */
+  int32_t bn_one_body;    /*   one-body-operator, energy and half-step */
+  int32_t bn_energy;      /*   contractions */
+  int32_t bn_half_step;
+  int32_t taylor_fused;   /* 1: fused tensor-core Taylor kernel (M <= 64) */
+  int32_t reserved[2];    /* zero */
+} afqmc_tuning;
+afqmc_status afqmc_get_tuning(afqmc_ctx* ctx, afqmc_tuning* out);
+afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t);
+
+/* Device memory of a context with these parameters: *resident bytes held
+ * from afqmc_create to afqmc_destroy (what afqmc_device_bytes reports), and
+ * *setup_peak further bytes of FP64 staging held during afqmc_create only.
+ * occ_up / occ_dn as for afqmc_create (they fix the active orbitals of a
+ * multi-determinant trial; may be NULL when n_det == 1). Host-only: needs no
+ * GPU. AFQMC_E_INVALID for parameters afqmc_create would reject by size. */
+afqmc_status afqmc_footprint(const afqmc_params* params, const int32_t* occ_up,
+                             const int32_t* occ_dn, size_t* resident,
+                             size_t* setup_peak);
+
+/* Device bytes allocated by the context (equals the footprint's resident). */
+size_t afqmc_device_bytes(const afqmc_ctx* ctx);
+
+/* Blocks of steps captured as CUDA graphs so far (0 when graphs are off or
+ * the stream could not be captured, in which case propagation falls back to
+ * plain launches). */
+int32_t afqmc_graph_count(const afqmc_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Multi-system batching (no counterpart in the paper, whose runs are one
+ * system per GPU).
+ *
+ * A batch advances several contexts of uneven sizes (M, electrons, n_chol,
+ * walkers, precision, trial) together. Each block of steps_per_block steps
+ * is ONE CUDA graph launch on the batch's stream: the graph holds every
+ * member's captured block as an independent branch, so the systems run
+ * concurrently on the GPU and the host issues one launch per block, not one
+ * per kernel. Each member advances exactly as afqmc_propagate(ctx,
+ * steps_per_block) would (same kernels, same Philox counters, same
+ * results). The batch orders its work after all work already issued on the
+ * members' streams and the members' later work after the batch's, so the
+ * contexts remain usable one by one between batch calls. Members must stay
+ * alive while the batch exists; kernel timing must be off on them.
+ * Errors are described by afqmc_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+typedef struct afqmc_batch afqmc_batch;
+afqmc_status afqmc_batch_create(afqmc_ctx* const* ctxs, int32_t n,
+                                int32_t steps_per_block, afqmc_batch** out);
+afqmc_status afqmc_batch_propagate(afqmc_batch* b, int32_t n_blocks);
+/* Number of graph launches issued by the batch so far. */
+int64_t afqmc_batch_launches(const afqmc_batch* b);
+afqmc_status afqmc_batch_synchronize(afqmc_batch* b);
+void afqmc_batch_destroy(afqmc_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper).
+ *
+ * A server accepts independent ph-AFQMC runs (each a full afqmc_create
+ * input plus n_blocks blocks of steps_per_block steps) and runs them on one
+ * GPU with continuous batching: a native scheduler thread admits queued runs
+ * in arrival order as soon as a slot is free and the HBM budget holds the
+ * run's footprint (resident + setup staging, afqmc_footprint), and a later
+ * run that fits may overtake a head run that does not (the head is overtaken
+ * at most 8 times, then admission waits for it). Each admitted run gets its
+ * own stream; its walkers stay on the device from admission to its last
+ * block; blocks are captured as CUDA graphs and kept two deep in each run's
+ * stream, so the work of all admitted runs overlaps on the GPU. A finished
+ * run's memory is freed at once. A run's results depend only on its own
+ * inputs (its Philox counters are keyed by its seed and run_id), so they are
+ * the same alone and in any mix.
+ * Errors of these calls are described by afqmc_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+typedef struct afqmc_server afqmc_server;
+
+typedef struct {
+  size_t hbm_budget;   /* device bytes for runs; 0: 90% of the free memory */
+  int32_t max_active;  /* runs on the GPU at once, 1..256 (0: 64) */
+  int32_t device;      /* CUDA device ordinal */
+  int32_t reserved[4]; /* zero */
+} afqmc_server_config;
+
+enum { AFQMC_RUN_QUEUED = 0, AFQMC_RUN_ACTIVE = 1, AFQMC_RUN_DONE = 2,
+       AFQMC_RUN_FAILED = 3 };
+
+typedef struct {
+  int32_t state;        /* AFQMC_RUN_* */
+  int32_t status;       /* afqmc_status of a failed run, else AFQMC_OK */
+  int32_t n_blocks, blocks_done;
+  double t_submit;      /* host seconds since the server started; -1 if */
+  double t_admit;       /*   the event has not happened yet */
+  double t_done;
+  size_t footprint;     /* resident + setup staging bytes used for admission */
+  char message[160];    /* error text of a failed run */
+} afqmc_run_info;
+
+typedef struct {
+  double t_start;       /* host seconds: the later of the block's enqueue and
+                           the previous block's completion */
+  double t_end;         /* host seconds: completion seen by the scheduler */
+  double device_ms;     /* device time between the block's start and end */
+  double e_mixed;       /* mixed energy of the latest measurement (NaN if none) */
+  double weight_sum;    /* sum of walker weights at that measurement */
+  int64_t step;         /* step count at the end of the block */
+} afqmc_block_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed, blocks;
+  double walker_steps;  /* walker-steps of all completed blocks */
+  double p50_ms, p99_ms;/* block latency t_end - t_start over completed blocks */
+  double elapsed_s;     /* host seconds since the server started */
+  int32_t active, queued, max_active_seen, reserved0;
+  size_t bytes_in_use, peak_bytes;  /* admitted footprints (resident only) */
+} afqmc_server_stats;
+
+afqmc_status afqmc_server_create(const afqmc_server_config* cfg, afqmc_server** out);
+/* Queue a run. All inputs as for afqmc_create (copied during the call);
+ * n_blocks >= 1 blocks of steps_per_block >= 1 steps. *run_id receives the
+ * run's handle (not the Philox run_id, which stays params->run_id). */
+afqmc_status afqmc_server_submit(afqmc_server* s, const afqmc_params* params,
+                                 const double* h1, const double* L,
+                                 const double* C_up, const double* C_dn,
+                                 const int32_t* occ_up, const int32_t* occ_dn,
+                                 const double* ci, int32_t n_blocks,
+                                 int32_t steps_per_block, int64_t* run_id);
+/* State of a run and up to max_blocks of its block results (blocks may be
+ * NULL). AFQMC_E_INVALID for an unknown run. */
+afqmc_status afqmc_server_poll(afqmc_server* s, int64_t run_id, afqmc_run_info* info,
+                               afqmc_block_result* blocks, int32_t max_blocks);
+/* Wait until the run (run_id >= 0) or every submitted run (run_id < 0) is
+ * done or failed; AFQMC_E_TIMEOUT after timeout_s seconds (< 0: no limit). */
+afqmc_status afqmc_server_wait(afqmc_server* s, int64_t run_id, double timeout_s);
+afqmc_status afqmc_server_stats_get(afqmc_server* s, afqmc_server_stats* out);
+/* Stop the scheduler (runs still queued or active are abandoned) and free
+ * everything. */
+void afqmc_server_destroy(afqmc_server* s);
 
 /* Comb population control that allocates no device memory.
  *

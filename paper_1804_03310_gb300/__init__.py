@@ -6,6 +6,10 @@ ABI of include/afqmc.h); this package is the thin Python binding.
 from .afqmc import (  # noqa: F401
     Afqmc,
     AfqmcError,
+    Batch,
+    Inputs,
+    Server,
+    afqmc_footprint,
     KERNEL_IDS,
     PRECISIONS,
     decode_state,

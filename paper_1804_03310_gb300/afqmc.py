@@ -33,7 +33,46 @@ class afqmc_params(C.Structure):
                 ("measure_every", C.c_int32), ("pc_every", C.c_int32),
                 ("taylor_order", C.c_int32), ("fb_cap", C.c_double),
                 ("e_shift", C.c_double), ("fp64_islands", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("graphs", C.c_int32), ("autotune", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class afqmc_tuning(C.Structure):
+    _fields_ = [("xsplit", C.c_int32), ("bn_force_bias", C.c_int32),
+                ("bn_one_body", C.c_int32), ("bn_energy", C.c_int32),
+                ("bn_half_step", C.c_int32), ("taylor_fused", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
+class afqmc_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int32),
+                ("device", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class afqmc_run_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("n_blocks", C.c_int32),
+                ("blocks_done", C.c_int32), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("footprint", C.c_size_t), ("message", C.c_char * 160)]
+
+
+class afqmc_block_result(C.Structure):
+    _fields_ = [("t_start", C.c_double), ("t_end", C.c_double),
+                ("device_ms", C.c_double), ("e_mixed", C.c_double),
+                ("weight_sum", C.c_double), ("step", C.c_int64)]
+
+
+class afqmc_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("failed", C.c_int64), ("blocks", C.c_int64),
+                ("walker_steps", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("elapsed_s", C.c_double),
+                ("active", C.c_int32), ("queued", C.c_int32),
+                ("max_active_seen", C.c_int32), ("reserved0", C.c_int32),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
+RUN_STATES = {0: "queued", 1: "active", 2: "done", 3: "failed"}
 
 
 class AfqmcError(RuntimeError):
@@ -79,6 +118,25 @@ def load_library(path: str = LIB_PATH):
         "afqmc_destroy": (None, [vp]),
         "afqmc_comb_static": (C.c_int, [vp, C.c_int32, C.c_uint64, C.c_int32,
                                         C.c_int64, vp, vp, vp]),
+        "afqmc_get_tuning": (C.c_int, [vp, P(afqmc_tuning)]),
+        "afqmc_set_tuning": (C.c_int, [vp, P(afqmc_tuning)]),
+        "afqmc_footprint": (C.c_int, [P(afqmc_params), i32, i32, P(C.c_size_t),
+                                      P(C.c_size_t)]),
+        "afqmc_device_bytes": (C.c_size_t, [vp]),
+        "afqmc_graph_count": (C.c_int32, [vp]),
+        "afqmc_batch_create": (C.c_int, [P(vp), C.c_int32, C.c_int32, P(vp)]),
+        "afqmc_batch_propagate": (C.c_int, [vp, C.c_int32]),
+        "afqmc_batch_launches": (C.c_int64, [vp]),
+        "afqmc_batch_synchronize": (C.c_int, [vp]),
+        "afqmc_batch_destroy": (None, [vp]),
+        "afqmc_server_create": (C.c_int, [P(afqmc_server_config), P(vp)]),
+        "afqmc_server_submit": (C.c_int, [vp, P(afqmc_params), d, d, d, d, i32, i32, d,
+                                          C.c_int32, C.c_int32, P(C.c_int64)]),
+        "afqmc_server_poll": (C.c_int, [vp, C.c_int64, P(afqmc_run_info),
+                                        P(afqmc_block_result), C.c_int32]),
+        "afqmc_server_wait": (C.c_int, [vp, C.c_int64, C.c_double]),
+        "afqmc_server_stats_get": (C.c_int, [vp, P(afqmc_server_stats)]),
+        "afqmc_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -102,29 +160,26 @@ def default_params() -> afqmc_params:
     return p
 
 
-class Afqmc:
-    """One ph-AFQMC context (a population of walkers of one system)."""
+class Inputs:
+    """afqmc_create's arguments as contiguous arrays plus the parameter block."""
 
     def __init__(self, h1, L, C_up, C_dn, occ_up, occ_dn, ci, *, dtau,
                  n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
                  measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
-                 e_shift=None, fp64_islands=False, stream=None):
-        lib = load_library()
-        self._lib = lib
-        h1 = np.ascontiguousarray(h1, dtype=np.float64)
-        L = np.ascontiguousarray(L, dtype=np.float64)
-        C_up = np.ascontiguousarray(C_up, dtype=np.float64)
-        C_dn = np.ascontiguousarray(C_dn, dtype=np.float64)
-        occ_up = np.ascontiguousarray(occ_up, dtype=np.int32)
-        occ_dn = np.ascontiguousarray(occ_dn, dtype=np.int32)
-        ci = np.ascontiguousarray(np.asarray(ci, dtype=np.complex128).view(np.float64))
-        M = h1.shape[0]
+                 e_shift=None, fp64_islands=False, graphs=True, autotune=True):
+        self.h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        self.L = np.ascontiguousarray(L, dtype=np.float64)
+        self.C_up = np.ascontiguousarray(C_up, dtype=np.float64)
+        self.C_dn = np.ascontiguousarray(C_dn, dtype=np.float64)
+        self.occ_up = np.ascontiguousarray(occ_up, dtype=np.int32)
+        self.occ_dn = np.ascontiguousarray(occ_dn, dtype=np.int32)
+        self.ci = np.ascontiguousarray(np.asarray(ci, dtype=np.complex128).view(np.float64))
         p = default_params()
-        p.M = M
-        p.n_up = occ_up.shape[1]
-        p.n_dn = occ_dn.shape[1]
-        p.n_chol = L.shape[0]
-        p.n_det = occ_up.shape[0]
+        p.M = self.h1.shape[0]
+        p.n_up = self.occ_up.shape[1]
+        p.n_dn = self.occ_dn.shape[1]
+        p.n_chol = self.L.shape[0]
+        p.n_det = self.occ_up.shape[0]
         p.n_walkers = n_walkers
         p.dtau = dtau
         p.seed = seed
@@ -137,16 +192,9 @@ class Afqmc:
         p.fb_cap = fb_cap
         p.e_shift = math.nan if e_shift is None else e_shift
         p.fp64_islands = int(bool(fp64_islands))
+        p.graphs = int(bool(graphs))
+        p.autotune = int(bool(autotune))
         self.params = p
-        self.M, self.n_up, self.n_dn = M, p.n_up, p.n_dn
-        self.n_chol, self.n_walkers = p.n_chol, n_walkers
-        self._h = C.c_void_p()
-        st = C.c_void_p(stream) if stream else None
-        s = lib.afqmc_create(C.byref(p), _dptr(h1), _dptr(L), _dptr(C_up),
-                             _dptr(C_dn), _iptr(occ_up), _iptr(occ_dn),
-                             _dptr(ci), st, C.byref(self._h))
-        if s != 0:
-            raise AfqmcError(s, lib.afqmc_last_error(None).decode())
 
     @classmethod
     def from_system(cls, system, **kw):
@@ -159,6 +207,45 @@ class Afqmc:
         args.update(kw)
         return cls(system.h1, system.L, system.C_up, system.C_dn,
                    system.occ_up, system.occ_dn, system.ci, **args)
+
+    def args(self):
+        """Pointer arguments h1, L, C_up, C_dn, occ_up, occ_dn, ci."""
+        return (_dptr(self.h1), _dptr(self.L), _dptr(self.C_up), _dptr(self.C_dn),
+                _iptr(self.occ_up), _iptr(self.occ_dn), _dptr(self.ci))
+
+
+def afqmc_footprint(inputs: "Inputs"):
+    """(resident, setup_peak) device bytes of a context (host-only call)."""
+    lib = load_library()
+    r = C.c_size_t()
+    sp = C.c_size_t()
+    s = lib.afqmc_footprint(C.byref(inputs.params), _iptr(inputs.occ_up),
+                            _iptr(inputs.occ_dn), C.byref(r), C.byref(sp))
+    if s != 0:
+        raise AfqmcError(s, lib.afqmc_last_error(None).decode())
+    return r.value, sp.value
+
+
+class Afqmc:
+    """One ph-AFQMC context (a population of walkers of one system)."""
+
+    def __init__(self, *args, stream=None, **kw):
+        lib = load_library()
+        self._lib = lib
+        self._h = C.c_void_p()
+        inp = args[0] if len(args) == 1 and isinstance(args[0], Inputs) else Inputs(*args, **kw)
+        p = inp.params
+        self.params = p
+        self.M, self.n_up, self.n_dn = p.M, p.n_up, p.n_dn
+        self.n_chol, self.n_walkers = p.n_chol, p.n_walkers
+        st = C.c_void_p(stream) if stream else None
+        s = lib.afqmc_create(C.byref(p), *inp.args(), st, C.byref(self._h))
+        if s != 0:
+            raise AfqmcError(s, lib.afqmc_last_error(None).decode())
+
+    @classmethod
+    def from_system(cls, system, stream=None, **kw):
+        return cls(Inputs.from_system(system, **kw), stream=stream)
 
     # -- helpers ------------------------------------------------------------
     def _check(self, s):
@@ -255,6 +342,24 @@ class Afqmc:
     def afqmc_launch_count(self) -> int:
         return int(self._lib.afqmc_launch_count(self._h))
 
+    def afqmc_get_tuning(self) -> dict:
+        t = afqmc_tuning()
+        self._check(self._lib.afqmc_get_tuning(self._h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in afqmc_tuning._fields_ if f != "reserved"}
+
+    def afqmc_set_tuning(self, **kw):
+        t = afqmc_tuning()
+        self._check(self._lib.afqmc_get_tuning(self._h, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._check(self._lib.afqmc_set_tuning(self._h, C.byref(t)))
+
+    def afqmc_device_bytes(self) -> int:
+        return int(self._lib.afqmc_device_bytes(self._h))
+
+    def afqmc_graph_count(self) -> int:
+        return int(self._lib.afqmc_graph_count(self._h))
+
     # -- views of the state --------------------------------------------------
     def walkers(self):
         """Walker orbitals as complex128 arrays Phi_up [W, M, n_up], Phi_dn [W, M, n_dn],
@@ -308,3 +413,103 @@ def afqmc_comb_static(d_weight: int, n_walkers: int, seed: int, run_id: int,
                               C.c_void_p(stream) if stream else None)
     if s != 0:
         raise AfqmcError(s, lib.afqmc_last_error(None).decode())
+
+
+class Batch:
+    """Several contexts advanced together, one CUDA graph launch per block
+    (afqmc_batch_* in include/afqmc.h). Keeps its members alive."""
+
+    def __init__(self, contexts, steps_per_block):
+        lib = load_library()
+        self._lib = lib
+        self.members = list(contexts)
+        self.steps_per_block = steps_per_block
+        arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        self._h = C.c_void_p()
+        s = lib.afqmc_batch_create(arr, len(self.members), steps_per_block, C.byref(self._h))
+        if s != 0:
+            raise AfqmcError(s, lib.afqmc_last_error(None).decode())
+
+    def _check(self, s):
+        if s != 0:
+            raise AfqmcError(s, self._lib.afqmc_last_error(None).decode())
+
+    def afqmc_batch_propagate(self, n_blocks: int):
+        self._check(self._lib.afqmc_batch_propagate(self._h, n_blocks))
+
+    def afqmc_batch_synchronize(self):
+        self._check(self._lib.afqmc_batch_synchronize(self._h))
+
+    def afqmc_batch_launches(self) -> int:
+        return int(self._lib.afqmc_batch_launches(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.afqmc_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (afqmc_server_* in include/afqmc.h): submit runs, poll
+    their per-block results, read latency statistics."""
+
+    def __init__(self, hbm_budget=0, max_active=0, device=0):
+        lib = load_library()
+        self._lib = lib
+        cfg = afqmc_server_config()
+        cfg.hbm_budget = hbm_budget
+        cfg.max_active = max_active
+        cfg.device = device
+        self._h = C.c_void_p()
+        s = lib.afqmc_server_create(C.byref(cfg), C.byref(self._h))
+        if s != 0:
+            raise AfqmcError(s, lib.afqmc_last_error(None).decode())
+
+    def _check(self, s):
+        if s != 0:
+            raise AfqmcError(s, self._lib.afqmc_last_error(None).decode())
+
+    def afqmc_server_submit(self, inputs: Inputs, n_blocks: int, steps_per_block: int) -> int:
+        rid = C.c_int64()
+        self._check(self._lib.afqmc_server_submit(self._h, C.byref(inputs.params),
+                                                  *inputs.args(), n_blocks,
+                                                  steps_per_block, C.byref(rid)))
+        return rid.value
+
+    def afqmc_server_poll(self, run_id: int):
+        info = afqmc_run_info()
+        self._check(self._lib.afqmc_server_poll(self._h, run_id, C.byref(info), None, 0))
+        n = info.blocks_done
+        blocks = (afqmc_block_result * max(n, 1))()
+        self._check(self._lib.afqmc_server_poll(self._h, run_id, C.byref(info), blocks, n))
+        out = {f: getattr(info, f) for f, _ in afqmc_run_info._fields_}
+        out["state"] = RUN_STATES[info.state]
+        out["message"] = info.message.decode(errors="replace")
+        out["blocks"] = [{f: getattr(b, f) for f, _ in afqmc_block_result._fields_}
+                         for b in blocks[:n]]
+        return out
+
+    def afqmc_server_wait(self, run_id: int = -1, timeout_s: float = -1.0):
+        self._check(self._lib.afqmc_server_wait(self._h, run_id, timeout_s))
+
+    def afqmc_server_stats(self) -> dict:
+        st = afqmc_server_stats()
+        self._check(self._lib.afqmc_server_stats_get(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in afqmc_server_stats._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.afqmc_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,10 +6,15 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/afqmc.h"
+#include "ctx_internal.h"
 #include "kernels.h"
 #include "multidet.h"
 #include "tc.h"
@@ -21,6 +26,15 @@ namespace {
 struct TimedPair {
   int id;
   cudaEvent_t a, b;
+};
+
+// A captured block of steps: replaying it advances the step counter by its
+// length and the measurement counter by `meas`.
+struct GraphEntry {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  long meas;
+  int64_t launches;
 };
 
 struct StateHeader {
@@ -47,7 +61,8 @@ struct afqmc_ctx {
   bool poisoned;
   int64_t launches;
 
-  // walker state and step intermediates (element type by precision)
+  // walker state and step intermediates (element type by precision); the
+  // buffers never change roles, so a captured graph stays valid
   void *Phi, *Phi2, *Phi3, *Theta, *Theta2, *V, *X, *S, *xbar, *Z;
   // precomputed operators in the step precision
   void *L, *Ltil, *Bhalf, *PsiT, *Yx_up, *Yx_dn;
@@ -55,7 +70,9 @@ struct afqmc_ctx {
   double *weight, *scan, *wnew, *escalar, *lr;
   double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
   int *parent, *status;
+  long long* ctr;   // device step counters: [0] completed steps, [1] measurements
   std::vector<void*> allocs;
+  size_t dev_bytes;
 
   // padded strides (TMA needs 16-byte-aligned rows)
   long ldS;          // S row stride: n_chol rounded up to 4
@@ -63,6 +80,7 @@ struct afqmc_ctx {
   long dn_off, ldt;  // Theta: down block offset and row stride
   long Jp[2];        // Yx / Z row strides per spin
   int xsplit;        // K splits of the force-bias contraction
+  int xsplit_max;    // partial sums the X buffer holds
   void* LT;          // L transposed [M*M][ldS] (tensor-core operand)
   void* dB;          // B_half - I (tensor-core operand)
   void* bimg;        // (B_half - I) operand image for the fused tensor-core Taylor kernel
@@ -72,6 +90,7 @@ struct afqmc_ctx {
   bool ref_only;            // evaluate with the reference determinant alone (E_T)
   const double* ci_h;       // caller's CI coefficients (valid during create only)
   MdTables mdt;
+  void *md_dets, *md_cc, *md_r0, *md_r1, *md_ct0, *md_ct1;
   int nact[2];
   long ldg, gdn_off;        // Gamma / LtilA row layout: up block at 0, down at gdn_off
   void *Gamma, *Gamma2, *LtilA;
@@ -83,6 +102,13 @@ struct afqmc_ctx {
   bool tc_taylor_ok;  // M <= 64: on-chip tensor-core Taylor kernel
   bool tc_bhalf_ok;   // M % 4 == 0: B_half on the tensor cores
   bool split3;
+  bool taylor_fused;  // use the fused tensor-core Taylor kernel
+  int bn_fb, bn_v, bn_e, bn_b;   // tensor-core tile widths per contraction
+
+  // CUDA graphs of blocks of steps, keyed by (phase in the cadence period, length)
+  bool use_graphs;
+  long period;        // steps after which the cadence pattern repeats (0: too long)
+  std::map<std::pair<long, long>, GraphEntry> graphs;
 
   bool timing;
   std::vector<TimedPair> pending;
@@ -100,6 +126,16 @@ thread_local std::string g_create_err;
 namespace afqmc {
 // Error text of calls that have no context (read by afqmc_last_error(NULL)).
 void set_global_error(const std::string& msg) { g_create_err = msg; }
+
+cudaError_t ctx_enqueue_readback(afqmc_ctx* c, double* e2, int* status) {
+  cudaError_t e = cudaMemcpyAsync(e2, c->escalar, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  return e;
+}
+
+long ctx_step(const afqmc_ctx* c) { return c->step; }
 }  // namespace afqmc
 
 namespace {
@@ -140,6 +176,7 @@ afqmc_status dalloc(afqmc_ctx* c, void** p, size_t bytes) {
     return fail(c, AFQMC_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
   c->allocs.push_back(*p);
+  c->dev_bytes += bytes;
   return AFQMC_OK;
 }
 
@@ -227,7 +264,7 @@ afqmc_status force_bias_contraction(afqmc_ctx* c) {
   if (c->tc) {
     LK(tc_gemm(c->tc, c->st, 2 * W, G + 1, (int)ld, (const float*)A, ld, (const float*)B, ld,
                (float*)c->X, c->ldx, 1.0f, 0.0f, nullptr, 0, c->split3, c->xsplit,
-               2L * W * c->ldx, c->status));
+               2L * W * c->ldx, c->status, c->bn_fb));
   } else {
     LK(gemm<T>(c->st, false, true, 2 * W, G + 1, (int)ld, T(1), (const T*)A, ld, 0,
                (const T*)B, ld, 0, T(0), (T*)c->X, c->ldx, 0, 1));
@@ -243,9 +280,8 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
     LK(launch_md_energy<T>(c->st, c->mdt, W, M, c->nu, c->nd, G, (const T*)c->Theta, c->ldt,
                            c->dn_off, c->logdet, (const T*)c->LtilA, c->ldg, c->gdn_off,
                            c->eloc, c->fp64_islands));
-    LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, (double)c->step,
-                           record ? c->hist : nullptr, (int)(c->n_meas % kHist),
-                           c->escalar));
+    LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, c->ctr, record ? c->hist : nullptr,
+                           kHist, c->escalar));
     if (record) c->n_meas += 1;
     return AFQMC_OK;
   }
@@ -264,7 +300,7 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
       if (c->tc) {
         LK(tc_gemm(c->tc, c->st, 2 * W, (int)J, (int)J, (const float*)c->Theta + off, c->ldt,
                    (const float*)Y, ldz, (float*)c->Z + zoff, ldz, 1.0f, 0.0f, nullptr, 0,
-                   c->split3, 1, 0, c->status));
+                   c->split3, 1, 0, c->status, c->bn_e));
       } else {
         LK(gemm<T>(c->st, false, false, 2 * W, (int)J, (int)J, T(1),
                    (const T*)c->Theta + off, c->ldt, 0, Y, ldz, 0, T(0), (T*)c->Z + zoff,
@@ -276,9 +312,8 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
                                c->xsplit, 2L * W * c->ldx, (const T*)c->Theta, c->ldt,
                                c->dn_off, (const T*)c->Z, c->Jp[0], c->Jp[1], c->eloc));
   }
-  LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, (double)c->step,
-                         record ? c->hist : nullptr, (int)(c->n_meas % kHist),
-                         c->escalar));
+  LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, c->ctr, record ? c->hist : nullptr,
+                         kHist, c->escalar));
   if (record) c->n_meas += 1;
   return AFQMC_OK;
 }
@@ -295,21 +330,28 @@ template <typename T>
 afqmc_status comb_T(afqmc_ctx* c) {
   const int W = c->W;
   KTimer t(c, 8);
-  LK(launch_comb(c->st, W, c->weight, c->p.seed, c->p.run_id, c->step, c->parent, c->scan,
+  LK(launch_comb(c->st, W, c->weight, c->p.seed, c->p.run_id, c->ctr, 0, c->parent, c->scan,
                  c->wnew, c->status));
+  // copies of the parents into the second buffers, then back, so that every
+  // buffer keeps its role
   const long pe = (long)c->N * 2 * c->M;
   LK(launch_gather<T>(c->st, W, pe, 2 * c->ldt, c->parent, (const T*)c->Phi, (T*)c->Phi2,
                       (const T*)c->Theta, (T*)c->Theta2, c->logO, c->logO2, c->wnew,
                       c->weight));
-  std::swap(c->Phi, c->Phi2);
-  std::swap(c->Theta, c->Theta2);
-  std::swap(c->logO, c->logO2);
+  const size_t es = sizeof(T);
+  CK(cudaMemcpyAsync(c->Phi, c->Phi2, (size_t)W * pe * es, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->Theta, c->Theta2, (size_t)W * 2 * c->ldt * es,
+                     cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->logO, c->logO2, (size_t)W * sizeof(double2), cudaMemcpyDeviceToDevice,
+                     c->st));
   if (c->md) {
     LK(launch_gather_rows<T>(c->st, W, 2 * c->ldg, c->parent, (const T*)c->Gamma,
                              (T*)c->Gamma2));
     LK(launch_gather_rows<double2>(c->st, W, 2, c->parent, c->logdet, c->logdet2));
-    std::swap(c->Gamma, c->Gamma2);
-    std::swap(c->logdet, c->logdet2);
+    CK(cudaMemcpyAsync(c->Gamma, c->Gamma2, (size_t)W * 2 * c->ldg * es,
+                       cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(c->logdet, c->logdet2, (size_t)W * 2 * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, c->st));
   }
   return AFQMC_OK;
 }
@@ -329,16 +371,52 @@ afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
   return AFQMC_OK;
 }
 
+// K5: out = B_half exp_T(V) B_half Phi. `out` is Phi itself during a step;
+// the tuner points it at scratch to time the path without moving walkers.
+template <typename T>
+afqmc_status propagate_T(afqmc_ctx* c, T* out) {
+  const int W = c->W, N = c->N, M = c->M;
+  const int rows = W * N * 2;
+  if (c->tc && c->taylor_fused) {   // B_half exp(V) B_half in one tensor-core kernel, in place
+    LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
+                 (const float*)c->Phi, (float*)out, (const float*)c->bimg, c->split3,
+                 c->status));
+    return AFQMC_OK;
+  }
+  // Phi2 = B_half Phi
+  if (c->tc && c->tc_bhalf_ok) {
+    LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi, M, (const float*)c->dB, M,
+               (float*)c->Phi2, M, 1.0f, 1.0f, (const float*)c->Phi, M, c->split3, 1, 0,
+               c->status, c->bn_b));
+  } else {
+    LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi, M, 0,
+               (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi2, M, 0, 1));
+  }
+  // Phi3 = exp_T(V) Phi2
+  LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V, (const T*)c->Phi2,
+                      (T*)c->Phi3));
+  // out = B_half Phi3
+  if (c->tc && c->tc_bhalf_ok) {
+    LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi3, M, (const float*)c->dB, M,
+               (float*)out, M, 1.0f, 1.0f, (const float*)c->Phi3, M, c->split3, 1, 0,
+               c->status, c->bn_b));
+  } else {
+    LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi3, M, 0,
+               (const T*)c->Bhalf, M, 0, T(0), out, M, 0, 1));
+  }
+  return AFQMC_OK;
+}
+
 template <typename T>
 afqmc_status step_T(afqmc_ctx* c) {
-  const int W = c->W, N = c->N, M = c->M, G = c->G;
+  const int W = c->W, M = c->M, G = c->G;
   const double dt = c->p.dtau;
   afqmc_status s = force_bias_contraction<T>(c);
   if (s != AFQMC_OK) return s;
   {
     KTimer t(c, 1);
     LK(launch_fields<T>(c->st, W, G, (const T*)c->X, c->ldx, c->xsplit, 2L * W * c->ldx,
-                        sqrt(dt), c->p.fb_cap, c->p.seed, c->p.run_id, c->step, (T*)c->S,
+                        sqrt(dt), c->p.fb_cap, c->p.seed, c->p.run_id, c->ctr, (T*)c->S,
                         c->ldS, (T*)c->xbar, c->lw));
   }
   {
@@ -346,7 +424,7 @@ afqmc_status step_T(afqmc_ctx* c) {
     if (c->tc) {
       LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
                  (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
-                 nullptr, 0, c->split3, 1, 0, c->status));
+                 nullptr, 0, c->split3, 1, 0, c->status, c->bn_v));
     } else {
       LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, c->ldS, 0,
                  (const T*)c->L, (long)M * M, 0, T(0), (T*)c->V, (long)M * M, 0, 1));
@@ -354,35 +432,8 @@ afqmc_status step_T(afqmc_ctx* c) {
   }
   {
     KTimer t(c, 3);
-    const int rows = W * N * 2;
-    if (c->tc && c->tc_taylor_ok) {   // B_half exp(V) B_half in one tensor-core kernel
-      LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
-                   (const float*)c->Phi, (float*)c->Phi3, (const float*)c->bimg, c->split3,
-                   c->status));
-      std::swap(c->Phi, c->Phi3);
-    } else {
-    // Phi2 = B_half Phi
-    if (c->tc && c->tc_bhalf_ok) {
-      LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi, M, (const float*)c->dB, M,
-                 (float*)c->Phi2, M, 1.0f, 1.0f, (const float*)c->Phi, M, c->split3, 1, 0,
-                 c->status));
-    } else {
-      LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi, M, 0,
-                 (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi2, M, 0, 1));
-    }
-    // Phi3 = exp_T(V) Phi2
-    LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V,
-                        (const T*)c->Phi2, (T*)c->Phi3));
-    // Phi = B_half Phi3
-    if (c->tc && c->tc_bhalf_ok) {
-      LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi3, M, (const float*)c->dB, M,
-                 (float*)c->Phi, M, 1.0f, 1.0f, (const float*)c->Phi3, M, c->split3, 1, 0,
-                 c->status));
-    } else {
-      LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi3, M, 0,
-                 (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi, M, 0, 1));
-    }
-    }
+    s = propagate_T<T>(c, (T*)c->Phi);
+    if (s != AFQMC_OK) return s;
   }
   {
     KTimer t(c, 4);
@@ -391,7 +442,8 @@ afqmc_status step_T(afqmc_ctx* c) {
   }
   {
     KTimer t(c, 5);
-    LK(launch_weights(c->st, W, c->logO_new, c->lw, dt, c->e_shift, c->weight, c->logO));
+    LK(launch_weights(c->st, W, c->logO_new, c->lw, dt, c->e_shift, c->weight, c->logO,
+                      c->ctr));
   }
   c->step += 1;
   const long n = c->step;
@@ -414,14 +466,14 @@ afqmc_status step_T(afqmc_ctx* c) {
 // Setup
 // ---------------------------------------------------------------------------
 
-afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
-                      const double* Cu, const double* Cd, const int32_t* ou,
-                      const int32_t* od, const double* ci) {
+// Size and option checks that need no matrix data.
+afqmc_status validate_sizes(const afqmc_params* p) {
   afqmc_ctx* c = nullptr;
-  if (!p || !h1 || !L || !Cu || !Cd || !ou || !od || !ci)
-    return fail(c, AFQMC_E_INVALID, "null argument");
-  for (int i = 0; i < 7; ++i)
+  if (!p) return fail(c, AFQMC_E_INVALID, "null argument");
+  for (int i = 0; i < 5; ++i)
     if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
+  if ((p->graphs != 0 && p->graphs != 1) || (p->autotune != 0 && p->autotune != 1))
+    return fail(c, AFQMC_E_INVALID, "graphs and autotune must be 0 or 1");
   const int M = p->M;
   if (M < 1 || M > 256) return fail(c, AFQMC_E_INVALID, "M must be in 1..256");
   if (p->n_up < 0 || p->n_dn < 0 || p->n_up > M || p->n_dn > M || p->n_up + p->n_dn < 1)
@@ -445,6 +497,18 @@ afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
     return fail(c, AFQMC_E_INVALID,
                 "M x electrons per spin too large for the on-chip overlap and QR in this "
                 "precision");
+  return AFQMC_OK;
+}
+
+afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
+                      const double* Cu, const double* Cd, const int32_t* ou,
+                      const int32_t* od, const double* ci) {
+  afqmc_ctx* c = nullptr;
+  if (!p || !h1 || !L || !Cu || !Cd || !ou || !od || !ci)
+    return fail(c, AFQMC_E_INVALID, "null argument");
+  afqmc_status s0 = validate_sizes(p);
+  if (s0 != AFQMC_OK) return s0;
+  const int M = p->M;
   // symmetry of h1 and L
   double scale = 0.0;
   for (long e = 0; e < (long)M * M; ++e) scale = fmax(scale, fabs(h1[e]));
@@ -714,78 +778,446 @@ afqmc_status prepare_multidet(afqmc_ctx* c, const int32_t* ou, const int32_t* od
   return AFQMC_OK;
 }
 
-afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
-                         const double* Cu, const double* Cd, const int32_t* ou,
-                         const int32_t* od) {
-  const int M = c->M, N = c->N, G = c->G, W = c->W;
-  const size_t es = esize(c);
-  const size_t MM = (size_t)M * M;
-  const size_t phi = (size_t)W * N * 2 * M;
-  const bool tcmode = c->p.precision == AFQMC_TF32 || c->p.precision == AFQMC_TF32X3;
-  c->ldS = round4(G);
-  c->ldx = G + 1;
-  c->dn_off = round4((long)c->nu * M);
-  c->ldt = c->dn_off + round4((long)c->nd * M);
-  c->Jp[0] = round4((long)c->nu * M);
-  c->Jp[1] = round4((long)c->nd * M);
-  c->xsplit = 1;
-  c->split3 = c->p.precision == AFQMC_TF32X3;
-  c->tc_taylor_ok = tcmode && M <= 64;
-  c->tc_bhalf_ok = tcmode && M % 4 == 0;
-  if (tcmode) {
+// ---------------------------------------------------------------------------
+// Autotuner: launch shapes of the tensor-core contractions, timed on the
+// context's own operands right after setup (the timed launches write only
+// scratch: X, V, Z and the spare walker buffers), the fastest kept and cached
+// per shape for the rest of the process.
+// ---------------------------------------------------------------------------
+
+struct TuneVal {
+  int xsplit, bn_fb, bn_v, bn_e, bn_b, fused;
+};
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+TuneKey tune_key(const afqmc_ctx* c) {
+  return TuneKey(c->M, c->nu, c->nd, c->G, c->W, c->md ? c->nact[0] : -1,
+                 c->md ? c->nact[1] : -1, c->p.precision, c->p.taylor_order);
+}
+
+// Shortest of three timed runs (after one untimed run) of `f`, in ms;
+// infinity when a launch fails.
+template <typename F>
+float best_ms(afqmc_ctx* c, F f) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return INFINITY;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return INFINITY; }
+  float best = INFINITY;
+  if (f() == AFQMC_OK) {
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(a, c->st);
+      if (f() != AFQMC_OK) { best = INFINITY; break; }
+      cudaEventRecord(b, c->st);
+      if (cudaEventSynchronize(b) != cudaSuccess) { best = INFINITY; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      best = std::min(best, ms);
+    }
+  }
+  cudaStreamSynchronize(c->st);
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+void apply_tune(afqmc_ctx* c, const TuneVal& v) {
+  c->xsplit = v.xsplit;
+  c->bn_fb = v.bn_fb;
+  c->bn_v = v.bn_v;
+  c->bn_e = v.bn_e;
+  c->bn_b = v.bn_b;
+  c->taylor_fused = v.fused != 0;
+}
+
+afqmc_status autotune(afqmc_ctx* c) {
+  const TuneKey key = tune_key(c);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      apply_tune(c, it->second);
+      return AFQMC_OK;
+    }
+  }
+  const int64_t launches0 = c->launches;
+  const std::string err0 = c->err;
+  const int W = c->W, M = c->M, G = c->G;
+  TuneVal v = {c->xsplit, 0, 0, 0, 0, c->taylor_fused ? 1 : 0};
+  const int bns[2] = {64, 128};
+  // force bias: K splits x tile width
+  {
+    const long kdim = (c->md ? c->ldg : c->ldt);
+    const long ktiles = (kdim + 31) / 32;
+    float best = INFINITY;
+    for (int ks = 1; ks <= c->xsplit_max; ++ks) {
+      if (ks > 1 && ktiles / ks < 4) break;
+      for (int bn : bns) {
+        c->xsplit = ks;
+        c->bn_fb = bn;
+        const float ms = best_ms(c, [&]() { return force_bias_contraction<float>(c); });
+        if (ms < best) { best = ms; v.xsplit = ks; v.bn_fb = bn; }
+      }
+    }
+  }
+  // one-body operator
+  {
+    float best = INFINITY;
+    for (int bn : bns) {
+      const float ms = best_ms(c, [&]() -> afqmc_status {
+        LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
+                   (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
+                   nullptr, 0, c->split3, 1, 0, c->status, bn));
+        return AFQMC_OK;
+      });
+      if (ms < best) { best = ms; v.bn_v = bn; }
+    }
+  }
+  // energy contraction (single determinant)
+  if (!c->md) {
+    float best = INFINITY;
+    for (int bn : bns) {
+      const float ms = best_ms(c, [&]() -> afqmc_status {
+        long zoff = 0;
+        for (int sig = 0; sig < 2; ++sig) {
+          const int ns = sig ? c->nd : c->nu;
+          const long off = sig ? c->dn_off : 0, ldz = c->Jp[sig];
+          if (ns == 0) continue;
+          const long J = (long)ns * M;
+          LK(tc_gemm(c->tc, c->st, 2 * W, (int)J, (int)J, (const float*)c->Theta + off,
+                     c->ldt, (const float*)(sig ? c->Yx_dn : c->Yx_up), ldz,
+                     (float*)c->Z + zoff, ldz, 1.0f, 0.0f, nullptr, 0, c->split3, 1, 0,
+                     c->status, bn));
+          zoff += 2L * W * ldz;
+        }
+        return AFQMC_OK;
+      });
+      if (ms < best) { best = ms; v.bn_e = bn; }
+    }
+  }
+  // propagation path (into the spare walker buffer Phi2)
+  {
+    float best = INFINITY;
+    for (int fused = c->tc_taylor_ok ? 1 : 0; fused >= 0; --fused) {
+      c->taylor_fused = fused != 0;
+      for (int bn : bns) {
+        if (fused && bn != bns[0]) continue;        // no half-step contraction
+        if (!fused && (!c->tc_bhalf_ok || M <= 64) && bn != bns[0]) continue;
+        c->bn_b = bn;
+        const float ms = best_ms(c, [&]() { return propagate_T<float>(c, (float*)c->Phi2); });
+        if (ms < best) { best = ms; v.fused = fused; v.bn_b = fused ? 0 : bn; }
+      }
+    }
+  }
+  apply_tune(c, v);
+  c->launches = launches0;
+  c->err = err0;
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+  CK(cudaStreamSynchronize(c->st));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.emplace(key, v);
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of blocks of steps. The cadence pattern of steps s+1 .. s+len
+// depends only on s modulo the period (the lcm of the cadences), so a block
+// captured at one phase replays at every later step with that phase.
+// ---------------------------------------------------------------------------
+
+long cadence_period(const afqmc_params* p) {
+  long P = 1;
+  const int ks[3] = {p->ortho_every, p->measure_every, p->pc_every};
+  for (int k : ks) {
+    if (k <= 0) continue;
+    long a = P, b = k;
+    while (b) { long t = a % b; a = b; b = t; }
+    P = P / a * k;
+    if (P > 4096) return 0;
+  }
+  return P;
+}
+
+void drop_graphs(afqmc_ctx* c) {
+  for (auto& kv : c->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
+  c->graphs.clear();
+}
+
+afqmc_status step_any(afqmc_ctx* c) { return c->fp64 ? step_T<double>(c) : step_T<float>(c); }
+
+// Capture `len` steps from the current phase. Host counters are left as
+// they were. Returns AFQMC_E_STATE (with graphs switched off for the
+// context, and no error recorded) when the stream cannot be captured.
+afqmc_status capture_block(afqmc_ctx* c, long len, GraphEntry* ge) {
+  const long step0 = c->step, meas0 = c->n_meas;
+  const int64_t l0 = c->launches;
+  const std::string err0 = c->err;
+  if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->use_graphs = false;
+    return AFQMC_E_STATE;
+  }
+  afqmc_status s = AFQMC_OK;
+  for (long i = 0; i < len && s == AFQMC_OK; ++i) s = step_any(c);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  ge->meas = c->n_meas - meas0;
+  ge->launches = c->launches - l0;
+  c->step = step0;
+  c->n_meas = meas0;
+  c->launches = l0;
+  cudaGraphExec_t ex = nullptr;
+  if (s == AFQMC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (s != AFQMC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c->poisoned = false;
+    c->err = err0;
+    c->use_graphs = false;
+    return AFQMC_E_STATE;
+  }
+  ge->graph = g;
+  ge->exec = ex;
+  return AFQMC_OK;
+}
+
+afqmc_status block_graph(afqmc_ctx* c, long len, GraphEntry** out) {
+  const std::pair<long, long> key(c->step % c->period, len);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    GraphEntry ge;
+    afqmc_status s = capture_block(c, len, &ge);
+    if (s != AFQMC_OK) return s;
+    it = c->graphs.emplace(key, ge).first;
+  }
+  *out = &it->second;
+  return AFQMC_OK;
+}
+
+void advance_host(afqmc_ctx* c, long len, const GraphEntry* ge) {
+  c->step += len;
+  c->n_meas += ge->meas;
+  c->launches += ge->launches;
+}
+
+// Strides, paths and sizes of a context, from its parameters alone (and the
+// active-orbital counts of a multi-determinant trial).
+struct Plan {
+  int M, nu, nd, N, G, W, ndet, nact[2];
+  bool fp64, tcmode, split3, md, tc_taylor_ok, tc_bhalf_ok;
+  size_t es;
+  long ldS, ldx, dn_off, ldt, Jp[2], gdn_off, ldg;
+  int xsplit, xsplit_max;
+};
+
+Plan make_plan(const afqmc_params* p, int nact_up, int nact_dn) {
+  Plan P;
+  P.M = p->M; P.nu = p->n_up; P.nd = p->n_dn; P.N = P.nu + P.nd; P.G = p->n_chol;
+  P.W = p->n_walkers; P.ndet = p->n_det;
+  P.md = P.ndet > 1;
+  P.nact[0] = P.md ? nact_up : P.nu;
+  P.nact[1] = P.md ? nact_dn : P.nd;
+  P.fp64 = p->precision == AFQMC_FP64;
+  P.tcmode = p->precision == AFQMC_TF32 || p->precision == AFQMC_TF32X3;
+  P.split3 = p->precision == AFQMC_TF32X3;
+  P.tc_taylor_ok = P.tcmode && P.M <= 64;
+  P.tc_bhalf_ok = P.tcmode && P.M % 4 == 0;
+  P.es = P.fp64 ? sizeof(double) : sizeof(float);
+  const int M = P.M, G = P.G, W = P.W;
+  P.ldS = round4(G);
+  P.ldx = G + 1;
+  P.dn_off = round4((long)P.nu * M);
+  P.ldt = P.dn_off + round4((long)P.nd * M);
+  P.Jp[0] = round4((long)P.nu * M);
+  P.Jp[1] = round4((long)P.nd * M);
+  P.gdn_off = round4((long)P.nact[0] * M);
+  P.ldg = P.gdn_off + round4((long)P.nact[1] * M);
+  P.xsplit = 1;
+  P.xsplit_max = 1;
+  if (P.tcmode) {
     // split K of the force-bias contraction so that its few output tiles
     // still fill the GPU; partial sums are added in order by the consumers
+    const long kdim = P.md ? P.ldg : P.ldt;
     const long tiles = ((2L * W + 127) / 128) * ((G + 1 + 127) / 128);
-    const long ktiles = (c->ldt + 31) / 32;
+    const long ktiles = (kdim + 31) / 32;
     int ks = (int)(152 / (tiles > 0 ? tiles : 1));
     if (ks > 8) ks = 8;
     while (ks > 1 && ktiles / ks < 4) --ks;
-    c->xsplit = ks < 1 ? 1 : ks;
+    P.xsplit = ks < 1 ? 1 : ks;
+    long mx = ktiles / 4;
+    if (mx > 8) mx = 8;
+    P.xsplit_max = (int)std::max<long>(mx, P.xsplit);
   }
+  return P;
+}
+
+struct Buf {
+  void** slot;
+  size_t bytes;
+};
+
+// Every device buffer of a context (slots into c), in allocation order.
+std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
+  const size_t es = P.es, W = P.W, M = P.M, N = P.N, G = P.G;
+  const size_t MM = M * M, phi = W * N * 2 * M;
+  std::vector<Buf> b;
+  auto add = [&](void* slot, size_t bytes) { b.push_back({(void**)slot, bytes ? bytes : 16}); };
+  if (P.md) {
+    add(&c->Gamma, W * 2 * P.ldg * es);
+    add(&c->Gamma2, W * 2 * P.ldg * es);
+    add(&c->LtilA, (G + 1) * P.ldg * es);
+    add(&c->CactT64, (size_t)(P.nact[0] + P.nact[1]) * M * sizeof(double));
+    add(&c->md_ct0, (size_t)P.nact[0] * M * es);
+    add(&c->md_ct1, (size_t)P.nact[1] * M * es);
+    add(&c->md_dets, sizeof(MdDet) * P.ndet);
+    add(&c->md_cc, sizeof(double2) * P.ndet);
+    add(&c->md_r0, sizeof(int) * (P.nu + 1));
+    add(&c->md_r1, sizeof(int) * (P.nd + 1));
+  }
+  add(&c->Phi, phi * es);
+  add(&c->Phi2, phi * es);
+  add(&c->Phi3, phi * es);
+  add(&c->Theta, W * 2 * P.ldt * es);
+  add(&c->Theta2, W * 2 * P.ldt * es);
+  add(&c->V, W * 2 * MM * es);
+  add(&c->X, (size_t)P.xsplit_max * W * 2 * P.ldx * es);
+  add(&c->S, W * 2 * P.ldS * es);
+  add(&c->xbar, W * 2 * G * es);
+  add(&c->Z, 2 * W * (P.Jp[0] + P.Jp[1]) * es);
+  add(&c->L, G * MM * es);
+  add(&c->Ltil, (G + 1) * P.ldt * es);
+  add(&c->Bhalf, MM * es);
+  add(&c->PsiT, N * M * es);
+  add(&c->PsiT64, N * M * sizeof(double));
+  add(&c->Yx_up, (size_t)P.nu * M * P.Jp[0] * es);
+  add(&c->Yx_dn, (size_t)P.nd * M * P.Jp[1] * es);
+  if (P.tcmode) {
+    add(&c->LT, MM * P.ldS * es);
+    add(&c->dB, MM * es);
+    if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_floats(P.split3) * sizeof(float));
+  }
+  add(&c->weight, W * sizeof(double));
+  add(&c->scan, W * sizeof(double));
+  add(&c->lr, 2 * W * sizeof(double));
+  add(&c->wnew, sizeof(double));
+  add(&c->escalar, 2 * sizeof(double));
+  add(&c->logO, W * sizeof(double2));
+  add(&c->logO2, W * sizeof(double2));
+  add(&c->logO_new, W * sizeof(double2));
+  add(&c->logdet, 2 * W * sizeof(double2));
+  add(&c->logdet2, 2 * W * sizeof(double2));
+  add(&c->lw, W * sizeof(double2));
+  add(&c->eloc, W * sizeof(double2));
+  add(&c->hist, kHist * sizeof(double2));
+  add(&c->parent, W * sizeof(int));
+  add(&c->status, sizeof(int));
+  add(&c->ctr, 2 * sizeof(long long));
+  return b;
+}
+
+// FP64 staging held by setup_T (all of it until setup ends).
+size_t setup_bytes(const Plan& P) {
+  const size_t M = P.M, N = P.N, G = P.G, MM = M * M;
+  size_t n = 0;
+  auto add = [&](size_t k) { n += (k ? k : 1) * sizeof(double); };
+  add(MM); add(G * MM); add(N * M); add(MM); add(MM);
+  add((G + 1) * N * M); add(MM); add(MM); add(MM); add(MM);
+  add((G + 1) * P.ldt);
+  for (int sig = 0; sig < 2; ++sig) {
+    const size_t ns = sig ? P.nd : P.nu;
+    if (ns == 0) continue;
+    const size_t J = ns * M;
+    add(J * J);
+    add(J * J);
+  }
+  if (P.tcmode) add(MM * P.ldS);
+  if (P.md) add((G + 1) * P.ldg);
+  return n;
+}
+
+// Active-orbital counts of a multi-determinant trial (reference orbitals
+// plus every other orbital occupied by some determinant), per spin.
+void count_active(const afqmc_params* p, const int32_t* ou, const int32_t* od, int* nact) {
+  for (int sg = 0; sg < 2; ++sg) {
+    const int ns = sg ? p->n_dn : p->n_up;
+    const int32_t* occ = sg ? od : ou;
+    std::vector<char> used(p->M, 0);
+    int n = 0;
+    for (long e = 0; e < (long)p->n_det * ns; ++e) {
+      const int o = occ[e];
+      if (o >= 0 && o < p->M && !used[o]) { used[o] = 1; ++n; }
+    }
+    nact[sg] = n;
+  }
+}
+
+afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
+                         const double* Cu, const double* Cd, const int32_t* ou,
+                         const int32_t* od) {
+  const int M = c->M;
   c->md = c->ndet > 1;
   c->ref_only = false;
   std::vector<MdDet> dets_h;
   std::vector<double2> cconj_h;
   c->nact[0] = c->nu;
   c->nact[1] = c->nd;
-  c->Gamma = c->Gamma2 = c->LtilA = nullptr;
-  c->CactT64 = nullptr;
   if (c->md) {
     afqmc_status s0 = prepare_multidet(c, ou, od, c->ci_h, dets_h, cconj_h);
     if (s0 != AFQMC_OK) return s0;
   }
-  c->gdn_off = round4((long)c->nact[0] * M);
-  c->ldg = c->gdn_off + round4((long)c->nact[1] * M);
+  const Plan P = make_plan(&c->p, c->nact[0], c->nact[1]);
+  c->ldS = P.ldS;
+  c->ldx = P.ldx;
+  c->dn_off = P.dn_off;
+  c->ldt = P.ldt;
+  c->Jp[0] = P.Jp[0];
+  c->Jp[1] = P.Jp[1];
+  c->gdn_off = P.gdn_off;
+  c->ldg = P.ldg;
+  c->xsplit = P.xsplit;
+  c->xsplit_max = P.xsplit_max;
+  c->split3 = P.split3;
+  c->tc_taylor_ok = P.tc_taylor_ok;
+  c->tc_bhalf_ok = P.tc_bhalf_ok;
+  c->taylor_fused = P.tc_taylor_ok;
+  c->bn_fb = c->bn_v = c->bn_e = c->bn_b = 0;
   if (c->md) {
     const bool f64c = c->fp64_islands;
     if (md_energy_smem(M, c->nu, c->nd, c->nact[0], c->nact[1], c->ndet, f64c) > 227 * 1024)
       return fail(c, AFQMC_E_INVALID,
                   "multi-determinant trial too large for the on-chip energy kernel");
-    DALLOC(c->Gamma, (size_t)W * 2 * c->ldg * es);
-    DALLOC(c->Gamma2, (size_t)W * 2 * c->ldg * es);
-    DALLOC(c->LtilA, (size_t)(G + 1) * c->ldg * es);
-    DALLOC(c->CactT64, (size_t)(c->nact[0] + c->nact[1]) * M * sizeof(double));
-    void *ct0, *ct1, *dt, *cc, *r0, *r1;
-    DALLOC(ct0, (size_t)c->nact[0] * M * es);
-    DALLOC(ct1, (size_t)c->nact[1] * M * es);
-    DALLOC(dt, sizeof(MdDet) * c->ndet);
-    DALLOC(cc, sizeof(double2) * c->ndet);
-    DALLOC(r0, sizeof(int) * (c->nu + 1));
-    DALLOC(r1, sizeof(int) * (c->nd + 1));
+  }
+  for (const Buf& b : buffer_list(c, P)) {
+    afqmc_status s0 = dalloc(c, b.slot, b.bytes);
+    if (s0 != AFQMC_OK) return s0;
+  }
+  const size_t es = P.es;
+  const int W = c->W, G = c->G;
+  if (c->md) {
     std::vector<int> ract_u(c->nu + 1), ract_d(c->nd + 1);
     for (int a = 0; a <= c->nu; ++a) ract_u[a] = a;
     for (int a = 0; a <= c->nd; ++a) ract_d[a] = a;
-    CK(cudaMemcpyAsync(dt, dets_h.data(), sizeof(MdDet) * c->ndet, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(cc, cconj_h.data(), sizeof(double2) * c->ndet, cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(r0, ract_u.data(), sizeof(int) * (c->nu + 1), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(r1, ract_d.data(), sizeof(int) * (c->nd + 1), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->md_dets, dets_h.data(), sizeof(MdDet) * c->ndet,
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->md_cc, cconj_h.data(), sizeof(double2) * c->ndet,
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->md_r0, ract_u.data(), sizeof(int) * (c->nu + 1),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->md_r1, ract_d.data(), sizeof(int) * (c->nd + 1),
+                       cudaMemcpyHostToDevice, c->st));
     // active orbitals as rows, FP64 copy for read-outs
     std::vector<double> cact((size_t)(c->nact[0] + c->nact[1]) * M);
     for (int sg = 0; sg < 2; ++sg) {
       const double* C = sg ? Cd : Cu;
       const size_t off = sg ? (size_t)c->nact[0] * M : 0;
       for (int q = 0; q < c->nact[sg]; ++q)
-        for (int k = 0; k < M; ++k) cact[off + (size_t)q * M + k] = C[(size_t)k * M + c->act_h[sg][q]];
+        for (int k = 0; k < M; ++k)
+          cact[off + (size_t)q * M + k] = C[(size_t)k * M + c->act_h[sg][q]];
     }
     CK(cudaMemcpyAsync(c->CactT64, cact.data(), cact.size() * sizeof(double),
                        cudaMemcpyHostToDevice, c->st));
@@ -793,61 +1225,23 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     c->mdt.ndet = c->ndet;
     c->mdt.nact[0] = c->nact[0];
     c->mdt.nact[1] = c->nact[1];
-    c->mdt.dets = (const MdDet*)dt;
-    c->mdt.cconj = (const double2*)cc;
-    c->mdt.ract[0] = (const int*)r0;
-    c->mdt.ract[1] = (const int*)r1;
-    c->mdt.CactT[0] = ct0;
-    c->mdt.CactT[1] = ct1;
+    c->mdt.dets = (const MdDet*)c->md_dets;
+    c->mdt.cconj = (const double2*)c->md_cc;
+    c->mdt.ract[0] = (const int*)c->md_r0;
+    c->mdt.ract[1] = (const int*)c->md_r1;
+    c->mdt.CactT[0] = c->md_ct0;
+    c->mdt.CactT[1] = c->md_ct1;
   }
-  DALLOC(c->Phi, phi * es);
-  DALLOC(c->Phi2, phi * es);
-  DALLOC(c->Phi3, phi * es);
-  DALLOC(c->Theta, (size_t)W * 2 * c->ldt * es);
-  DALLOC(c->Theta2, (size_t)W * 2 * c->ldt * es);
-  DALLOC(c->V, (size_t)W * 2 * MM * es);
-  DALLOC(c->X, (size_t)c->xsplit * W * 2 * c->ldx * es);
-  DALLOC(c->S, (size_t)W * 2 * c->ldS * es);
-  DALLOC(c->xbar, (size_t)W * 2 * G * es);
-  DALLOC(c->Z, (size_t)2 * W * (c->Jp[0] + c->Jp[1]) * es);
-  DALLOC(c->L, (size_t)G * MM * es);
-  DALLOC(c->Ltil, (size_t)(G + 1) * c->ldt * es);
-  DALLOC(c->Bhalf, MM * es);
-  DALLOC(c->PsiT, (size_t)N * M * es);
-  DALLOC(c->PsiT64, (size_t)N * M * sizeof(double));
-  DALLOC(c->Yx_up, (size_t)c->nu * M * c->Jp[0] * es);
-  DALLOC(c->Yx_dn, (size_t)c->nd * M * c->Jp[1] * es);
-  c->LT = nullptr;
-  c->dB = nullptr;
-  c->bimg = nullptr;
-  if (tcmode) {
-    DALLOC(c->LT, MM * c->ldS * es);
-    DALLOC(c->dB, MM * es);
-    if (c->tc_taylor_ok) DALLOC(c->bimg, tc_bhalf_image_floats(c->split3) * sizeof(float));
-  }
-  DALLOC(c->weight, W * sizeof(double));
-  DALLOC(c->scan, W * sizeof(double));
-  DALLOC(c->lr, 2 * W * sizeof(double));
-  DALLOC(c->wnew, sizeof(double));
-  DALLOC(c->escalar, sizeof(double));
-  DALLOC(c->logO, W * sizeof(double2));
-  DALLOC(c->logO2, W * sizeof(double2));
-  DALLOC(c->logO_new, W * sizeof(double2));
-  DALLOC(c->logdet, 2 * W * sizeof(double2));
-  DALLOC(c->logdet2, 2 * W * sizeof(double2));
-  DALLOC(c->lw, W * sizeof(double2));
-  DALLOC(c->eloc, W * sizeof(double2));
-  DALLOC(c->hist, kHist * sizeof(double2));
-  DALLOC(c->parent, W * sizeof(int));
-  DALLOC(c->status, sizeof(int));
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+  CK(cudaMemsetAsync(c->ctr, 0, 2 * sizeof(long long), c->st));
   CK(cudaMemsetAsync(c->lw, 0, W * sizeof(double2), c->st));
   CK(cudaMemsetAsync(c->xbar, 0, (size_t)W * 2 * G * es, c->st));
   CK(cudaMemsetAsync(c->S, 0, (size_t)W * 2 * c->ldS * es, c->st));
+  CK(cudaMemsetAsync(c->V, 0, (size_t)W * 2 * M * M * es, c->st));
   CK(cudaMemsetAsync(c->Theta, 0, (size_t)W * 2 * c->ldt * es, c->st));
   CK(cudaMemsetAsync(c->Theta2, 0, (size_t)W * 2 * c->ldt * es, c->st));
-  CK(cudaMemsetAsync(c->X, 0, (size_t)c->xsplit * W * 2 * c->ldx * es, c->st));
-  if (tcmode) {
+  CK(cudaMemsetAsync(c->X, 0, (size_t)c->xsplit_max * W * 2 * c->ldx * es, c->st));
+  if (P.tcmode) {
     cudaError_t e = tc_create(&c->tc);
     if (e != cudaSuccess)
       return fail(c, AFQMC_E_CUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
@@ -855,6 +1249,10 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   afqmc_status s = c->fp64 ? setup_T<double>(c, h1, L, Cu, Cd, ou, od)
                            : setup_T<float>(c, h1, L, Cu, Cd, ou, od);
   if (s != AFQMC_OK) return s;
+  if (c->tc && c->p.autotune) {
+    s = autotune(c);
+    if (s != AFQMC_OK) return s;
+  }
   CK(cudaStreamSynchronize(c->st));
   return AFQMC_OK;
 }
@@ -880,6 +1278,8 @@ void afqmc_params_default(afqmc_params* p) {
   p->ortho_every = 2;
   p->measure_every = 20;
   p->pc_every = 20;
+  p->graphs = 1;
+  p->autotune = 1;
 }
 
 afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const double* L,
@@ -906,8 +1306,11 @@ afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const do
   c->n_meas = 0;
   c->poisoned = false;
   c->launches = 0;
+  c->dev_bytes = 0;
   c->timing = false;
   c->tc = nullptr;
+  c->use_graphs = params->graphs != 0;
+  c->period = cadence_period(params);
   for (int i = 0; i < AFQMC_N_KERNEL_IDS; ++i) { c->k_launch[i] = 0; c->k_ms[i] = 0.0; }
   if (stream) {
     c->st = (cudaStream_t)stream;
@@ -935,8 +1338,23 @@ afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const do
 afqmc_status afqmc_propagate(afqmc_ctx* c, int32_t n_steps) {
   GUARD(c);
   if (n_steps < 0) return fail(c, AFQMC_E_INVALID, "n_steps < 0");
-  for (int i = 0; i < n_steps; ++i) {
-    afqmc_status s = c->fp64 ? step_T<double>(c) : step_T<float>(c);
+  long n = n_steps;
+  // whole periods as graph replays (at least ~32 steps per replay when the
+  // period is short), the remainder as plain launches
+  while (c->use_graphs && !c->timing && c->period > 0 && n >= c->period) {
+    const long per = c->period;
+    long k = std::min(n / per, std::max(1L, 32 / per));
+    const long len = k * per;
+    GraphEntry* ge = nullptr;
+    afqmc_status s = block_graph(c, len, &ge);
+    if (s == AFQMC_E_STATE) break;   // not capturable: plain launches
+    if (s != AFQMC_OK) return s;
+    CK(cudaGraphLaunch(ge->exec, c->st));
+    advance_host(c, len, ge);
+    n -= len;
+  }
+  for (long i = 0; i < n; ++i) {
+    afqmc_status s = step_any(c);
     if (s != AFQMC_OK) return s;
   }
   return AFQMC_OK;
@@ -1146,6 +1564,8 @@ afqmc_status afqmc_set_state(afqmc_ctx* c, const void* buf, size_t bytes) {
   CK(cudaMemcpyAsync(c->weight, wt, W * sizeof(double), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->logO, lo, W * sizeof(double2), cudaMemcpyHostToDevice, c->st));
   c->step = h.step;
+  const long long ctr_h[2] = {(long long)c->step, (long long)c->n_meas};
+  CK(cudaMemcpyAsync(c->ctr, ctr_h, sizeof(ctr_h), cudaMemcpyHostToDevice, c->st));
   afqmc_status s = c->fp64 ? overlap_T<double>(c, c->logO_new) : overlap_T<float>(c, c->logO_new);
   if (s != AFQMC_OK) return s;
   CK(cudaStreamSynchronize(c->st));
@@ -1221,6 +1641,78 @@ afqmc_status afqmc_kernel_stats(afqmc_ctx* c, int32_t id, int64_t* launches, dou
 
 int64_t afqmc_launch_count(const afqmc_ctx* c) { return c ? c->launches : 0; }
 
+afqmc_status afqmc_get_tuning(afqmc_ctx* c, afqmc_tuning* out) {
+  GUARD(c);
+  if (!out) return fail(c, AFQMC_E_INVALID, "out is NULL");
+  memset(out, 0, sizeof(*out));
+  out->xsplit = c->xsplit;
+  if (c->tc) {
+    out->bn_force_bias = c->bn_fb ? c->bn_fb : (c->G + 1 <= 64 ? 64 : 128);
+    out->bn_one_body = c->bn_v ? c->bn_v : (c->M * c->M <= 64 ? 64 : 128);
+    long jmax = (long)std::max(c->nu, c->nd) * c->M;
+    out->bn_energy = c->bn_e ? c->bn_e : (jmax <= 64 ? 64 : 128);
+    out->bn_half_step = c->bn_b ? c->bn_b : (c->M <= 64 ? 64 : 128);
+    out->taylor_fused = c->taylor_fused ? 1 : 0;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_tuning(afqmc_ctx* c, const afqmc_tuning* t) {
+  GUARD(c);
+  if (!t) return fail(c, AFQMC_E_INVALID, "tuning is NULL");
+  if (t->reserved[0] || t->reserved[1]) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
+  if (!c->tc) {
+    if (t->xsplit != 1 || t->bn_force_bias || t->bn_one_body || t->bn_energy ||
+        t->bn_half_step || t->taylor_fused)
+      return fail(c, AFQMC_E_INVALID, "launch shapes apply to the tensor-core modes only");
+    return AFQMC_OK;
+  }
+  auto bn_ok = [](int b) { return b == 64 || b == 128; };
+  if (t->xsplit < 1 || t->xsplit > c->xsplit_max)
+    return fail(c, AFQMC_E_INVALID,
+                "xsplit must be in 1.." + std::to_string(c->xsplit_max) + " for this system");
+  if (!bn_ok(t->bn_force_bias) || !bn_ok(t->bn_one_body) || !bn_ok(t->bn_energy) ||
+      !bn_ok(t->bn_half_step))
+    return fail(c, AFQMC_E_INVALID, "tile widths must be 64 or 128");
+  if (t->taylor_fused != 0 && t->taylor_fused != 1)
+    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0 or 1");
+  if (t->taylor_fused && !c->tc_taylor_ok)
+    return fail(c, AFQMC_E_INVALID, "the fused Taylor kernel needs M <= 64");
+  CK(cudaStreamSynchronize(c->st));
+  drop_graphs(c);
+  apply_tune(c, TuneVal{t->xsplit, t->bn_force_bias, t->bn_one_body, t->bn_energy,
+                        t->bn_half_step, t->taylor_fused});
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_footprint(const afqmc_params* p, const int32_t* occ_up,
+                             const int32_t* occ_dn, size_t* resident, size_t* setup_peak) {
+  g_create_err.clear();
+  afqmc_status s = validate_sizes(p);
+  if (s != AFQMC_OK) return s;
+  int nact[2] = {p->n_up, p->n_dn};
+  if (p->n_det > 1) {
+    if (!occ_up || !occ_dn)
+      return fail(nullptr, AFQMC_E_INVALID, "a multi-determinant footprint needs the occupations");
+    count_active(p, occ_up, occ_dn, nact);
+    const bool f64c = p->precision == AFQMC_FP64 || p->fp64_islands;
+    if (md_energy_smem(p->M, p->n_up, p->n_dn, nact[0], nact[1], p->n_det, f64c) > 227 * 1024)
+      return fail(nullptr, AFQMC_E_INVALID,
+                  "multi-determinant trial too large for the on-chip energy kernel");
+  }
+  const Plan P = make_plan(p, nact[0], nact[1]);
+  afqmc_ctx dummy;
+  size_t total = 0;
+  for (const Buf& b : buffer_list(&dummy, P)) total += b.bytes;
+  if (resident) *resident = total;
+  if (setup_peak) *setup_peak = setup_bytes(P);
+  return AFQMC_OK;
+}
+
+size_t afqmc_device_bytes(const afqmc_ctx* c) { return c ? c->dev_bytes : 0; }
+
+int32_t afqmc_graph_count(const afqmc_ctx* c) { return c ? (int32_t)c->graphs.size() : 0; }
+
 const char* afqmc_last_error(const afqmc_ctx* c) {
   if (!c) return g_create_err.c_str();
   return c->err.c_str();
@@ -1231,10 +1723,142 @@ void afqmc_destroy(afqmc_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (auto& t : c->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   for (auto e : c->free_events) cudaEventDestroy(e);
+  drop_graphs(c);
   if (c->tc) tc_destroy(c->tc);
   for (void* p : c->allocs) cudaFree(p);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Multi-system batching: one graph launch per block, one branch per member.
+// ---------------------------------------------------------------------------
+
+struct afqmc_batch {
+  std::vector<afqmc_ctx*> ctx;
+  long spb;
+  cudaStream_t st;
+  cudaEvent_t done;
+  std::vector<cudaEvent_t> ready;
+  // instantiated batch graphs keyed by the members' phases
+  std::map<std::vector<long>, cudaGraphExec_t> execs;
+  int64_t launches;
+};
+
+afqmc_status afqmc_batch_create(afqmc_ctx* const* ctxs, int32_t n, int32_t steps_per_block,
+                                afqmc_batch** out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, AFQMC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || n < 1) return fail(nullptr, AFQMC_E_INVALID, "a batch needs at least one context");
+  if (steps_per_block < 1) return fail(nullptr, AFQMC_E_INVALID, "steps_per_block must be >= 1");
+  for (int i = 0; i < n; ++i) {
+    afqmc_ctx* c = ctxs[i];
+    if (!c) return fail(nullptr, AFQMC_E_INVALID, "NULL context in the batch");
+    if (c->poisoned) return fail(nullptr, AFQMC_E_INVALID, "a member context is poisoned");
+    if (c->period <= 0)
+      return fail(nullptr, AFQMC_E_INVALID, "a member's cadence period exceeds 4096 steps");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(nullptr, AFQMC_E_INVALID, "a context appears twice");
+  }
+  afqmc_batch* b = new afqmc_batch();
+  b->ctx.assign(ctxs, ctxs + n);
+  b->spb = steps_per_block;
+  b->launches = 0;
+  b->st = nullptr;
+  b->done = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ready.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    afqmc_batch_destroy(b);
+    cudaGetLastError();
+    return fail(nullptr, AFQMC_E_CUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_propagate(afqmc_batch* b, int32_t n_blocks) {
+  if (!b) return fail(nullptr, AFQMC_E_INVALID, "batch is NULL");
+  if (n_blocks < 0) return fail(nullptr, AFQMC_E_INVALID, "n_blocks < 0");
+  const size_t n = b->ctx.size();
+  for (int blk = 0; blk < n_blocks; ++blk) {
+    std::vector<long> key(n);
+    std::vector<GraphEntry*> ge(n);
+    for (size_t i = 0; i < n; ++i) {
+      afqmc_ctx* c = b->ctx[i];
+      if (c->poisoned) return fail(nullptr, AFQMC_E_CUDA, "member context poisoned: " + c->err);
+      if (c->timing) return fail(nullptr, AFQMC_E_INVALID, "kernel timing is on for a member");
+      const bool was = c->use_graphs;
+      c->use_graphs = true;
+      afqmc_status s = block_graph(c, b->spb, &ge[i]);
+      c->use_graphs = was && c->use_graphs;
+      if (s == AFQMC_E_STATE)
+        return fail(nullptr, AFQMC_E_CUDA, "a member's block could not be captured");
+      if (s != AFQMC_OK) return fail(nullptr, s, "member " + std::to_string(i) + ": " + c->err);
+      key[i] = c->step % c->period;
+    }
+    auto it = b->execs.find(key);
+    if (it == b->execs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaGraphCreate(&g, 0);
+      for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, ge[i]->graph);
+      }
+      cudaGraphExec_t ex = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, AFQMC_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+      }
+      it = b->execs.emplace(key, ex).first;
+    }
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(b->ready[i], b->ctx[i]->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ready[i], 0);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(it->second, b->st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done, b->st);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i)
+      e = cudaStreamWaitEvent(b->ctx[i]->st, b->done, 0);
+    if (e != cudaSuccess)
+      return fail(nullptr, AFQMC_E_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    b->launches += 1;
+    for (size_t i = 0; i < n; ++i) advance_host(b->ctx[i], b->spb, ge[i]);
+  }
+  return AFQMC_OK;
+}
+
+int64_t afqmc_batch_launches(const afqmc_batch* b) { return b ? b->launches : 0; }
+
+afqmc_status afqmc_batch_synchronize(afqmc_batch* b) {
+  if (!b) return fail(nullptr, AFQMC_E_INVALID, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess)
+    return fail(nullptr, AFQMC_E_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+  for (afqmc_ctx* c : b->ctx) {
+    afqmc_status s = check_status(c);
+    if (s != AFQMC_OK) return fail(nullptr, s, c->err);
+  }
+  return AFQMC_OK;
+}
+
+void afqmc_batch_destroy(afqmc_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (auto& kv : b->execs) cudaGraphExecDestroy(kv.second);
+  for (cudaEvent_t ev : b->ready) cudaEventDestroy(ev);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
 }
 
 }  // extern "C"

@@ -25,14 +25,19 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, T alpha
                  const T* A, long lda, long sA, const T* B, long ldb, long sB,
                  T beta, T* C, long ldc, long sC, int batch);
 
+// Step counters live in device memory, ctr[0] = completed steps and
+// ctr[1] = recorded measurements, so that a block of steps can be captured
+// once as a CUDA graph and replayed: the kernels read the step from there.
+
 // K1 + K3: Philox fields, capped force bias, shifted fields and the log of
-// the importance factor sum_g (x xbar - xbar^2/2) per walker. X holds
-// `nsplit` partial sums (split_stride elements apart) that are added in order.
+// the importance factor sum_g (x xbar - xbar^2/2) per walker, at step
+// ctr[0]. X holds `nsplit` partial sums (split_stride elements apart) that
+// are added in order.
 template <typename T>
 cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
                           int nsplit, long split_stride, double sqdt, double cap,
-                          uint64_t seed, int run_id, long step, T* S, long ldS, T* xbar,
-                          double2* lw);
+                          uint64_t seed, int run_id, const long long* ctr, T* S, long ldS,
+                          T* xbar, double2* lw);
 
 // K5 on the CUDA cores: Phi_out = sum_{n<=order} V^n Phi_in / n!.
 template <typename T>
@@ -49,10 +54,11 @@ cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
                            double2* logdet, double2* Ainv, bool fp64_compute);
 
-// K7: hybrid weight and phaseless cut from the new log-overlap.
+// K7: hybrid weight and phaseless cut from the new log-overlap; ends the
+// step (ctr[0] += 1).
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
                            const double2* lw, double dtau, double e_shift,
-                           double* weight, double2* logO);
+                           double* weight, double2* logO, long long* ctr);
 
 // Sum of the two spins' log-determinants (single-determinant overlap).
 cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,
@@ -76,17 +82,19 @@ cudaError_t launch_energy_reduce(cudaStream_t st, int W, int M, int n_up, int n_
                                  const T* Z, long ldz_up, long ldz_dn, double2* eloc);
 
 // Weighted mixed estimate sum W Re E / sum W (walkers with W > 0) into
-// hist[slot] = (step, value).
+// out[0] and the weight sum into out[1]; with hist, also recorded as
+// hist[ctr[1] % hist_len] = (ctr[0], value) and ctr[1] += 1.
 cudaError_t launch_mixed_energy(cudaStream_t st, int W, const double* weight,
-                                const double2* eloc, double step, double2* hist,
-                                int slot, double* out_scalar);
+                                const double2* eloc, long long* ctr, double2* hist,
+                                int hist_len, double* out);
 
 // K11: blocked FP64 prefix sum and comb; parent[j] per new walker, the new
 // common weight in *wnew; on zero total weight sets bit 1 of *status and
-// leaves parent = identity.
+// leaves parent = identity. The comb's uniform is drawn at step ctr[0], or
+// at `step` when ctr is NULL.
 cudaError_t launch_comb(cudaStream_t st, int W, const double* weight, uint64_t seed,
-                        int run_id, long step, int* parent, double* scratch,
-                        double* wnew, int* status);
+                        int run_id, const long long* ctr, long step, int* parent,
+                        double* scratch, double* wnew, int* status);
 
 // Walker copies after the comb.
 template <typename T>

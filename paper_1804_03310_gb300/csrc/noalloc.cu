@@ -82,8 +82,8 @@ extern "C" afqmc_status afqmc_comb_static(const double* d_weight, int32_t n_walk
   // at zero (the prefix sums are fully rewritten by the kernel).
   e = cudaMemsetAsync(status, 0, sizeof(int), st);
   if (e == cudaSuccess)
-    e = afqmc::launch_comb(st, n_walkers, d_weight, seed, run_id, (long)step, d_parent,
-                           scratch, d_wnew, status);
+    e = afqmc::launch_comb(st, n_walkers, d_weight, seed, run_id, nullptr, (long)step,
+                           d_parent, scratch, d_wnew, status);
   if (e != cudaSuccess)
     return fail(AFQMC_E_CUDA, std::string("afqmc_comb_static: ") + cudaGetErrorString(e));
   return AFQMC_OK;

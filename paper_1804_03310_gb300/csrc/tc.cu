@@ -296,7 +296,7 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint
 template <bool SPLIT3>
 __global__ void __launch_bounds__(128, 1)
 tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
-                 const float* __restrict__ Pin, float* __restrict__ Pout,
+                 const float* Pin, float* Pout,
                  const float* __restrict__ dB_img, int* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -555,10 +555,12 @@ void tc_destroy(TcCtx* t) { delete t; }
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A, long lda,
                     const float* B, long ldb, float* C, long ldc, float alpha, float beta,
                     const float* R, long ldr, bool split3, int ksplit, long split_stride,
-                    int* status) {
+                    int* status, int bn) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ksplit < 1 || (ksplit > 1 && (R || beta != 0.f))) return cudaErrorInvalidValue;
-  if (n <= 64) {
+  if (bn != 0 && bn != 64 && bn != 128) return cudaErrorInvalidValue;
+  if (bn == 0) bn = n <= 64 ? 64 : 128;
+  if (bn == 64) {
     return split3 ? launch_gemm<64, true>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
                                           R, ldr, ksplit, split_stride, status)
                   : launch_gemm<64, false>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha,

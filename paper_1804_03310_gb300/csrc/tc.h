@@ -15,17 +15,20 @@ void tc_destroy(TcCtx* t);
 // A and B are row-major fp32 (K contiguous) with lda, ldb multiples of 4 and
 // 16-byte-aligned bases. split3: three TF32 products (hi*hi + hi*lo + lo*hi)
 // instead of one. ksplit > 1 splits K into that many ranges and writes
-// partial sums to C + s * split_stride (beta must then be 0). A device-side
-// wait that times out sets bit 4 of *status.
+// partial sums to C + s * split_stride (beta must then be 0). bn is the
+// output tile width (64 or 128; 0 picks 64 for n <= 64, else 128). A
+// device-side wait that times out sets bit 4 of *status.
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
                     long lda, const float* B, long ldb, float* C, long ldc, float alpha,
                     float beta, const float* R, long ldr, bool split3, int ksplit,
-                    long split_stride, int* status);
+                    long split_stride, int* status, int bn = 0);
 
 // Taylor propagation of W walkers (M <= 64): Pout = sum_{n<=order} V^n Pin / n!
 // with V [W][2][M][M] and Pin, Pout [W][N][2][M], on the tensor cores. With a
 // half-step image (see tc_bhalf_image) the two half-step factors are applied
-// around the series: Pout = B_half exp_T(V) B_half Pin.
+// around the series: Pout = B_half exp_T(V) B_half Pin. Pout may be Pin:
+// each CTA reads a walker's column chunk completely before writing it, and
+// no other CTA touches that chunk.
 cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
                       const float* V, const float* Pin, float* Pout, const float* bhalf_img,
                       bool split3, int* status);

@@ -57,11 +57,13 @@ struct FieldMath<double> { using type = double; };
 template <typename T>
 __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int nsplit,
                               long split_stride, double sqdt_d, double cap_d, uint32_t k0,
-                              uint32_t k1, int run_id, uint32_t step, T* __restrict__ S,
-                              long ldS, T* __restrict__ xbar, double2* __restrict__ lw) {
+                              uint32_t k1, int run_id, const long long* __restrict__ ctr,
+                              T* __restrict__ S, long ldS, T* __restrict__ xbar,
+                              double2* __restrict__ lw) {
   using C = typename FieldMath<T>::type;
   __shared__ double red[32];
   const int w = blockIdx.x;
+  const uint32_t step = (uint32_t)ctr[0];
   const T* Xr = X + (2L * w) * ldx;
   const T* Xi = Xr + ldx;
   T* Sr = S + (2L * w) * ldS;
@@ -417,8 +419,9 @@ __global__ void logdet_sum_kernel(int W, const double2* __restrict__ ld,
 __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
                                const double2* __restrict__ lw, double dtau,
                                double e_shift, double* __restrict__ weight,
-                               double2* __restrict__ logO) {
+                               double2* __restrict__ logO, long long* __restrict__ ctr) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w == 0) ctr[0] += 1;   // the step is complete once its weights are
   if (w >= W) return;
   double2 ln = logO_new[w];
   double2 lnR = csub(ln, logO[w]);
@@ -571,9 +574,9 @@ __global__ void energy_reduce_kernel(int M, int n_up, int n_dn, int n_chol,
 }
 
 __global__ void mixed_energy_kernel(int W, const double* __restrict__ weight,
-                                    const double2* __restrict__ eloc, double step,
-                                    double2* __restrict__ hist, int slot,
-                                    double* out_scalar) {
+                                    const double2* __restrict__ eloc,
+                                    long long* __restrict__ ctr, double2* __restrict__ hist,
+                                    int hist_len, double* out_scalar) {
   __shared__ double red[32];
   double num = 0.0, den = 0.0;
   for (int w = threadIdx.x; w < W; w += blockDim.x) {
@@ -587,8 +590,12 @@ __global__ void mixed_energy_kernel(int W, const double* __restrict__ weight,
   den = block_sum(den, red);
   if (threadIdx.x == 0) {
     double e = den > 0.0 ? num / den : NAN;
-    if (hist) hist[slot] = make_double2(step, e);
-    if (out_scalar) *out_scalar = e;
+    if (hist) {
+      hist[ctr[1] % hist_len] = make_double2((double)ctr[0], e);
+      ctr[1] += 1;
+    }
+    out_scalar[0] = e;
+    out_scalar[1] = den;
   }
 }
 
@@ -596,7 +603,8 @@ __global__ void mixed_energy_kernel(int W, const double* __restrict__ weight,
 constexpr int kScanBlock = 32;
 
 __global__ void comb_kernel(int W, const double* __restrict__ weight, uint32_t k0,
-                            uint32_t k1, int run_id, uint32_t step,
+                            uint32_t k1, int run_id, const long long* __restrict__ ctr,
+                            long long step_val,
                             int* __restrict__ parent, double* __restrict__ C,
                             double* __restrict__ wnew, int* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
@@ -642,6 +650,7 @@ __global__ void comb_kernel(int W, const double* __restrict__ weight, uint32_t k
     }
     return;
   }
+  const uint32_t step = (uint32_t)(ctr ? ctr[0] : step_val);
   U4 c = {0u, 0u, step, (uint32_t)(4 * run_id + kStreamComb)};
   const double u = open01(philox4x32_10(c, k0, k1).x);
   const double stepw = __ddiv_rn(S, (double)W);
@@ -781,11 +790,11 @@ inline unsigned blocks_for(long n, int t) { return (unsigned)((n + t - 1) / t); 
 template <typename T>
 cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
                           int nsplit, long split_stride, double sqdt, double cap,
-                          uint64_t seed, int run_id, long step, T* S, long ldS, T* xbar,
-                          double2* lw) {
+                          uint64_t seed, int run_id, const long long* ctr, T* S, long ldS,
+                          T* xbar, double2* lw) {
   fields_kernel<T><<<W, 128, 0, st>>>(n_chol, X, ldx, nsplit, split_stride, sqdt, cap,
-                                      (uint32_t)seed, (uint32_t)(seed >> 32), run_id,
-                                      (uint32_t)step, S, ldS, xbar, lw);
+                                      (uint32_t)seed, (uint32_t)(seed >> 32), run_id, ctr,
+                                      S, ldS, xbar, lw);
   return cudaGetLastError();
 }
 
@@ -833,9 +842,9 @@ cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
 
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
                            const double2* lw, double dtau, double e_shift,
-                           double* weight, double2* logO) {
+                           double* weight, double2* logO, long long* ctr) {
   weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, lw, dtau, e_shift,
-                                                     weight, logO);
+                                                     weight, logO, ctr);
   return cudaGetLastError();
 }
 
@@ -880,21 +889,21 @@ cudaError_t launch_energy_reduce(cudaStream_t st, int W, int M, int n_up, int n_
 }
 
 cudaError_t launch_mixed_energy(cudaStream_t st, int W, const double* weight,
-                                const double2* eloc, double step, double2* hist,
-                                int slot, double* out_scalar) {
-  mixed_energy_kernel<<<1, 1024, 0, st>>>(W, weight, eloc, step, hist, slot, out_scalar);
+                                const double2* eloc, long long* ctr, double2* hist,
+                                int hist_len, double* out) {
+  mixed_energy_kernel<<<1, 1024, 0, st>>>(W, weight, eloc, ctr, hist, hist_len, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_comb(cudaStream_t st, int W, const double* weight, uint64_t seed,
-                        int run_id, long step, int* parent, double* scratch,
-                        double* wnew, int* status) {
+                        int run_id, const long long* ctr, long step, int* parent,
+                        double* scratch, double* wnew, int* status) {
   static const size_t smem_cap = allow_big_smem(comb_kernel);
   int nb = (W + kScanBlock - 1) / kScanBlock;
   size_t smem = sizeof(double) * 2 * (size_t)nb;
   if (smem > smem_cap) return cudaErrorInvalidValue;
   comb_kernel<<<1, 1024, smem, st>>>(W, weight, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                     run_id, (uint32_t)step, parent, scratch, wnew,
+                                     run_id, ctr, (long long)step, parent, scratch, wnew,
                                      status);
   return cudaGetLastError();
 }
@@ -981,8 +990,8 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
 
 #define AFQMC_INST(T)                                                                    \
   template cudaError_t launch_fields<T>(cudaStream_t, int, int, const T*, long, int,    \
-                                        long, double, double, uint64_t, int, long, T*,  \
-                                        long, T*, double2*);                            \
+                                        long, double, double, uint64_t, int,            \
+                                        const long long*, T*, long, T*, double2*);      \
   template cudaError_t launch_taylor<T>(cudaStream_t, int, int, int, int, const T*,     \
                                         const T*, T*);                                  \
   template cudaError_t launch_overlap<T>(cudaStream_t, int, int, int, int, const T*,    \

@@ -108,3 +108,65 @@ def test_state_codec_round_trip():
     assert np.array_equal(d["Phi_up"], Pu) and np.array_equal(d["Phi_dn"], Pd)
     assert np.array_equal(d["weight"], w) and np.array_equal(d["logO"], lo)
     assert d["step"] == 7
+
+
+def _inputs(system, **kw):
+    from paper_1804_03310_gb300 import Inputs
+    return Inputs.from_system(system, **kw)
+
+
+def test_footprint_is_host_only_and_grows_with_walkers(lib):
+    from paper_1804_03310_gb300 import afqmc_footprint
+    s = small_system(M=12, n_up=3, n_dn=2, n_chol=7)
+    r1, s1 = afqmc_footprint(_inputs(s.replace(n_walkers=16)))
+    r2, s2 = afqmc_footprint(_inputs(s.replace(n_walkers=32)))
+    r3, _ = afqmc_footprint(_inputs(s.replace(n_walkers=48)))
+    # setup staging does not depend on the walker count; resident memory is
+    # affine in it
+    assert s1 == s2 and s1 > 0
+    assert r2 > r1 and (r3 - r2) == (r2 - r1)
+    # the walker-proportional part holds at least three copies of the
+    # orbitals (propagation buffers) and the one-body operator per walker
+    M, N, G = 12, 5, 7
+    per_walker = (r2 - r1) / 16
+    assert per_walker >= 16 * (3 * N * M + M * M)
+    # the tensor-core modes keep extra operand copies
+    rt, _ = afqmc_footprint(_inputs(s, precision="tf32x3"))
+    rf, _ = afqmc_footprint(_inputs(s, precision="fp32"))
+    assert rt > rf
+
+
+def test_footprint_rejects_what_create_rejects(lib):
+    from paper_1804_03310_gb300 import AfqmcError, afqmc_footprint
+    s = small_system(M=6, n_up=2, n_dn=2, n_chol=3)
+    with pytest.raises(AfqmcError) as e:
+        afqmc_footprint(_inputs(s, taylor_order=0))
+    assert e.value.status == 1
+    inp = _inputs(s)
+    inp.params.graphs = 2
+    with pytest.raises(AfqmcError) as e:
+        afqmc_footprint(inp)
+    assert "graphs" in str(e.value)
+
+
+def test_multidet_footprint_counts_active_orbitals(lib):
+    from paper_1804_03310_gb300 import afqmc_footprint
+    s = small_system(M=12, n_up=3, n_dn=3, n_chol=5, n_det=6, seed=1)
+    r_md, _ = afqmc_footprint(_inputs(s))
+    r_sd, _ = afqmc_footprint(_inputs(s.replace(occ_up=s.occ_up[:1], occ_dn=s.occ_dn[:1],
+                                                ci=s.ci[:1])))
+    assert r_md > r_sd
+
+
+def test_batch_and_server_validate_before_device(lib):
+    from paper_1804_03310_gb300.afqmc import afqmc_server_config
+    out = C.c_void_p()
+    assert lib.afqmc_batch_create(None, 0, 10, C.byref(out)) == 1
+    assert lib.afqmc_batch_propagate(None, 1) == 1
+    cfg = afqmc_server_config()
+    cfg.max_active = 1000
+    assert lib.afqmc_server_create(C.byref(cfg), C.byref(out)) == 1
+    assert b"max_active" in lib.afqmc_last_error(None)
+    cfg.max_active = 4
+    cfg.reserved[0] = 1
+    assert lib.afqmc_server_create(C.byref(cfg), C.byref(out)) == 1
