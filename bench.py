@@ -45,9 +45,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="tf32x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64 GPU comparison run (speed and energy)")
     return ap.parse_args()
 
 
@@ -323,6 +325,73 @@ def run_e2e(args, s):
             "includes": "context creation with setup precompute, host read-back every block"}
 
 
+def fp64_compare(args, s, hist):
+    """The plain FP64 GPU path on the same workload and seed: its
+    walker-steps/s over two timed blocks, the cuBLAS DGEMM rate of this GPU
+    (the FP64 roofline), and the paired difference of the mixed energies
+    recorded at the same steps (both runs draw the same fields)."""
+    import numpy as np
+    import torch
+    from paper_1804_03310_gb300 import Afqmc
+    n_blocks = min(3, args.warmup + args.steps)
+    stream = torch.cuda.Stream()
+    ctx = Afqmc.from_system(s, precision="fp64", stream=stream.cuda_stream)
+    times = []
+    for b in range(n_blocks):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.afqmc_propagate(BLOCK)
+        e.record(stream)
+        e.synchronize()
+        times.append(a.elapsed_time(e))
+    ctx.close()
+    timed = times[1:] if len(times) > 1 else times
+    v64 = s.n_walkers * BLOCK * len(timed) / (sum(timed) / 1e3)
+    # cuBLAS DGEMM on this GPU, the measured FP64 denominator
+    n = 4096
+    x = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    y = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(x, y)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record()
+    reps = 5
+    for _ in range(reps):
+        torch.matmul(x, y)
+    e.record()
+    e.synchronize()
+    dgemm = 2.0 * n ** 3 * reps / (a.elapsed_time(e) / 1e3) / 1e12
+    return {"value": round(v64, 1), "unit": METRIC, "blocks_timed": len(timed),
+            "dgemm_tflops": round(dgemm, 3),
+            "energy_check": energy_check(args.precision)}
+
+
+def energy_check(precision, n_steps=600):
+    """Mixed energies of the plain 10-orbital system (5+5 electrons, 40 dense
+    fields, 512 walkers, dt = 0.01, comb off) in `precision` and on the FP64
+    GPU path with the same seed: walker i of one run is walker i of the
+    other, so the difference, measurement by measurement, is the precision
+    error alone."""
+    import numpy as np
+    from synth import config_c1
+    from paper_1804_03310_gb300 import Afqmc
+    s = config_c1().replace(n_walkers=512, pc_every=0)
+    out = {}
+    for p in ("fp64", precision):
+        with Afqmc.from_system(s, precision=p) as ctx:
+            ctx.afqmc_propagate(n_steps)
+            out[p] = ctx.afqmc_energy_history()[:, 1]
+    d = (out[precision] - out["fp64"]) * 1e3
+    return {"workload": f"{s.name}: M={s.M} N={s.n_up}+{s.n_dn} n_chol={s.n_chol} "
+                        f"W={s.n_walkers} dtau={s.dtau}, {n_steps} steps, shared draws, comb off",
+            "measurements": int(len(d)),
+            "max_abs_mHa": round(float(np.max(np.abs(d))), 6),
+            "mean_mHa": round(float(np.mean(d)), 6)}
+
+
 def dtype_of(precision):
     return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[precision]
 
@@ -362,6 +431,10 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_fp64_compare and world == 1 and args.precision != "fp64":
+        f64 = fp64_compare(args, s, hist)
+        f64["speedup"] = round(value / f64["value"], 2)
+        line["fp64_gpu"] = f64
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,

@@ -203,8 +203,7 @@ int64_t afqmc_launch_count(const afqmc_ctx* ctx);
 
 /* Launch shapes of the tensor-core modes (TF32, TF32X3). Shapes change the
  * numerics only through the order of FP32 sums (split K) and through the
- * Taylor path (one fused tensor-core kernel for B_half exp_T(V) B_half, or
- * the half steps on the tensor cores around the series on the CUDA cores);
+ * propagation path (taylor_fused below);
  * every choice meets the same tolerance against the FP64 path. In the FP64
  * and FP32 modes get returns xsplit 1 and zeros, and set accepts only that. */
 typedef struct {
@@ -213,7 +212,11 @@ typedef struct {
   int32_t bn_one_body;    /*   one-body-operator, energy and half-step */
   int32_t bn_energy;      /*   contractions */
   int32_t bn_half_step;
-  int32_t taylor_fused;   /* 1: fused tensor-core Taylor kernel (M <= 64) */
+  int32_t taylor_fused;   /* propagation path: 0 = series on the CUDA cores,
+                             half steps as contractions; 1 = one fused
+                             tensor-core kernel for B_half exp_T(V) B_half;
+                             2 = series on the tensor cores, half steps as
+                             separate contractions (1 and 2 need M <= 64) */
   int32_t reserved[2];    /* zero */
 } afqmc_tuning;
 afqmc_status afqmc_get_tuning(afqmc_ctx* ctx, afqmc_tuning* out);

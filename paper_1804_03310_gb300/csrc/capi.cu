@@ -70,6 +70,7 @@ struct afqmc_ctx {
   double *weight, *scan, *wnew, *escalar, *lr;
   double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
   int *parent, *status;
+  int* redo;          // [W][2] matrices the FP32 overlap kernel left to FP64
   long long* ctr;   // device step counters: [0] completed steps, [1] measurements
   std::vector<void*> allocs;
   size_t dev_bytes;
@@ -102,7 +103,8 @@ struct afqmc_ctx {
   bool tc_taylor_ok;  // M <= 64: on-chip tensor-core Taylor kernel
   bool tc_bhalf_ok;   // M % 4 == 0: B_half on the tensor cores
   bool split3;
-  bool taylor_fused;  // use the fused tensor-core Taylor kernel
+  int taylor_fused;   // 0: CUDA-core series; 1: fused tensor-core kernel with the
+                      // half steps; 2: tensor-core series, half steps as GEMMs
   int bn_fb, bn_v, bn_e, bn_b;   // tensor-core tile widths per contraction
 
   // CUDA graphs of blocks of steps, keyed by (phase in the cadence period, length)
@@ -360,7 +362,7 @@ template <typename T>
 afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
   LK(launch_overlap<T>(c->st, c->W, c->M, c->nu, c->nd, (const T*)c->Phi,
                        (const T*)c->PsiT, (T*)c->Theta, c->ldt, c->dn_off, c->logdet,
-                       nullptr, c->fp64_islands));
+                       nullptr, c->fp64_islands, c->redo));
   if (c->md) {   // ratios by Sherman-Morrison-Woodbury, ln O_T and Gamma
     LK(launch_md_step<T>(c->st, c->mdt, c->W, c->M, c->nu, c->nd, (const T*)c->Theta, c->ldt,
                          c->dn_off, c->logdet, logO_out, (T*)c->Gamma, c->ldg, c->gdn_off,
@@ -377,7 +379,7 @@ template <typename T>
 afqmc_status propagate_T(afqmc_ctx* c, T* out) {
   const int W = c->W, N = c->N, M = c->M;
   const int rows = W * N * 2;
-  if (c->tc && c->taylor_fused) {   // B_half exp(V) B_half in one tensor-core kernel, in place
+  if (c->tc && c->taylor_fused == 1) {   // B_half exp(V) B_half in one tensor-core kernel, in place
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
                  (const float*)c->Phi, (float*)out, (const float*)c->bimg, c->split3,
                  c->status));
@@ -388,18 +390,33 @@ afqmc_status propagate_T(afqmc_ctx* c, T* out) {
     LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi, M, (const float*)c->dB, M,
                (float*)c->Phi2, M, 1.0f, 1.0f, (const float*)c->Phi, M, c->split3, 1, 0,
                c->status, c->bn_b));
+  } else if (c->dB) {   // Phi + Phi (B_half - I): the identity part exact in FP32
+    CK(cudaMemcpyAsync(c->Phi2, c->Phi, (size_t)rows * M * sizeof(T), cudaMemcpyDeviceToDevice,
+                       c->st));
+    LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi, M, 0,
+               (const T*)c->dB, M, 0, T(1), (T*)c->Phi2, M, 0, 1));
   } else {
     LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi, M, 0,
                (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi2, M, 0, 1));
   }
   // Phi3 = exp_T(V) Phi2
-  LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V, (const T*)c->Phi2,
-                      (T*)c->Phi3));
+  if (c->tc && c->taylor_fused == 2) {
+    LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
+                 (const float*)c->Phi2, (float*)c->Phi3, nullptr, c->split3, c->status));
+  } else {
+    LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V, (const T*)c->Phi2,
+                        (T*)c->Phi3));
+  }
   // out = B_half Phi3
   if (c->tc && c->tc_bhalf_ok) {
     LK(tc_gemm(c->tc, c->st, rows, M, M, (const float*)c->Phi3, M, (const float*)c->dB, M,
                (float*)out, M, 1.0f, 1.0f, (const float*)c->Phi3, M, c->split3, 1, 0,
                c->status, c->bn_b));
+  } else if (c->dB) {
+    CK(cudaMemcpyAsync(out, c->Phi3, (size_t)rows * M * sizeof(T), cudaMemcpyDeviceToDevice,
+                       c->st));
+    LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi3, M, 0,
+               (const T*)c->dB, M, 0, T(1), out, M, 0, 1));
   } else {
     LK(gemm<T>(c->st, false, true, rows, M, M, T(1), (const T*)c->Phi3, M, 0,
                (const T*)c->Bhalf, M, 0, T(0), out, M, 0, 1));
@@ -642,14 +659,16 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   LK(launch_pad_rows(st, G + 1, (long)c->nu * M, (long)c->nd * M, Ltil, Ltil_pad, c->ldt,
                      c->dn_off));
   LK(launch_convert<T>(st, (long)(G + 1) * c->ldt, Ltil_pad, (T*)c->Ltil));
-  if (c->LT) {   // L transposed [M*M][ldS] and B_half - I for the tensor cores
+  if (c->LT) {   // L transposed [M*M][ldS] for the tensor cores
     double *lt;
     TM(lt, MM * c->ldS);
     CK(cudaMemsetAsync(lt, 0, MM * c->ldS * sizeof(double), st));
     LK(launch_transpose(st, G, (long)MM, L, lt, c->ldS));
     LK(launch_convert<T>(st, (long)MM * c->ldS, lt, (T*)c->LT));
+  }
+  if (c->dB) {   // B_half - I: the reduced modes add the identity part exactly
     CK(cudaMemcpyAsync(tb, Bh, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    LK(launch_add_diag(st, M, tb, -1.0));                  // B_half - I
+    LK(launch_add_diag(st, M, tb, -1.0));
     LK(launch_convert<T>(st, MM, tb, (T*)c->dB));
     if (c->bimg)
       LK(tc_bhalf_image(st, M, (const float*)c->dB, (float*)c->bimg, c->split3));
@@ -829,7 +848,7 @@ void apply_tune(afqmc_ctx* c, const TuneVal& v) {
   c->bn_v = v.bn_v;
   c->bn_e = v.bn_e;
   c->bn_b = v.bn_b;
-  c->taylor_fused = v.fused != 0;
+  c->taylor_fused = v.fused;
 }
 
 afqmc_status autotune(afqmc_ctx* c) {
@@ -845,7 +864,7 @@ afqmc_status autotune(afqmc_ctx* c) {
   const int64_t launches0 = c->launches;
   const std::string err0 = c->err;
   const int W = c->W, M = c->M, G = c->G;
-  TuneVal v = {c->xsplit, 0, 0, 0, 0, c->taylor_fused ? 1 : 0};
+  TuneVal v = {c->xsplit, 0, 0, 0, 0, c->taylor_fused};
   const int bns[2] = {64, 128};
   // force bias: K splits x tile width
   {
@@ -900,14 +919,14 @@ afqmc_status autotune(afqmc_ctx* c) {
   // propagation path (into the spare walker buffer Phi2)
   {
     float best = INFINITY;
-    for (int fused = c->tc_taylor_ok ? 1 : 0; fused >= 0; --fused) {
-      c->taylor_fused = fused != 0;
+    for (int fused = c->tc_taylor_ok ? 2 : 0; fused >= 0; --fused) {
+      c->taylor_fused = fused;
       for (int bn : bns) {
-        if (fused && bn != bns[0]) continue;        // no half-step contraction
-        if (!fused && (!c->tc_bhalf_ok || M <= 64) && bn != bns[0]) continue;
+        if (fused == 1 && bn != bns[0]) continue;   // no half-step contraction
+        if (fused != 1 && (!c->tc_bhalf_ok || M <= 64) && bn != bns[0]) continue;
         c->bn_b = bn;
         const float ms = best_ms(c, [&]() { return propagate_T<float>(c, (float*)c->Phi2); });
-        if (ms < best) { best = ms; v.fused = fused; v.bn_b = fused ? 0 : bn; }
+        if (ms < best) { best = ms; v.fused = fused; v.bn_b = fused == 1 ? 0 : bn; }
       }
     }
   }
@@ -1096,11 +1115,9 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->PsiT64, N * M * sizeof(double));
   add(&c->Yx_up, (size_t)P.nu * M * P.Jp[0] * es);
   add(&c->Yx_dn, (size_t)P.nd * M * P.Jp[1] * es);
-  if (P.tcmode) {
-    add(&c->LT, MM * P.ldS * es);
-    add(&c->dB, MM * es);
-    if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_floats(P.split3) * sizeof(float));
-  }
+  if (P.tcmode) add(&c->LT, MM * P.ldS * es);
+  if (!P.fp64) add(&c->dB, MM * es);
+  if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_floats(P.split3) * sizeof(float));
   add(&c->weight, W * sizeof(double));
   add(&c->scan, W * sizeof(double));
   add(&c->lr, 2 * W * sizeof(double));
@@ -1115,6 +1132,7 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->eloc, W * sizeof(double2));
   add(&c->hist, kHist * sizeof(double2));
   add(&c->parent, W * sizeof(int));
+  add(&c->redo, 2 * W * sizeof(int));
   add(&c->status, sizeof(int));
   add(&c->ctr, 2 * sizeof(long long));
   return b;
@@ -1184,7 +1202,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   c->split3 = P.split3;
   c->tc_taylor_ok = P.tc_taylor_ok;
   c->tc_bhalf_ok = P.tc_bhalf_ok;
-  c->taylor_fused = P.tc_taylor_ok;
+  c->taylor_fused = P.tc_taylor_ok ? 1 : 0;
   c->bn_fb = c->bn_v = c->bn_e = c->bn_b = 0;
   if (c->md) {
     const bool f64c = c->fp64_islands;
@@ -1652,7 +1670,7 @@ afqmc_status afqmc_get_tuning(afqmc_ctx* c, afqmc_tuning* out) {
     long jmax = (long)std::max(c->nu, c->nd) * c->M;
     out->bn_energy = c->bn_e ? c->bn_e : (jmax <= 64 ? 64 : 128);
     out->bn_half_step = c->bn_b ? c->bn_b : (c->M <= 64 ? 64 : 128);
-    out->taylor_fused = c->taylor_fused ? 1 : 0;
+    out->taylor_fused = c->taylor_fused;
   }
   return AFQMC_OK;
 }
@@ -1674,10 +1692,10 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* c, const afqmc_tuning* t) {
   if (!bn_ok(t->bn_force_bias) || !bn_ok(t->bn_one_body) || !bn_ok(t->bn_energy) ||
       !bn_ok(t->bn_half_step))
     return fail(c, AFQMC_E_INVALID, "tile widths must be 64 or 128");
-  if (t->taylor_fused != 0 && t->taylor_fused != 1)
-    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0 or 1");
+  if (t->taylor_fused < 0 || t->taylor_fused > 2)
+    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0, 1 or 2");
   if (t->taylor_fused && !c->tc_taylor_ok)
-    return fail(c, AFQMC_E_INVALID, "the fused Taylor kernel needs M <= 64");
+    return fail(c, AFQMC_E_INVALID, "the tensor-core Taylor kernel needs M <= 64");
   CK(cudaStreamSynchronize(c->st));
   drop_graphs(c);
   apply_tune(c, TuneVal{t->xsplit, t->bn_force_bias, t->bn_one_body, t->bn_energy,

@@ -44,15 +44,17 @@ template <typename T>
 cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
                           const T* V, const T* Phi_in, T* Phi_out);
 
-// K6: A = D^H Phi per spin, Gauss-Jordan inverse with partial pivoting
+// K6: A = D^H Phi per spin, inverse by elimination with partial pivoting
 // (FP64 arithmetic when fp64_compute, else FP32), ln det A accumulated in
 // FP64, Theta = Phi A^-1. PsiT [N][M] holds the reference determinant's
 // orbitals as rows (up orbitals then down orbitals). Ainv (optional)
-// [W][2][nmax][nmax] double2 receives A^-1 per spin.
+// [W][2][nmax][nmax] double2 receives A^-1 per spin. With redo ([W][2] int
+// scratch) the FP32 path recomputes in FP64 every matrix whose pivots put
+// its condition number above 1e3.
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
-                           double2* logdet, double2* Ainv, bool fp64_compute);
+                           double2* logdet, double2* Ainv, bool fp64_compute, int* redo);
 
 // K7: hybrid weight and phaseless cut from the new log-overlap; ends the
 // step (ctr[0] += 1).

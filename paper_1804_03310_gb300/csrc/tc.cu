@@ -32,12 +32,13 @@ namespace {
 
 constexpr int BM = 128, BK = 32;
 
-// x rounded to the nearest TF32 value (10 explicit mantissa bits, ties to
-// even), so that x - tf32_hi(x) is exact in FP32 and at most 2^-11 |x|.
+// x rounded to the nearest TF32 value (10 explicit mantissa bits, the 13
+// low bits of the FP32 pattern cleared), so that x - tf32_hi(x) is exact in
+// FP32 and at most 2^-11 |x|. One conversion instruction.
 __device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t u = __float_as_uint(x);
-  u += 0x0FFFu + ((u >> 13) & 1u);
-  return __uint_as_float(u & 0xFFFFE000u);
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 __device__ __forceinline__ void flag_timeout(int* status) {
@@ -45,20 +46,41 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 }
 
 // ------------------------------------------------------------------ GEMM
+// Persistent: each CTA walks work items (output tile, K range) i = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the TMA -> MMA ring of stages runs on across
+// items, and the accumulator lives in one of two TMEM buffers so that the
+// epilogue of item j overlaps the main loop of item j + 1.
+// Warps: 0 TMA producer, 1 MMA issuer, 2-5 epilogue (TMEM lane quadrant =
+// warp % 4), 6-9 operand split (TF32X3 only).
 template <int BN, bool SPLIT3>
 struct GemmCfg {
-  static constexpr int STAGES = SPLIT3 ? (BN == 128 ? 3 : 4) : 4;
   static constexpr int A_BYTES = BM * BK * 4;
   static constexpr int B_BYTES = BN * BK * 4;
   static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT3 ? 2 : 1);
+  static constexpr int STAGES = (196 * 1024) / STAGE_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int THREADS = SPLIT3 ? 320 : 192;
+};
+
+struct GemmWork {
+  int mt, nt, ktiles_total, ktiles_per_split, items;
+  __device__ void item(int i, int& m0, int& n0, int& z, int& kt0, int& nkt) const {
+    const int tn = i % nt;
+    const int rest = i / nt;
+    const int tm = rest % mt;
+    z = rest / mt;
+    m0 = tm * BM;
+    n0 = tn;            // scaled by BN by the caller
+    kt0 = z * ktiles_per_split;
+    nkt = max(0, min(ktiles_total, kt0 + ktiles_per_split) - kt0);
+  }
 };
 
 template <int BN, bool SPLIT3>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(GemmCfg<BN, SPLIT3>::THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-               const __grid_constant__ CUtensorMap mapB, int m, int n, int ktiles_total,
-               int ktiles_per_split, float* __restrict__ C, long ldc, float alpha,
+               const __grid_constant__ CUtensorMap mapB, int m, int n, GemmWork wk,
+               float* __restrict__ C, long ldc, float alpha,
                float beta, const float* __restrict__ R, long ldr, long split_stride,
                int* status) {
   using Cfg = GemmCfg<BN, SPLIT3>;
@@ -75,15 +97,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   uint64_t* full = bars;
   uint64_t* conv = bars + S;
   uint64_t* empty = bars + 2 * S;
-  uint64_t* done = bars + 3 * S;
-  uint32_t* tslot = (uint32_t*)(bars + 3 * S + 1);
+  uint64_t* tfull = bars + 3 * S;       // [2] accumulator ready
+  uint64_t* tempty = bars + 3 * S + 2;  // [2] accumulator drained
+  uint32_t* tslot = (uint32_t*)(bars + 3 * S + 4);
   __shared__ int s_fail;
+  volatile int* fail = &s_fail;       // read afresh: a timed-out role stops the others
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, z = blockIdx.z;
-  const int kt0 = z * ktiles_per_split;
-  const int nkt = max(0, min(ktiles_total, kt0 + ktiles_per_split) - kt0);
-
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < S; ++s) {
@@ -91,10 +111,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       mbar_init(smem_u32(&conv[s]), 128);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(done), 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tfull[a]), 1);
+      mbar_init(smem_u32(&tempty[a]), 4);
+    }
     mbar_fence_init();
   }
-  if (warp == 1) tmem_alloc(smem_u32(tslot), BN);
+  if (warp == 1) tmem_alloc(smem_u32(tslot), 2 * BN);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -102,55 +125,138 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int i = 0; i < nkt; ++i) {
-        const int s = i % S;
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (i >= S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
-          flag_timeout(status);
-          s_fail = 1;
-          break;
+      int it = 0;
+      for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x) {
+        int m0, tn, z, kt0, nkt;
+        wk.item(i, m0, tn, z, kt0, nkt);
+        const int n0 = tn * BN;
+        for (int k = 0; k < nkt; ++k, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (it >= S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
+            flag_timeout(status);
+            *fail = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(smem_u32(&full[s]), Cfg::A_BYTES + Cfg::B_BYTES);
+          tma_load_2d(smem_u32(a_hi(s)), &mapA, (kt0 + k) * BK, m0, smem_u32(&full[s]));
+          tma_load_2d(smem_u32(b_hi(s)), &mapB, (kt0 + k) * BK, n0, smem_u32(&full[s]));
         }
-        mbar_arrive_expect_tx(smem_u32(&full[s]), Cfg::A_BYTES + Cfg::B_BYTES);
-        tma_load_2d(smem_u32(a_hi(s)), &mapA, (kt0 + i) * BK, m0, smem_u32(&full[s]));
-        tma_load_2d(smem_u32(b_hi(s)), &mapB, (kt0 + i) * BK, n0, smem_u32(&full[s]));
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && nkt > 0) {
+    if (lane == 0) {
       const uint32_t id = idesc_tf32(BM, BN);
-      for (int i = 0; i < nkt; ++i) {
-        const int s = i % S;
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (!mbar_wait(smem_u32(SPLIT3 ? &conv[s] : &full[s]), ph)) {
+      int it = 0, j = 0;
+      for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x, ++j) {
+        int m0, tn, z, kt0, nkt;
+        wk.item(i, m0, tn, z, kt0, nkt);
+        const int acc = j & 1;
+        const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+        if (j >= 2 && !mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
           flag_timeout(status);
-          s_fail = 1;
+          *fail = 1;
           break;
         }
         fence_after_sync();
+        const uint32_t td = tmem + (uint32_t)(acc * BN);
+        for (int k = 0; k < nkt; ++k, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!mbar_wait(smem_u32(SPLIT3 ? &conv[s] : &full[s]), ph)) {
+            flag_timeout(status);
+            *fail = 1;
+            break;
+          }
+          fence_after_sync();
 #pragma unroll
-        for (int ks = 0; ks < BK / 8; ++ks) {
-          const uint64_t ad = desc_sw128(smem_u32(a_hi(s)) + ks * 32);
-          const uint64_t bd = desc_sw128(smem_u32(b_hi(s)) + ks * 32);
-          mma_tf32(tmem, ad, bd, id, (i > 0 || ks > 0) ? 1u : 0u);
-          if (SPLIT3) {
-            mma_tf32(tmem, ad, desc_sw128(smem_u32(b_lo(s)) + ks * 32), id, 1u);
-            mma_tf32(tmem, desc_sw128(smem_u32(a_lo(s)) + ks * 32), bd, id, 1u);
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            const uint64_t ad = desc_sw128(smem_u32(a_hi(s)) + ks * 32);
+            const uint64_t bd = desc_sw128(smem_u32(b_hi(s)) + ks * 32);
+            mma_tf32(td, ad, bd, id, (k > 0 || ks > 0) ? 1u : 0u);
+            if (SPLIT3) {
+              mma_tf32(td, ad, desc_sw128(smem_u32(b_lo(s)) + ks * 32), id, 1u);
+              mma_tf32(td, desc_sw128(smem_u32(a_lo(s)) + ks * 32), bd, id, 1u);
+            }
+          }
+          mma_commit(smem_u32(&empty[s]));
+        }
+        mma_commit(smem_u32(&tfull[acc]));
+      }
+    }
+  } else if (warp < 6) {
+    // epilogue: TMEM lane quadrant q = warp % 4 holds rows 32q .. 32q + 31
+    const int q = warp & 3;
+    int j = 0;
+    for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x, ++j) {
+      int m0, tn, z, kt0, nkt;
+      wk.item(i, m0, tn, z, kt0, nkt);
+      const int n0 = tn * BN;
+      const int acc = j & 1;
+      const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+      const bool ok = mbar_wait(smem_u32(&tfull[acc]), aph);
+      if (!ok) {
+        flag_timeout(status);
+        *fail = 1;
+        break;
+      }
+      fence_after_sync();
+      const int row = m0 + 32 * q + lane;
+      float* crow = C + (long)z * split_stride + (long)row * ldc;
+      const float* rrow = R ? R + (long)row * ldr : nullptr;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c0), v);
+        if (nkt == 0) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) v[jj] = 0.f;
+        }
+        if (row < m) {
+          const int cb = n0 + c0;
+          if (cb + 32 <= n && (ldc & 3) == 0 && (!rrow || (ldr & 3) == 0) &&
+              ((uintptr_t)(crow + cb) & 15) == 0 &&
+              (!rrow || ((uintptr_t)(rrow + cb) & 15) == 0)) {
+#pragma unroll
+            for (int jj = 0; jj < 32; jj += 4) {
+              float4 o;
+              o.x = alpha * v[jj]; o.y = alpha * v[jj + 1];
+              o.z = alpha * v[jj + 2]; o.w = alpha * v[jj + 3];
+              if (rrow) {
+                float4 r = *(const float4*)(rrow + cb + jj);
+                o.x += beta * r.x; o.y += beta * r.y; o.z += beta * r.z; o.w += beta * r.w;
+              }
+              *(float4*)(crow + cb + jj) = o;
+            }
+          } else {
+            for (int jj = 0; jj < 32; ++jj) {
+              const int col = cb + jj;
+              if (col < n) {
+                float o = alpha * v[jj];
+                if (rrow) o += beta * rrow[col];
+                crow[col] = o;
+              }
+            }
           }
         }
-        mma_commit(smem_u32(&empty[s]));
       }
-      mma_commit(smem_u32(done));
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
     }
-  } else {
-    // warps 2..5: operand split (TF32X3), then the epilogue
-    const int t = threadIdx.x - 64;
-    if (SPLIT3) {
-      for (int i = 0; i < nkt; ++i) {
-        const int s = i % S;
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
+  } else if (SPLIT3) {
+    // operand split: hi = x rounded to TF32 in place, lo = x - hi
+    const int t = threadIdx.x - 192;
+    int it = 0;
+    for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x) {
+      int m0, tn, z, kt0, nkt;
+      wk.item(i, m0, tn, z, kt0, nkt);
+      for (int k = 0; k < nkt; ++k, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
         if (!mbar_wait(smem_u32(&full[s]), ph)) {
           flag_timeout(status);
-          s_fail = 1;
+          *fail = 1;
           break;
         }
         float4* ah = (float4*)a_hi(s);
@@ -175,55 +281,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
         mbar_arrive(smem_u32(&conv[s]));
       }
     }
-    bool ok = true;
-    if (nkt > 0) {
-      ok = mbar_wait(smem_u32(done), 0);
-      if (!ok) flag_timeout(status);
-    }
-    fence_after_sync();
-    const int q = warp & 3;
-    const int row = m0 + 32 * q + lane;
-    float* crow = C + (long)z * split_stride + (long)row * ldc;
-    const float* rrow = R ? R + (long)row * ldr : nullptr;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      if (nkt > 0 && ok) {
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.f;
-      }
-      if (row < m) {
-        const int cb = n0 + c0;
-        if (cb + 32 <= n && (ldc & 3) == 0 && (!rrow || (ldr & 3) == 0) &&
-            ((uintptr_t)(crow + cb) & 15) == 0 && (!rrow || ((uintptr_t)(rrow + cb) & 15) == 0)) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 o;
-            o.x = alpha * v[j]; o.y = alpha * v[j + 1]; o.z = alpha * v[j + 2]; o.w = alpha * v[j + 3];
-            if (rrow) {
-              float4 r = *(const float4*)(rrow + cb + j);
-              o.x += beta * r.x; o.y += beta * r.y; o.z += beta * r.z; o.w += beta * r.w;
-            }
-            *(float4*)(crow + cb + j) = o;
-          }
-        } else {
-          for (int j = 0; j < 32; ++j) {
-            const int col = cb + j;
-            if (col < n) {
-              float o = alpha * v[j];
-              if (rrow) o += beta * rrow[col];
-              crow[col] = o;
-            }
-          }
-        }
-      }
-    }
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, BN);
+  if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
 
 // ------------------------------------------------------------------ Taylor
@@ -240,9 +301,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
 // into the operand buffer from a pre-swizzled (and pre-split) image.
 constexpr int TY_A_BYTES = 128 * 128 * 4;     // [[Vr, -Vi], [Vi, Vr]], 4 K-blocks
 constexpr int TY_B_BYTES = 64 * 128 * 4;      // current term t, 64 columns
+constexpr int TY_V_BYTES = 2 * 64 * 64 * 4;   // raw V of the next walker (TF32X3)
 template <bool SPLIT3>
 constexpr int taylor_smem() {
-  return (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1) + 1024 + 64;
+  return (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1) + 1024 + 128 + (SPLIT3 ? TY_V_BYTES : 0);
 }
 
 // (B_half - I) as the operand image the Taylor kernel copies in: hi tile,
@@ -307,7 +369,11 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   unsigned char* Blo = Bhi + TY_B_BYTES;
   uint64_t* bar = (uint64_t*)(base + (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1));
   uint64_t* lbar = bar + 1;
-  uint32_t* tslot = (uint32_t*)(bar + 2);
+  uint64_t* vbar = bar + 2;
+  uint32_t* tslot = (uint32_t*)(bar + 3);
+  // TF32X3 with M even: the next walker's V (2 M^2 floats, contiguous) is
+  // bulk-copied into the spare shared memory while this walker's series runs
+  float* vst = (float*)(base + (TY_A_BYTES + TY_B_BYTES) * 2 + 128);
   __shared__ int s_fail;
 
   const int tid = threadIdx.x;
@@ -320,6 +386,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     s_fail = 0;
     mbar_init(smem_u32(bar), 1);
     mbar_init(smem_u32(lbar), 1);
+    mbar_init(smem_u32(vbar), 1);
     mbar_fence_init();
   }
   // The V operand's padding (rows and K beyond M in each half) stays zero for
@@ -369,6 +436,19 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     }
     lphase ^= 1u;
   };
+  const bool vpre = SPLIT3 && (M & 1) == 0;   // rows of 8 M^2 bytes, 16-byte multiples
+  const uint32_t vbytes = (uint32_t)(8 * MM);
+  uint32_t vphase = 0;
+  bool v_inflight = false;
+  auto load_v = [&](int it) {             // called by every thread after a barrier
+    if (tid == 0) {
+      fence_proxy_async();                // earlier generic reads of vst come first
+      mbar_arrive_expect_tx(smem_u32(vbar), vbytes);
+      bulk_load(smem_u32(vst), V + (long)(it / nchunk) * 2 * MM, vbytes, smem_u32(vbar));
+    }
+    v_inflight = true;
+  };
+  if (vpre && (int)blockIdx.x < items) load_v(blockIdx.x);
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int w = item / nchunk;
@@ -403,29 +483,58 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         }
       }
     }
-    // ---- A = [[Vr, -Vi], [Vi, Vr]]: each V element lands in two quadrants
-    for (int e0 = tid; e0 < 2 * MM; e0 += 128 * 8) {
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * 128;
-        v[u] = e < 2 * MM ? Vw[e] : 0.f;
+    // ---- A = [[Vr, -Vi], [Vi, Vr]]: thread (i, plane) = (tid % 64, tid / 64)
+    // copies row i of Vr (plane 0) or Vi (plane 1) into its two quadrants,
+    // 4 consecutive K values (one 16-byte chunk of the swizzled tile) at a time
+    const float* vsrc = Vw;
+    if (vpre) {
+      if (!mbar_wait(smem_u32(vbar), vphase)) {
+        flag_timeout(status);
+        s_fail = 1;
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * 128;
-        if (e >= 2 * MM) break;
-        const int plane = e >= MM;
-        const int rem = e - plane * MM;
-        const int i = rem / M, j = rem - i * M;
-        if (plane == 0) {          // Vr on both diagonal blocks
-          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(i, j, 128), v[u]);
-          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(64 + i, 64 + j, 128), v[u]);
-        } else {                   // Vi below, -Vi above the diagonal
-          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(64 + i, j, 128), v[u]);
-          put_operand<SPLIT3>(Ahi, Alo, sw128_offset(i, 64 + j, 128), -v[u]);
+      vphase ^= 1u;
+      v_inflight = false;
+      vsrc = vst;
+    }
+    if (rr < M) {
+      const float* src = vsrc + (long)rc * MM + (long)rr * M;
+      const bool vec = (M & 3) == 0;     // rows 16-byte aligned
+      const uint32_t row1 = rc ? 64 + rr : rr, row2 = rc ? rr : 64 + rr;
+      const uint32_t k1 = 0, k2 = 64;    // plane 0: (i, k), (64+i, 64+k); plane 1: (64+i, k), (i, 64+k)
+      const float sgn2 = rc ? -1.f : 1.f;
+      for (int k0 = 0; k0 < M; k0 += 4) {
+        float4 x;
+        if (vec) {
+          x = *reinterpret_cast<const float4*>(src + k0);
+        } else {
+          x.x = src[k0];
+          x.y = k0 + 1 < M ? src[k0 + 1] : 0.f;
+          x.z = k0 + 2 < M ? src[k0 + 2] : 0.f;
+          x.w = k0 + 3 < M ? src[k0 + 3] : 0.f;
+        }
+        const uint32_t o1 = sw128_offset(row1, k1 + k0, 128);
+        const uint32_t o2 = sw128_offset(row2, k2 + k0, 128);
+        const float4 y = make_float4(sgn2 * x.x, sgn2 * x.y, sgn2 * x.z, sgn2 * x.w);
+        if (SPLIT3) {
+          float4 h1, l1, h2, l2;
+          h1.x = tf32_hi(x.x); h1.y = tf32_hi(x.y); h1.z = tf32_hi(x.z); h1.w = tf32_hi(x.w);
+          l1.x = x.x - h1.x; l1.y = x.y - h1.y; l1.z = x.z - h1.z; l1.w = x.w - h1.w;
+          h2 = make_float4(sgn2 * h1.x, sgn2 * h1.y, sgn2 * h1.z, sgn2 * h1.w);
+          l2 = make_float4(sgn2 * l1.x, sgn2 * l1.y, sgn2 * l1.z, sgn2 * l1.w);
+          *reinterpret_cast<float4*>(Ahi + o1) = h1;
+          *reinterpret_cast<float4*>(Alo + o1) = l1;
+          *reinterpret_cast<float4*>(Ahi + o2) = h2;
+          *reinterpret_cast<float4*>(Alo + o2) = l2;
+        } else {
+          *reinterpret_cast<float4*>(Ahi + o1) = x;
+          *reinterpret_cast<float4*>(Ahi + o2) = y;
         }
       }
+    }
+    if (vpre) {
+      __syncthreads();                    // every thread has read vst
+      const int next = item + (int)gridDim.x;
+      if (next < items && !s_fail) load_v(next);
     }
     for (int term = 1; term <= order; ++term) {
       sync_for_mma();
@@ -479,6 +588,8 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     fence_after_sync();
     if (s_fail) break;
   }
+  if (v_inflight && !mbar_wait(smem_u32(vbar), vphase))   // no copy may outlive the CTA
+    flag_timeout(status);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 64);
@@ -519,13 +630,17 @@ cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const fl
   if (e != cudaSuccess) return e;
   e = make_map(t, &mb, B, n, k, ldb, BN);
   if (e != cudaSuccess) return e;
-  const int kt = (k + BK - 1) / BK;
-  const int per = (kt + ksplit - 1) / ksplit;
-  dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, ksplit);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  tc_gemm_kernel<BN, SPLIT3><<<grid, 192, Cfg::SMEM, st>>>(ma, mb, m, n, kt, per, C, ldc,
-                                                           alpha, beta, R, ldr,
-                                                           split_stride, status);
+  GemmWork wk;
+  wk.ktiles_total = (k + BK - 1) / BK;
+  wk.ktiles_per_split = (wk.ktiles_total + ksplit - 1) / ksplit;
+  wk.mt = (m + BM - 1) / BM;
+  wk.nt = (n + BN - 1) / BN;
+  const long items = (long)wk.mt * wk.nt * ksplit;
+  if (items > (1L << 30)) return cudaErrorInvalidConfiguration;
+  wk.items = (int)items;
+  const int grid = wk.items < t->num_sms ? wk.items : t->num_sms;
+  tc_gemm_kernel<BN, SPLIT3><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(
+      ma, mb, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status);
   return cudaGetLastError();
 }
 

@@ -82,7 +82,7 @@ def _variants(c0):
     out = []
     for xs in sorted({1, 2, t["xsplit"]}):
         for bn in (64, 128):
-            for fused in (0, 1):
+            for fused in (0, 1, 2):
                 out.append(dict(xsplit=xs, bn_force_bias=bn, bn_one_body=bn, bn_energy=bn,
                                 bn_half_step=bn, taylor_fused=fused))
     return out
@@ -113,6 +113,10 @@ def test_tuning_rejects_invalid_shapes():
     c = ctx(s, precision="tf32")
     with pytest.raises(AfqmcError):
         c.afqmc_set_tuning(taylor_fused=1)           # M > 64
+    with pytest.raises(AfqmcError):
+        c.afqmc_set_tuning(taylor_fused=2)           # M > 64
+    with pytest.raises(AfqmcError):
+        c.afqmc_set_tuning(taylor_fused=3)
     with pytest.raises(AfqmcError):
         c.afqmc_set_tuning(bn_energy=96)
     c.close()
