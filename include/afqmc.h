@@ -94,7 +94,16 @@ typedef struct {
                             (afqmc_tuning) on this system at creation and keep
                             the fastest, cached per shape for the process;
                             0 = fixed heuristics */
-  int32_t reserved[5];   /* must be zero */
+  int32_t weight_cap;    /* 0 (default): no cap, the paper's hybrid weights.
+                            k > 0: after each step a walker's weight is capped
+                            at k times the reference weight, the common weight
+                            the last comb gave every walker (1 before the
+                            first comb; a restored checkpoint takes the mean
+                            of its positive weights). Guards long runs against
+                            a walker near a node of the trial taking a runaway
+                            weight, at the price of a bias that vanishes as k
+                            grows. */
+  int32_t reserved[4];   /* must be zero */
 } afqmc_params;
 
 /* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,

@@ -186,16 +186,21 @@ def importance_log(x, xbar):
     return np.sum(x * xbar - 0.5 * xbar * xbar, axis=1)
 
 
-def update_weights(weight, logO_old, logO_new, x, xbar, dtau, e_shift):
+def update_weights(weight, logO_old, logO_new, x, xbar, dtau, e_shift, cap=0,
+                   w_ref=1.0):
     """Hybrid weight with the phaseless cut (Sec. II):
     W <- W |I| max(0, cos(Im ln R)), ln I = ln R + sum(x xbar - xbar^2/2)
-    + dt E_T. A walker at weight 0 stays there; non-finite results give 0."""
+    + dt E_T. A walker at weight 0 stays there; non-finite results give 0.
+    With cap > 0 (an option, not part of the paper's step) the result is
+    capped at cap * w_ref, w_ref the common weight of the last comb."""
     lnR = logO_new - logO_old
     lnI = lnR + importance_log(x, xbar) + dtau * e_shift
     with np.errstate(over="ignore", invalid="ignore"):
         w = weight * np.exp(lnI.real) * np.maximum(0.0, np.cos(lnR.imag))
     w = np.where(weight == 0.0, 0.0, w)
     w = np.where(np.isfinite(w), w, 0.0)
+    if cap > 0 and w_ref > 0:
+        w = np.minimum(w, cap * w_ref)
     return w
 
 
@@ -403,6 +408,7 @@ class OracleRun:
             e_shift = reference_energy(self.h1, self.L, self.trial)
         self.e_shift = e_shift
         self.step_count = 0
+        self.w_ref = 1.0            # common weight of the last comb (weight cap)
         self.energies = []          # (step, mixed energy, E_L per walker)
         self.last = {}
 
@@ -422,7 +428,8 @@ class OracleRun:
         self.Phi_dn = propagate(self.Bhalf, V, self.Phi_dn, s.taylor_order)
         logO_new, _ = trial_overlap(self.trial, self.Phi_up, self.Phi_dn)
         self.weight = update_weights(self.weight, self.logO, logO_new, x,
-                                     xbar, s.dtau, self.e_shift)
+                                     xbar, s.dtau, self.e_shift,
+                                     getattr(s, "weight_cap", 0), self.w_ref)
         self.logO = logO_new
         self.last = dict(X=X, xbar=xbar, x=x, V=V)
         self.step_count += 1
@@ -453,6 +460,7 @@ class OracleRun:
     def population_control(self):
         u = comb_uniform(self.s.seed, self.s.run_id, self.step_count)
         parent, wnew = comb(self.weight, u)
+        self.w_ref = wnew
         self.Phi_up = self.Phi_up[parent].copy()
         self.Phi_dn = self.Phi_dn[parent].copy()
         self.logO = self.logO[parent].copy()

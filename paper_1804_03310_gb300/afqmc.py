@@ -34,7 +34,7 @@ class afqmc_params(C.Structure):
                 ("taylor_order", C.c_int32), ("fb_cap", C.c_double),
                 ("e_shift", C.c_double), ("fp64_islands", C.c_int32),
                 ("graphs", C.c_int32), ("autotune", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("weight_cap", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class afqmc_tuning(C.Structure):
@@ -166,7 +166,8 @@ class Inputs:
     def __init__(self, h1, L, C_up, C_dn, occ_up, occ_dn, ci, *, dtau,
                  n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
                  measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
-                 e_shift=None, fp64_islands=False, graphs=True, autotune=True):
+                 e_shift=None, fp64_islands=False, graphs=True, autotune=True,
+                 weight_cap=0):
         self.h1 = np.ascontiguousarray(h1, dtype=np.float64)
         self.L = np.ascontiguousarray(L, dtype=np.float64)
         self.C_up = np.ascontiguousarray(C_up, dtype=np.float64)
@@ -194,6 +195,7 @@ class Inputs:
         p.fp64_islands = int(bool(fp64_islands))
         p.graphs = int(bool(graphs))
         p.autotune = int(bool(autotune))
+        p.weight_cap = int(weight_cap)
         self.params = p
 
     @classmethod
@@ -203,7 +205,7 @@ class Inputs:
                     ortho_every=system.ortho_every,
                     measure_every=system.measure_every,
                     pc_every=system.pc_every, taylor_order=system.taylor_order,
-                    fb_cap=system.fb_cap)
+                    fb_cap=system.fb_cap, weight_cap=system.weight_cap)
         args.update(kw)
         return cls(system.h1, system.L, system.C_up, system.C_dn,
                    system.occ_up, system.occ_dn, system.ci, **args)

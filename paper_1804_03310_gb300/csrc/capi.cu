@@ -70,7 +70,7 @@ struct afqmc_ctx {
   double *weight, *scan, *wnew, *escalar, *lr;
   double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
   int *parent, *status;
-  int* redo;          // [W][2] matrices the FP32 overlap kernel left to FP64
+  double wref_host;   // staging of a restored reference weight
   long long* ctr;   // device step counters: [0] completed steps, [1] measurements
   std::vector<void*> allocs;
   size_t dev_bytes;
@@ -362,7 +362,7 @@ template <typename T>
 afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
   LK(launch_overlap<T>(c->st, c->W, c->M, c->nu, c->nd, (const T*)c->Phi,
                        (const T*)c->PsiT, (T*)c->Theta, c->ldt, c->dn_off, c->logdet,
-                       nullptr, c->fp64_islands, c->redo));
+                       nullptr, c->fp64_islands));
   if (c->md) {   // ratios by Sherman-Morrison-Woodbury, ln O_T and Gamma
     LK(launch_md_step<T>(c->st, c->mdt, c->W, c->M, c->nu, c->nd, (const T*)c->Theta, c->ldt,
                          c->dn_off, c->logdet, logO_out, (T*)c->Gamma, c->ldg, c->gdn_off,
@@ -459,7 +459,8 @@ afqmc_status step_T(afqmc_ctx* c) {
   }
   {
     KTimer t(c, 5);
-    LK(launch_weights(c->st, W, c->logO_new, c->lw, dt, c->e_shift, c->weight, c->logO,
+    LK(launch_weights(c->st, W, c->logO_new, c->lw, dt, c->e_shift, (double)c->p.weight_cap,
+                      c->wnew, c->weight, c->logO,
                       c->ctr));
   }
   c->step += 1;
@@ -487,8 +488,9 @@ afqmc_status step_T(afqmc_ctx* c) {
 afqmc_status validate_sizes(const afqmc_params* p) {
   afqmc_ctx* c = nullptr;
   if (!p) return fail(c, AFQMC_E_INVALID, "null argument");
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
+  if (p->weight_cap < 0) return fail(c, AFQMC_E_INVALID, "weight_cap must be >= 0");
   if ((p->graphs != 0 && p->graphs != 1) || (p->autotune != 0 && p->autotune != 1))
     return fail(c, AFQMC_E_INVALID, "graphs and autotune must be 0 or 1");
   const int M = p->M;
@@ -697,6 +699,10 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
 #undef TM
   // walkers start at the reference determinant, weight 1
   LK(launch_init_walkers<T>(st, W, M, N, (const T*)c->PsiT, (T*)c->Phi, c->weight));
+  {                                   // reference weight of the weight cap
+    static const double one = 1.0;
+    CK(cudaMemcpyAsync(c->wnew, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
   afqmc_status s = overlap_T<T>(c, c->logO);
   if (s != AFQMC_OK) return s;
   if (isnan(c->p.e_shift)) {
@@ -1132,7 +1138,6 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->eloc, W * sizeof(double2));
   add(&c->hist, kHist * sizeof(double2));
   add(&c->parent, W * sizeof(int));
-  add(&c->redo, 2 * W * sizeof(int));
   add(&c->status, sizeof(int));
   add(&c->ctr, 2 * sizeof(long long));
   return b;
@@ -1581,6 +1586,14 @@ afqmc_status afqmc_set_state(afqmc_ctx* c, const void* buf, size_t bytes) {
   CK(cudaMemcpyAsync(c->Phi, ph.data(), ph.size(), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->weight, wt, W * sizeof(double), cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->logO, lo, W * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+  {                                   // reference weight of the weight cap
+    double sum = 0.0;
+    int live = 0;
+    for (int w = 0; w < W; ++w)
+      if (wt[w] > 0.0) { sum += wt[w]; ++live; }
+    c->wref_host = live ? sum / live : 1.0;
+    CK(cudaMemcpyAsync(c->wnew, &c->wref_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  }
   c->step = h.step;
   const long long ctr_h[2] = {(long long)c->step, (long long)c->n_meas};
   CK(cudaMemcpyAsync(c->ctr, ctr_h, sizeof(ctr_h), cudaMemcpyHostToDevice, c->st));

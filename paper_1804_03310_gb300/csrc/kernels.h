@@ -48,19 +48,19 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
 // (FP64 arithmetic when fp64_compute, else FP32), ln det A accumulated in
 // FP64, Theta = Phi A^-1. PsiT [N][M] holds the reference determinant's
 // orbitals as rows (up orbitals then down orbitals). Ainv (optional)
-// [W][2][nmax][nmax] double2 receives A^-1 per spin. With redo ([W][2] int
-// scratch) the FP32 path recomputes in FP64 every matrix whose pivots put
-// its condition number above 1e3.
+// [W][2][nmax][nmax] double2 receives A^-1 per spin.
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
-                           double2* logdet, double2* Ainv, bool fp64_compute, int* redo);
+                           double2* logdet, double2* Ainv, bool fp64_compute);
 
 // K7: hybrid weight and phaseless cut from the new log-overlap; ends the
-// step (ctr[0] += 1).
+// step (ctr[0] += 1). With cap > 0 a weight is capped at cap * (*wref) when
+// *wref > 0.
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
-                           const double2* lw, double dtau, double e_shift,
-                           double* weight, double2* logO, long long* ctr);
+                           const double2* lw, double dtau, double e_shift, double cap,
+                           const double* wref, double* weight, double2* logO,
+                           long long* ctr);
 
 // Sum of the two spins' log-determinants (single-determinant overlap).
 cudaError_t launch_logdet_sum(cudaStream_t st, int W, const double2* logdet,

@@ -294,18 +294,26 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
 // TMEM lane; it keeps the running sum of the series for its row in
 // registers.
 //
+// The operator, in its real form A = [[Vr, -Vi], [Vi, Vr]] (2M x 2M padded to
+// 128 x 128), is the MMA's A operand in tensor memory: lane r holds row r,
+// one 32-bit column per K index (TF32X3: hi in columns 128..255, lo in
+// 256..383; the accumulator in columns 0..63). Each thread writes its own row
+// with tcgen05.st, so the operand needs no shared-memory swizzle and the
+// MMAs read only the current term t (the B operand) from shared memory.
+//
 // With a half-step image (FUSE_B), the symmetric Trotter factors are applied
 // on the tensor cores too: t0 = Phi + (B_half - I) Phi before the series and
 // out = s + (B_half - I) s after it, the identity part added exactly in FP32
 // and (B_half - I) in its real 2M-row form [[dB, 0], [0, dB]] bulk-copied
-// into the operand buffer from a pre-swizzled (and pre-split) image.
-constexpr int TY_A_BYTES = 128 * 128 * 4;     // [[Vr, -Vi], [Vi, Vr]], 4 K-blocks
+// once per CTA into shared memory from a pre-swizzled (and pre-split) image.
+constexpr int TY_A_BYTES = 128 * 128 * 4;     // half-step image, 4 K-blocks
 constexpr int TY_B_BYTES = 64 * 128 * 4;      // current term t, 64 columns
 constexpr int TY_V_BYTES = 2 * 64 * 64 * 4;   // raw V of the next walker (TF32X3)
 template <bool SPLIT3>
 constexpr int taylor_smem() {
   return (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1) + 1024 + 128 + (SPLIT3 ? TY_V_BYTES : 0);
 }
+constexpr uint32_t TY_TMEM_AHI = 128, TY_TMEM_ALO = 256;   // column offsets
 
 // (B_half - I) as the operand image the Taylor kernel copies in: hi tile,
 // then (TF32X3) lo tile, each 128 x 128 fp32 in the K-major SW128 layout.
@@ -339,6 +347,7 @@ __device__ __forceinline__ void put_operand(unsigned char* hi, unsigned char* lo
   }
 }
 
+// D (+)= A B with both operands in shared memory (the half-step image).
 template <bool SPLIT3>
 __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint32_t Alo,
                                                uint32_t Bhi, uint32_t Blo, uint32_t id) {
@@ -355,6 +364,22 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint
   }
 }
 
+// D = A B with A in tensor memory (the operator) and B in shared memory.
+template <bool SPLIT3>
+__device__ __forceinline__ void issue_products_ts(uint32_t tD, uint32_t tAhi, uint32_t tAlo,
+                                                  uint32_t Bhi, uint32_t Blo, uint32_t id) {
+#pragma unroll
+  for (int ks = 0; ks < 16; ++ks) {
+    const int kb = ks >> 2, koff = (ks & 3) * 32;
+    const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
+    mma_tf32_ts(tD, tAhi + 8 * ks, bd, id, ks > 0 ? 1u : 0u);
+    if (SPLIT3) {
+      mma_tf32_ts(tD, tAhi + 8 * ks, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
+      mma_tf32_ts(tD, tAlo + 8 * ks, bd, id, 1u);
+    }
+  }
+}
+
 template <bool SPLIT3>
 __global__ void __launch_bounds__(128, 1)
 tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
@@ -362,9 +387,9 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
                  const float* __restrict__ dB_img, int* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // A hi and lo are adjacent so one bulk copy fills both
-  unsigned char* Ahi = base;
-  unsigned char* Alo = base + TY_A_BYTES;
+  // image hi and lo are adjacent so one bulk copy fills both
+  unsigned char* Ihi = base;
+  unsigned char* Ilo = base + TY_A_BYTES;
   unsigned char* Bhi = base + TY_A_BYTES * (SPLIT3 ? 2 : 1);
   unsigned char* Blo = Bhi + TY_B_BYTES;
   uint64_t* bar = (uint64_t*)(base + (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1));
@@ -375,6 +400,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   // bulk-copied into the spare shared memory while this walker's series runs
   float* vst = (float*)(base + (TY_A_BYTES + TY_B_BYTES) * 2 + 128);
   __shared__ int s_fail;
+  constexpr uint32_t kCols = SPLIT3 ? 512 : 256;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -389,21 +415,18 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     mbar_init(smem_u32(vbar), 1);
     mbar_fence_init();
   }
-  // The V operand's padding (rows and K beyond M in each half) stays zero for
-  // every walker: the V build writes only the M x M blocks, and the half-step
-  // image is zero there too.
-  for (int e = tid; e < TY_A_BYTES / 4 * (SPLIT3 ? 2 : 1); e += 128) ((float*)Ahi)[e] = 0.f;
-  fence_proxy_async();
-  if (warp == 0) tmem_alloc(smem_u32(tslot), 64);
+  if (warp == 0) tmem_alloc(smem_u32(tslot), kCols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
+  const uint32_t tAhi = tmem + TY_TMEM_AHI, tAlo = tmem + TY_TMEM_ALO;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
   const uint32_t id = idesc_tf32(128, 64);
-  uint32_t phase = 0, lphase = 0;
+  uint32_t phase = 0;
   const int r = tid;                       // embedded row / K index owned
   const int rc = r >> 6, rr = r & 63;      // component (0 re, 1 im), orbital row
-  const uint32_t sAhi = smem_u32(Ahi), sAlo = smem_u32(Alo);
+  const uint32_t sIhi = smem_u32(Ihi), sIlo = smem_u32(Ilo);
   const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
   const int MM = M * M;
 
@@ -423,19 +446,14 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     __syncthreads();
     fence_after_sync();
   };
-  auto load_bhalf = [&]() {
+  bool img_pending = false;
+  if (fuse_b) {                            // the half-step image, once per CTA
     if (tid == 0) {
       mbar_arrive_expect_tx(smem_u32(lbar), img_bytes);
-      bulk_load(sAhi, dB_img, img_bytes, smem_u32(lbar));
+      bulk_load(sIhi, dB_img, img_bytes, smem_u32(lbar));
     }
-  };
-  auto wait_bhalf = [&]() {
-    if (!mbar_wait(smem_u32(lbar), lphase)) {
-      flag_timeout(status);
-      s_fail = 1;
-    }
-    lphase ^= 1u;
-  };
+    img_pending = true;
+  }
   const bool vpre = SPLIT3 && (M & 1) == 0;   // rows of 8 M^2 bytes, 16-byte multiples
   const uint32_t vbytes = (uint32_t)(8 * MM);
   uint32_t vphase = 0;
@@ -455,7 +473,6 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     const int j0 = (item - w * nchunk) * 64;
     const int nc = min(64, N - j0);
     const float* Vw = V + (long)w * 2 * MM;
-    if (fuse_b) load_bhalf();
     // ---- t0 = the chunk's columns; this thread's row of it seeds the sum
     float acc[64];
     const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
@@ -465,17 +482,23 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
 #pragma unroll
     for (int j = 0; j < 64; ++j) put_operand<SPLIT3>(Bhi, Blo, sw128_offset(j, r, 64), acc[j]);
     if (fuse_b) {                          // t0 = Phi + dB Phi
-      wait_bhalf();
+      if (img_pending) {
+        if (!mbar_wait(smem_u32(lbar), 0)) {
+          flag_timeout(status);
+          s_fail = 1;
+        }
+        img_pending = false;
+      }
       sync_for_mma();
       if (tid == 0) {
-        issue_products<SPLIT3>(tmem, sAhi, sAlo, sBhi, sBlo, id);
+        issue_products<SPLIT3>(tmem, sIhi, sIlo, sBhi, sBlo, id);
         mma_commit(smem_u32(bar));
       }
       wait_mma();
 #pragma unroll
       for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           acc[c0 + j] += v[j];
@@ -483,9 +506,9 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         }
       }
     }
-    // ---- A = [[Vr, -Vi], [Vi, Vr]]: thread (i, plane) = (tid % 64, tid / 64)
-    // copies row i of Vr (plane 0) or Vi (plane 1) into its two quadrants,
-    // 4 consecutive K values (one 16-byte chunk of the swizzled tile) at a time
+    // ---- the operator into tensor memory: row r of [[Vr, -Vi], [Vi, Vr]],
+    // columns 0..63 from plane rc of V, columns 64..127 from the other plane
+    // (negated for the real rows), zero beyond M in each half
     const float* vsrc = Vw;
     if (vpre) {
       if (!mbar_wait(smem_u32(vbar), vphase)) {
@@ -496,40 +519,41 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
       v_inflight = false;
       vsrc = vst;
     }
-    if (rr < M) {
-      const float* src = vsrc + (long)rc * MM + (long)rr * M;
-      const bool vec = (M & 3) == 0;     // rows 16-byte aligned
-      const uint32_t row1 = rc ? 64 + rr : rr, row2 = rc ? rr : 64 + rr;
-      const uint32_t k1 = 0, k2 = 64;    // plane 0: (i, k), (64+i, 64+k); plane 1: (64+i, k), (i, 64+k)
-      const float sgn2 = rc ? -1.f : 1.f;
-      for (int k0 = 0; k0 < M; k0 += 4) {
-        float4 x;
-        if (vec) {
-          x = *reinterpret_cast<const float4*>(src + k0);
+    {
+      const bool vec = (M & 3) == 0;       // rows 16-byte aligned
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 16) {
+        const int half = c0 >> 6, k0 = c0 & 63;
+        const int plane = half == 0 ? rc : 1 - rc;
+        const float sgn = (rc == 0 && half == 1) ? -1.f : 1.f;
+        const float* src = vsrc + (long)plane * MM + (long)rr * M;
+        float x[16];
+        if (rr < M && vec && k0 + 16 <= M) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 f = *reinterpret_cast<const float4*>(src + k0 + 4 * q);
+            x[4 * q] = f.x; x[4 * q + 1] = f.y; x[4 * q + 2] = f.z; x[4 * q + 3] = f.w;
+          }
         } else {
-          x.x = src[k0];
-          x.y = k0 + 1 < M ? src[k0 + 1] : 0.f;
-          x.z = k0 + 2 < M ? src[k0 + 2] : 0.f;
-          x.w = k0 + 3 < M ? src[k0 + 3] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 16; ++u) x[u] = (rr < M && k0 + u < M) ? src[k0 + u] : 0.f;
         }
-        const uint32_t o1 = sw128_offset(row1, k1 + k0, 128);
-        const uint32_t o2 = sw128_offset(row2, k2 + k0, 128);
-        const float4 y = make_float4(sgn2 * x.x, sgn2 * x.y, sgn2 * x.z, sgn2 * x.w);
         if (SPLIT3) {
-          float4 h1, l1, h2, l2;
-          h1.x = tf32_hi(x.x); h1.y = tf32_hi(x.y); h1.z = tf32_hi(x.z); h1.w = tf32_hi(x.w);
-          l1.x = x.x - h1.x; l1.y = x.y - h1.y; l1.z = x.z - h1.z; l1.w = x.w - h1.w;
-          h2 = make_float4(sgn2 * h1.x, sgn2 * h1.y, sgn2 * h1.z, sgn2 * h1.w);
-          l2 = make_float4(sgn2 * l1.x, sgn2 * l1.y, sgn2 * l1.z, sgn2 * l1.w);
-          *reinterpret_cast<float4*>(Ahi + o1) = h1;
-          *reinterpret_cast<float4*>(Alo + o1) = l1;
-          *reinterpret_cast<float4*>(Ahi + o2) = h2;
-          *reinterpret_cast<float4*>(Alo + o2) = l2;
+          float h[16], l[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            h[u] = tf32_hi(sgn * x[u]);
+            l[u] = sgn * x[u] - h[u];
+          }
+          tmem_st16(tAhi + lane_base + (uint32_t)c0, h);
+          tmem_st16(tAlo + lane_base + (uint32_t)c0, l);
         } else {
-          *reinterpret_cast<float4*>(Ahi + o1) = x;
-          *reinterpret_cast<float4*>(Ahi + o2) = y;
+#pragma unroll
+          for (int u = 0; u < 16; ++u) x[u] *= sgn;
+          tmem_st16(tAhi + lane_base + (uint32_t)c0, x);
         }
       }
+      tmem_wait_st();
     }
     if (vpre) {
       __syncthreads();                    // every thread has read vst
@@ -539,7 +563,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     for (int term = 1; term <= order; ++term) {
       sync_for_mma();
       if (tid == 0) {
-        issue_products<SPLIT3>(tmem, sAhi, sAlo, sBhi, sBlo, id);
+        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id);
         mma_commit(smem_u32(bar));
       }
       wait_mma();
@@ -547,7 +571,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
 #pragma unroll
       for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float x = v[j] * inv;
@@ -559,20 +583,16 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
       }
     }
     if (fuse_b) {                          // out = s + dB s
-      fence_before_sync();
-      __syncthreads();
-      load_bhalf();
-      wait_bhalf();
       sync_for_mma();
       if (tid == 0) {
-        issue_products<SPLIT3>(tmem, sAhi, sAlo, sBhi, sBlo, id);
+        issue_products<SPLIT3>(tmem, sIhi, sIlo, sBhi, sBlo, id);
         mma_commit(smem_u32(bar));
       }
       wait_mma();
 #pragma unroll
       for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[c0 + j] += v[j];
       }
@@ -590,9 +610,10 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   }
   if (v_inflight && !mbar_wait(smem_u32(vbar), vphase))   // no copy may outlive the CTA
     flag_timeout(status);
+  if (img_pending && !mbar_wait(smem_u32(lbar), 0)) flag_timeout(status);
   fence_before_sync();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 64);
+  if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 template <typename K>

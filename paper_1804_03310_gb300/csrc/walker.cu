@@ -256,11 +256,9 @@ template <typename T, typename R>
 __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
                                const T* __restrict__ PsiT, T* __restrict__ Theta,
                                long ldt, long dn_off, double2* __restrict__ logdet,
-                               double2* __restrict__ Ainv_out, int nmax,
-                               const int* __restrict__ only) {
+                               double2* __restrict__ Ainv_out, int nmax) {
   extern __shared__ unsigned char smem_raw[];
   const int w = blockIdx.x, sig = blockIdx.y;
-  if (only && !only[2 * w + sig]) return;   // recomputing flagged matrices only
   const int N = n_up + n_dn;
   const int ns = sig ? n_dn : n_up;
   const int j0 = sig ? n_up : 0;
@@ -420,7 +418,8 @@ __global__ void logdet_sum_kernel(int W, const double2* __restrict__ ld,
 // --------------------------------------------------------------- K7
 __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
                                const double2* __restrict__ lw, double dtau,
-                               double e_shift, double* __restrict__ weight,
+                               double e_shift, double cap, const double* __restrict__ wref,
+                               double* __restrict__ weight,
                                double2* __restrict__ logO, long long* __restrict__ ctr) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w == 0) ctr[0] += 1;   // the step is complete once its weights are
@@ -434,6 +433,10 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
   if (wt != 0.0) {
     out = wt * exp(lnI_re) * fmax(0.0, cos(lnR.y));
     if (!isfinite(out)) out = 0.0;
+    if (cap > 0.0) {
+      const double ref = *wref;
+      if (ref > 0.0) out = fmin(out, cap * ref);
+    }
   }
   weight[w] = out;
   logO[w] = ln;
@@ -449,10 +452,9 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
 // sum_j ln R_jj is accumulated in FP64 into lr[w][spin].
 template <typename T, typename R>
 __global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
-                          double* __restrict__ lr, const int* __restrict__ only) {
+                          double* __restrict__ lr) {
   extern __shared__ unsigned char smem_raw[];
   const int w = blockIdx.x, sig = blockIdx.y;
-  if (only && !only[2 * w + sig]) return;   // recomputing flagged matrices only
   const int N = n_up + n_dn;
   const int ns = sig ? n_dn : n_up;
   const int j0 = sig ? n_up : 0;
@@ -519,252 +521,6 @@ __global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
     l = warp_sum(l);
     if (tid == 0) lr[2 * w + sig] = l;
   }
-}
-
-// K6 for spin blocks of at most 32 electrons in FP32 arithmetic, one warp per
-// (walker, spin) matrix and four matrices per block, so that no phase waits
-// on a block-wide barrier. Lane a owns row a of the n x n matrix in
-// registers; the walker's orbitals are read from global memory (the same 16
-// bytes by every lane where a phase broadcasts them, a lane's own basis rows
-// where it does not); the trial orbitals are staged once per block.
-constexpr int kWmThreads = 128;
-constexpr int kWmMax = 32;      // largest spin block handled here
-constexpr int kWmLdi = 32;      // row stride (complex) of a warp's inverse
-
-__host__ __device__ inline size_t wm_warp_bytes() {
-  return sizeof(float2) * kWmMax * kWmLdi                        // inverse
-         + sizeof(float2) * kWmMax                                // broadcast row
-         + sizeof(int) * kWmMax;                                  // pivot rows
-}
-
-__host__ __device__ inline size_t wm_smem(int M, int n_up, int n_dn) {
-  const size_t ldq = (size_t)(M | 1);
-  size_t b = sizeof(float) * (size_t)(n_up + n_dn) * ldq;       // trial rows
-  b = (b + 15) & ~(size_t)15;
-  return b + 4 * wm_warp_bytes();
-}
-
-struct WmShared {
-  float2* X;      // [32][kWmLdi] inverse (rows and columns in order)
-  float2* row;    // [32] row broadcast to the warp
-  int* rsel;      // [32] pivot row of each step
-};
-
-__device__ inline WmShared wm_carve(unsigned char* smem, int M, int n_up, int n_dn,
-                                    int warp, float** D) {
-  const size_t ldq = (size_t)(M | 1);
-  *D = reinterpret_cast<float*>(smem);
-  size_t off = sizeof(float) * (size_t)(n_up + n_dn) * ldq;
-  off = (off + 15) & ~(size_t)15;
-  unsigned char* p = smem + off + wm_warp_bytes() * warp;   // 16-byte multiples
-  WmShared g;
-  g.X = reinterpret_cast<float2*>(p);
-  g.row = g.X + kWmMax * kWmLdi;
-  g.rsel = reinterpret_cast<int*>(g.row + kWmMax);
-  return g;
-}
-
-// 4 consecutive basis values of one plane of a spin-block column.
-template <typename T>
-__device__ __forceinline__ float4 ld4(const T* p, bool vec) {
-  if (sizeof(T) == 4 && vec) return *reinterpret_cast<const float4*>(p);
-  return make_float4((float)p[0], (float)p[1], (float)p[2], (float)p[3]);
-}
-
-// out[c][k] (re at out_r, im at out_i, column stride ostride) = sum_i
-// Phi[k][i] X[i][c], lane = basis row k (k = lane, lane + 32, ...).
-template <typename T>
-__device__ void wm_tall_product(const T* Pw, int M, int n, const float2* X, T* out_r,
-                                T* out_i, long ostride, bool zero) {
-  const int lane = threadIdx.x & 31;
-  for (int k = lane; k < M; k += 32) {
-    float2 acc[kWmMax];
-#pragma unroll
-    for (int c = 0; c < kWmMax; ++c) acc[c] = make_float2(0.f, 0.f);
-    if (!zero) {
-      for (int i = 0; i < n; ++i) {
-        const float qr = (float)Pw[(long)i * 2 * M + k];
-        const float qi = (float)Pw[(long)i * 2 * M + M + k];
-        const float4* xr = reinterpret_cast<const float4*>(X + i * kWmLdi);
-#pragma unroll
-        for (int c2 = 0; c2 < kWmMax / 2; ++c2) {
-          if (2 * c2 < n) {
-            const float4 x = xr[c2];   // columns 2 c2, 2 c2 + 1
-            acc[2 * c2].x = fmaf(qr, x.x, fmaf(-qi, x.y, acc[2 * c2].x));
-            acc[2 * c2].y = fmaf(qr, x.y, fmaf(qi, x.x, acc[2 * c2].y));
-            acc[2 * c2 + 1].x = fmaf(qr, x.z, fmaf(-qi, x.w, acc[2 * c2 + 1].x));
-            acc[2 * c2 + 1].y = fmaf(qr, x.w, fmaf(qi, x.z, acc[2 * c2 + 1].y));
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < kWmMax; ++c) {
-      if (c < n) {
-        out_r[(long)c * ostride + k] = (T)acc[c].x;
-        out_i[(long)c * ostride + k] = (T)acc[c].y;
-      }
-    }
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kWmThreads, 4)
-overlap_warp_kernel(int W, int M, int n_up, int n_dn, const T* __restrict__ Phi,
-                    const T* __restrict__ PsiT, T* __restrict__ Theta, long ldt, long dn_off,
-                    double2* __restrict__ logdet, int* __restrict__ redo) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int N = n_up + n_dn, ldq = M | 1;
-  float* D;
-  const WmShared g = wm_carve(smem_raw, M, n_up, n_dn, warp, &D);
-  for (int e = tid; e < N * M; e += kWmThreads) {
-    const int a = e / M, k = e - a * M;
-    D[a * ldq + k] = (float)PsiT[e];
-  }
-  __syncthreads();
-  const int mi = blockIdx.x * 4 + warp;
-  if (mi >= 2 * W) return;
-  const int w = mi >> 1, sig = mi & 1;
-  const int ns = sig ? n_dn : n_up;
-  const int j0 = sig ? n_up : 0;
-  if (ns == 0) {
-    if (lane == 0) {
-      logdet[2 * w + sig] = make_double2(0.0, 0.0);
-      if (redo) redo[2 * w + sig] = 0;
-    }
-    return;
-  }
-  const T* Pw = Phi + ((long)w * N + j0) * 2 * M;
-  const float* Dw = D + (long)j0 * ldq;
-  const bool vec = (M & 3) == 0 && (((uintptr_t)Pw) & 15) == 0;
-  // ---- row `lane` of A = D^T Phi
-  float2 a[kWmMax];
-#pragma unroll
-  for (int b = 0; b < kWmMax; ++b) a[b] = make_float2(0.f, 0.f);
-  const int arow = lane < ns ? lane : 0;
-  int k = 0;
-  for (; k + 4 <= M; k += 4) {
-    const float d0 = Dw[arow * ldq + k], d1 = Dw[arow * ldq + k + 1];
-    const float d2 = Dw[arow * ldq + k + 2], d3 = Dw[arow * ldq + k + 3];
-#pragma unroll
-    for (int b = 0; b < kWmMax; ++b) {
-      if (b < ns) {
-        const float4 qr = ld4(Pw + (long)b * 2 * M + k, vec);
-        const float4 qi = ld4(Pw + (long)b * 2 * M + M + k, vec);
-        a[b].x = fmaf(d0, qr.x, fmaf(d1, qr.y, fmaf(d2, qr.z, fmaf(d3, qr.w, a[b].x))));
-        a[b].y = fmaf(d0, qi.x, fmaf(d1, qi.y, fmaf(d2, qi.z, fmaf(d3, qi.w, a[b].y))));
-      }
-    }
-  }
-  for (; k < M; ++k) {
-    const float d0 = Dw[arow * ldq + k];
-#pragma unroll
-    for (int b = 0; b < kWmMax; ++b) {
-      if (b < ns) {
-        a[b].x = fmaf(d0, (float)Pw[(long)b * 2 * M + k], a[b].x);
-        a[b].y = fmaf(d0, (float)Pw[(long)b * 2 * M + M + k], a[b].y);
-      }
-    }
-  }
-  if (lane >= ns) {
-#pragma unroll
-    for (int b = 0; b < kWmMax; ++b) a[b] = make_float2(0.f, 0.f);
-  }
-  // ---- in-place Gauss-Jordan with partial pivoting among unused rows.
-  // Step k: pivot row p; every row i updates a_i -= f_i row_p with the
-  // unscaled pivot row, f_i = a_i[k] / piv (i != p) or 1 - 1/piv (i = p, which
-  // scales row p by 1/piv); then column k <- -f_i (i != p), 1/piv (i = p).
-  // Afterwards A^-1[k'][r(k)] = row r(k')[k].
-  bool used = lane >= ns;
-  int mypos = 0, sing = 0;
-  float2 mypiv = make_float2(1.f, 0.f);     // pivot of step `lane`
-#pragma unroll
-  for (int kk = 0; kk < kWmMax; ++kk) {
-    if (kk < ns && !sing) {
-      float mag = a[kk].x * a[kk].x + a[kk].y * a[kk].y;
-      // key: magnitude bits (monotonic for mag >= 0) with the low 5 bits
-      // replaced by 31 - lane, so that the maximum is unique and ties pick
-      // the lowest lane; used rows, NaN and 0 give key 0
-      uint32_t key = 0;
-      if (!used && mag > 0.f && mag <= 3.4e38f) key = (__float_as_uint(mag) & ~31u) | (31u - lane);
-      key = __reduce_max_sync(0xffffffffu, key);
-      if (key == 0) {
-        sing = 1;
-      } else {
-        const int p = 31 - (int)(key & 31u);
-        const float pr = __shfl_sync(0xffffffffu, a[kk].x, p);
-        const float pi = __shfl_sync(0xffffffffu, a[kk].y, p);
-        const float dd = pr * pr + pi * pi;
-        const float ir = pr / dd, ii = -pi / dd;       // 1 / piv
-        if (lane == kk) mypiv = make_float2(pr, pi);
-        if (lane == p) {
-#pragma unroll
-          for (int b = 0; b < kWmMax; ++b)
-            if (b < ns) g.row[b] = a[b];
-          g.rsel[kk] = p;
-          used = true;
-          mypos = kk;
-        }
-        __syncwarp();
-        float fr, fi;
-        if (lane == p) {                               // 1 - 1/piv
-          fr = 1.f - ir;
-          fi = -ii;
-        } else {                                       // a_i[k] / piv
-          fr = a[kk].x * ir - a[kk].y * ii;
-          fi = a[kk].x * ii + a[kk].y * ir;
-        }
-#pragma unroll
-        for (int b = 0; b < kWmMax; ++b) {
-          if (b < ns) {
-            const float2 r = g.row[b];
-            a[b].x -= fr * r.x - fi * r.y;
-            a[b].y -= fr * r.y + fi * r.x;
-          }
-        }
-        a[kk] = (lane == p) ? make_float2(ir, ii) : make_float2(-fr, -fi);
-        __syncwarp();
-      }
-    }
-  }
-  double lre = 0.0, lim = 0.0;
-  if (!sing && lane < ns) {
-    const double pr = mypiv.x, pi = mypiv.y;
-    lre = 0.5 * log(pr * pr + pi * pi);
-    lim = atan2(pi, pr);
-  }
-  lre = warp_sum(lre);
-  lim = warp_sum(lim);
-  int inv = 0;
-  if (!sing && lane < ns) {
-    const int rk = g.rsel[lane];
-    for (int j = lane + 1; j < ns; ++j) inv += g.rsel[j] < rk;
-#pragma unroll
-    for (int kk = 0; kk < kWmMax; ++kk)
-      if (kk < ns) g.X[mypos * kWmLdi + g.rsel[kk]] = a[kk];
-  }
-  inv = __reduce_add_sync(0xffffffffu, inv);
-  // Conditioning: the pivots' magnitudes bound kappa(A) from below; past
-  // 1e3 the FP32 inverse and log-determinant lose more than ~1e-4 (walkers
-  // near a node of the trial), so with `redo` the matrix is flagged and left
-  // to the FP64 elimination instead of being written here.
-  const float pm = (lane < ns) ? mypiv.x * mypiv.x + mypiv.y * mypiv.y : 1.f;
-  const float pmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(pm)));
-  const float pmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(pm)));
-  const bool flag = redo && (sing || !(pmin >= 1e-6f * pmax));
-  if (lane == 0) {
-    double2 out = make_double2(lre, lim + ((inv & 1) ? 3.141592653589793 : 0.0));
-    if (sing) out = make_double2(-INFINITY, 0.0);
-    if (!flag) logdet[2 * w + sig] = out;
-    if (redo) redo[2 * w + sig] = flag ? 1 : 0;
-  }
-  if (flag) return;
-  __syncwarp();
-  // ---- Theta = Phi A^-1
-  T* Tr = Theta + ((long)w * 2 + 0) * ldt + (sig ? dn_off : 0);
-  T* Ti = Theta + ((long)w * 2 + 1) * ldt + (sig ? dn_off : 0);
-  wm_tall_product(Pw, M, ns, g.X, Tr, Ti, M, sing != 0);
 }
 
 __global__ void sub_logdet_r_kernel(int W, const double* __restrict__ lr,
@@ -1069,47 +825,32 @@ size_t overlap_smem(int M, int nmax, size_t csize) {
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
-                           double2* logdet, double2* Ainv, bool fp64_compute, int* redo) {
+                           double2* logdet, double2* Ainv, bool fp64_compute) {
   const int nmax = n_up > n_dn ? n_up : n_dn;
   const int threads = M > 96 ? 256 : 128;
   dim3 grid(W, 2);
-  static const size_t wm_cap = allow_big_smem(overlap_warp_kernel<T>);
   static const size_t cap64 = allow_big_smem(overlap_kernel<T, double>);
   const size_t smem64 = overlap_smem(M, nmax, sizeof(double2));
-  if (!fp64_compute && !Ainv && nmax <= kWmMax && wm_smem(M, n_up, n_dn) <= wm_cap) {
-    int* flags = (redo && smem64 <= cap64) ? redo : nullptr;
-    const int blocks = (2 * W + 3) / 4;
-    overlap_warp_kernel<T><<<blocks, kWmThreads, wm_smem(M, n_up, n_dn), st>>>(
-        W, M, n_up, n_dn, Phi, PsiT, Theta, ldt, dn_off, logdet, flags);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !flags) return e;
-    // ill-conditioned matrices again, in FP64 arithmetic
-    overlap_kernel<T, double><<<grid, threads, smem64, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                            ldt, dn_off, logdet, nullptr,
-                                                            nmax, flags);
-    return cudaGetLastError();
-  }
   if (fp64_compute) {
     if (smem64 > cap64) return cudaErrorInvalidValue;
     overlap_kernel<T, double><<<grid, threads, smem64, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                            ldt, dn_off, logdet, Ainv, nmax,
-                                                            nullptr);
+                                                            ldt, dn_off, logdet, Ainv, nmax);
   } else {
     static const size_t cap = allow_big_smem(overlap_kernel<T, float>);
     const size_t smem = overlap_smem(M, nmax, sizeof(float2));
     if (smem > cap) return cudaErrorInvalidValue;
     overlap_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                         ldt, dn_off, logdet, Ainv, nmax,
-                                                         nullptr);
+                                                         ldt, dn_off, logdet, Ainv, nmax);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
-                           const double2* lw, double dtau, double e_shift,
-                           double* weight, double2* logO, long long* ctr) {
-  weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, lw, dtau, e_shift,
-                                                     weight, logO, ctr);
+                           const double2* lw, double dtau, double e_shift, double cap,
+                           const double* wref, double* weight, double2* logO,
+                           long long* ctr) {
+  weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, lw, dtau, e_shift, cap,
+                                                     wref, weight, logO, ctr);
   return cudaGetLastError();
 }
 
@@ -1129,12 +870,12 @@ cudaError_t launch_qr(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
     static const size_t cap = allow_big_smem(qr_kernel<T, double>);
     const size_t smem = sizeof(double2) * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
     if (smem > cap) return cudaErrorInvalidValue;
-    qr_kernel<T, double><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr, nullptr);
+    qr_kernel<T, double><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   } else {
     static const size_t cap = allow_big_smem(qr_kernel<T, float>);
     const size_t smem = sizeof(float2) * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
     if (smem > cap) return cudaErrorInvalidValue;
-    qr_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr, nullptr);
+    qr_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1261,7 +1002,7 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
                                         const T*, T*);                                  \
   template cudaError_t launch_overlap<T>(cudaStream_t, int, int, int, int, const T*,    \
                                          const T*, T*, long, long, double2*, double2*,  \
-                                         bool, int*);                                   \
+                                         bool);                                         \
   template cudaError_t launch_qr<T>(cudaStream_t, int, int, int, int, T*, double2*,     \
                                     double*, bool);                                     \
   template cudaError_t launch_energy_reduce<T>(cudaStream_t, int, int, int, int, int,   \

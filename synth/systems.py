@@ -57,6 +57,7 @@ class System:
     taylor_order: int = 6
     fb_cap: float = 1.0
     run_id: int = 0
+    weight_cap: int = 0
 
     @property
     def M(self) -> int:

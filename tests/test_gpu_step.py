@@ -123,6 +123,16 @@ def test_c2_full_size_sampled_fp32(islands):
     print(f"c2 fp32 islands={islands} worst", w)
 
 
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-10), ("tf32x3", 1e-4)])
+def test_weight_cap_matches_oracle(prec, rtol):
+    # a cap of 1x the last comb's common weight binds on most steps
+    s = small_system(M=12, n_up=3, n_dn=3, n_chol=16, seed=11, n_walkers=24, dtau=0.02,
+                     l_sigma=0.1, ortho_every=2, measure_every=6, pc_every=3,
+                     trial="eig").replace(weight_cap=1)
+    w = side_by_side(s, prec, 12, rtol, energy_at=(6, 12))
+    print(f"weight cap {prec} worst", w)
+
+
 def test_checkpoint_resume_is_bitwise():
     s = config_c1()
     gpu = gpu_ctx(s, precision="fp64")

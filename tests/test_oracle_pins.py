@@ -305,6 +305,34 @@ def test_weight_update_phaseless_cut():
     assert abs(out[3] - np.exp(0.5 - 0.01)) < 1e-15
 
 
+def test_weight_cap_option():
+    # the cap (an option beside the paper's step) clips at cap * w_ref and
+    # changes nothing below it; an unbounded cap is the uncapped update
+    w = np.array([1.0, 2.0, 0.0, 1.0])
+    lo = np.zeros(4, complex)
+    ln = np.array([0.1 + 0.2j, 1.5 + 0.1j, 0.0, 0.5 + 0j])
+    x = np.zeros((4, 2))
+    xb = np.zeros((4, 2), complex)
+    free = O.update_weights(w, lo, ln, x, xb, 0.01, -1.0)
+    capped = O.update_weights(w, lo, ln, x, xb, 0.01, -1.0, cap=2, w_ref=0.75)
+    assert np.array_equal(capped, np.minimum(free, 1.5))
+    assert capped[1] == 1.5 and capped[0] == free[0] and capped[2] == 0.0
+    assert np.array_equal(O.update_weights(w, lo, ln, x, xb, 0.01, -1.0, cap=10 ** 9), free)
+    # in a run the reference is the common weight of the last comb
+    s = small_system(M=6, n_up=2, n_dn=2, n_chol=8, seed=3, n_walkers=16, dtau=0.05,
+                     l_sigma=0.3, ortho_every=2, measure_every=0, pc_every=3)
+    run = O.OracleRun(s.replace(weight_cap=1))
+    ref = O.OracleRun(s)
+    bound, differs = 1.0, False
+    for k in range(1, 10):
+        run.step()
+        ref.step()
+        assert np.all(run.weight <= bound * (1 + 1e-15)) or k % 3 == 0
+        differs |= not np.array_equal(run.weight, ref.weight)
+        bound = run.w_ref
+    assert differs                              # the cap did bind in this run
+
+
 # ---------------------------------------------------------------- comb
 
 
