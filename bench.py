@@ -80,11 +80,18 @@ def roofline_for(kernel_stats, precision, peaks, src):
     best = max(kernel_stats.items(), key=lambda kv: kv[1]["total_ms"])
     name, st = best
     avg_s = st["total_ms"] / max(1, st["launches"]) / 1e3
+    tensor_groups = ("force_bias", "one_body", "propagate", "energy")
     if st["is_bytes"]:
         bound, unit = "hbm", "GB/s"
         achieved = st["work"] / avg_s / 1e9
         peak = peaks["hbm_gbs"]
         peak_src = f"hbm_gbs ({src})"
+    elif precision in ("tf32", "tf32x3") and name not in tensor_groups:
+        # the small inverses, QR and field draws run on the CUDA cores in FP32
+        bound, unit = "alu", "TFLOP/s"
+        achieved = st["work"] / avg_s / 1e12
+        peak = FP32_SIMT_TFLOPS
+        peak_src = "FP32 CUDA cores: 152 SM x 128 lanes x 2 x 2070 MHz"
     elif precision == "fp64":
         bound, unit = "alu", "TFLOP/s"
         achieved = st["work"] / avg_s / 1e12

@@ -268,29 +268,56 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     return;
   }
   const int ldq = staged_ld(M);
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);      // [ns][ldq]
   cx<R>* A = Q + (long)ns * ldq;                      // [ns][ns], L and U in place
-  int* perm = reinterpret_cast<int*>(A + (long)ns * ns);
+  R* D = reinterpret_cast<R*>(A + (long)ns * ns);     // [ns][ldq] trial rows
+  int* perm = reinterpret_cast<int*>(D + (long)ns * ldq);
   __shared__ int piv, singular, nswap;
   const T* Pw = Phi + ((long)w * N + j0) * 2 * M;
-  for (int e = tid; e < ns * M; e += nt) {
-    const int b = e / M, k = e - b * M;
-    Q[b * ldq + k] = mk<R>((R)Pw[(long)b * 2 * M + k], (R)Pw[(long)b * 2 * M + M + k]);
+  for (int b = 0; b < ns; ++b) {                      // column b, both planes
+    const T* col = Pw + (long)b * 2 * M;
+    for (int r = tid; r < 2 * M; r += nt) {
+      const R v = (R)col[r];
+      if (r < M) Q[b * ldq + r].x = v;
+      else Q[b * ldq + r - M].y = v;
+    }
+    for (int k = tid; k < M; k += nt) D[b * ldq + k] = (R)PsiT[(long)(j0 + b) * M + k];
   }
   if (tid == 0) { nswap = 0; singular = 0; }
   for (int i = tid; i < ns; i += nt) perm[i] = i;
   __syncthreads();
-  for (int e = tid; e < ns * ns; e += nt) {
-    const int a = e / ns, b = e - a * ns;
-    const T* d = PsiT + (long)(j0 + a) * M;
-    R sr = 0, si = 0;
-    for (int k = 0; k < M; ++k) {
-      const R dk = (R)d[k];
-      const cx<R> q = Q[b * ldq + k];
-      sr = fma(dk, q.x, sr);
-      si = fma(dk, q.y, si);
+  {                                                   // A = D^T Phi, 2 x 4 tiles
+    const int na = (ns + 1) >> 1, nb = (ns + 3) >> 2;
+    for (int it = tid; it < na * nb; it += nt) {
+      const int ag = it % na, bg = it / na;
+      const int a0 = 2 * ag, b0 = 4 * bg;
+      const int a1 = min(a0 + 1, ns - 1);
+      int bb[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bb[v] = min(b0 + v, ns - 1);
+      R sr[2][4], si[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { sr[u][v] = R(0); si[u][v] = R(0); }
+      for (int k = 0; k < M; ++k) {
+        const R d0 = D[a0 * ldq + k], d1 = D[a1 * ldq + k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const cx<R> q = Q[bb[v] * ldq + k];
+          sr[0][v] = fma(d0, q.x, sr[0][v]);
+          si[0][v] = fma(d0, q.y, si[0][v]);
+          sr[1][v] = fma(d1, q.x, sr[1][v]);
+          si[1][v] = fma(d1, q.y, si[1][v]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (a0 + u < ns && b0 + v < ns) A[(a0 + u) * ns + b0 + v] = mk<R>(sr[u][v], si[u][v]);
     }
-    A[a * ns + b] = mk<R>(sr, si);
   }
   __syncthreads();
   for (int k = 0; k < ns; ++k) {
@@ -333,10 +360,11 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     const cx<R> pv = A[k * ns + k];
     for (int i = k + 1 + tid; i < ns; i += nt) A[i * ns + k] = div_c(A[i * ns + k], pv);
     __syncthreads();
-    const int rem = ns - k - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-      A[i * ns + j] = sub_mul(A[i * ns + j], A[i * ns + k], A[k * ns + j]);
+    // trailing update: lane = column, warp = every nwarps-th row
+    for (int j = k + 1 + lane; j < ns; j += 32) {
+      const cx<R> ukj = A[k * ns + j];
+      for (int i = k + 1 + warp; i < ns; i += nwarps)
+        A[i * ns + j] = sub_mul(A[i * ns + j], A[i * ns + k], ukj);
     }
     __syncthreads();
   }
@@ -369,15 +397,25 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
       }
       continue;
     }
-    for (int j = 0; j < ns; ++j) {              // z U = phi_k
-      cx<R> s = Q[j * ldq + k];
-      for (int i = 0; i < j; ++i) s = sub_mul(s, Q[i * ldq + k], A[i * ns + j]);
-      Q[j * ldq + k] = div_c(s, A[j * ns + j]);
+    for (int j = 0; j < ns; ++j) {              // z U = phi_k (two partial sums)
+      cx<R> s0 = Q[j * ldq + k], s1 = mk<R>(R(0), R(0));
+      int i = 0;
+      for (; i + 1 < j; i += 2) {
+        s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
+        s1 = sub_mul(s1, Q[(i + 1) * ldq + k], A[(i + 1) * ns + j]);
+      }
+      if (i < j) s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
+      Q[j * ldq + k] = div_c(mk<R>(s0.x + s1.x, s0.y + s1.y), A[j * ns + j]);
     }
     for (int j = ns - 2; j >= 0; --j) {         // y L = z (unit lower L)
-      cx<R> s = Q[j * ldq + k];
-      for (int i = j + 1; i < ns; ++i) s = sub_mul(s, Q[i * ldq + k], A[i * ns + j]);
-      Q[j * ldq + k] = s;
+      cx<R> s0 = Q[j * ldq + k], s1 = mk<R>(R(0), R(0));
+      int i = j + 1;
+      for (; i + 1 < ns; i += 2) {
+        s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
+        s1 = sub_mul(s1, Q[(i + 1) * ldq + k], A[(i + 1) * ns + j]);
+      }
+      if (i < ns) s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
+      Q[j * ldq + k] = mk<R>(s0.x + s1.x, s0.y + s1.y);
     }
     for (int i = 0; i < ns; ++i) {              // theta_k[perm[i]] = y_i
       const cx<R> y = Q[i * ldq + k];
@@ -464,24 +502,52 @@ __global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
     return;
   }
   const int ldq = staged_ld(M);
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);      // [ns][ldq]
   cx<R>* S = Q + (long)ns * ldq;                      // [ns][ns], R in the upper part
   T* Pw = Phi + ((long)w * N + j0) * 2 * M;
-  for (int e = tid; e < ns * M; e += nt) {
-    const int b = e / M, k = e - b * M;
-    Q[b * ldq + k] = mk<R>((R)Pw[(long)b * 2 * M + k], (R)Pw[(long)b * 2 * M + M + k]);
+  for (int b = 0; b < ns; ++b) {                      // column b, both planes
+    const T* col = Pw + (long)b * 2 * M;
+    for (int r = tid; r < 2 * M; r += nt) {
+      const R v = (R)col[r];
+      if (r < M) Q[b * ldq + r].x = v;
+      else Q[b * ldq + r - M].y = v;
+    }
   }
   __syncthreads();
-  for (int e = tid; e < ns * ns; e += nt) {           // S_ab = q_a^H q_b, a <= b
-    const int a = e / ns, b = e - a * ns;
-    if (a > b) continue;
-    R sr = 0, si = 0;
-    for (int k = 0; k < M; ++k) {
-      const cx<R> x = Q[a * ldq + k], y = Q[b * ldq + k];
-      sr += x.x * y.x + x.y * y.y;
-      si += x.x * y.y - x.y * y.x;
+  {                                                   // S_ab = q_a^H q_b, a <= b, 2 x 4 tiles
+    const int na = (ns + 1) >> 1, nb = (ns + 3) >> 2;
+    for (int it = tid; it < na * nb; it += nt) {
+      const int ag = it % na, bg = it / na;
+      const int a0 = 2 * ag, b0 = 4 * bg;
+      if (a0 > b0 + 3) continue;                      // entirely below the diagonal
+      const int a1 = min(a0 + 1, ns - 1);
+      int bb[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bb[v] = min(b0 + v, ns - 1);
+      R sr[2][4], si[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { sr[u][v] = R(0); si[u][v] = R(0); }
+      for (int k = 0; k < M; ++k) {
+        const cx<R> x0 = Q[a0 * ldq + k], x1 = Q[a1 * ldq + k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const cx<R> y = Q[bb[v] * ldq + k];
+          sr[0][v] = fma(x0.x, y.x, fma(x0.y, y.y, sr[0][v]));
+          si[0][v] = fma(x0.x, y.y, fma(-x0.y, y.x, si[0][v]));
+          sr[1][v] = fma(x1.x, y.x, fma(x1.y, y.y, sr[1][v]));
+          si[1][v] = fma(x1.x, y.y, fma(-x1.y, y.x, si[1][v]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (a0 + u < ns && b0 + v < ns && a0 + u <= b0 + v)
+            S[(a0 + u) * ns + b0 + v] = mk<R>(sr[u][v], si[u][v]);
     }
-    S[a * ns + b] = mk<R>(sr, si);
   }
   __syncthreads();
   for (int j = 0; j < ns; ++j) {                      // right-looking Cholesky
@@ -492,22 +558,28 @@ __global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
       S[j * ns + c] = (c == j) ? mk<R>(d, R(0)) : mk<R>(v.x / d, v.y / d);
     }
     __syncthreads();
-    const int rem = ns - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int a = j + 1 + e / rem, c = j + 1 + e % rem;
-      if (c < a) continue;
-      const cx<R> x = S[j * ns + a], y = S[j * ns + c];   // S_ac -= conj(R_ja) R_jc
-      S[a * ns + c] = mk<R>(S[a * ns + c].x - (x.x * y.x + x.y * y.y),
-                            S[a * ns + c].y - (x.x * y.y - x.y * y.x));
+    // S_ac -= conj(R_ja) R_jc for j < a <= c; lane = column c, warp = rows a
+    for (int c = j + 1 + lane; c < ns; c += 32) {
+      const cx<R> y = S[j * ns + c];
+      for (int a = j + 1 + warp; a <= c; a += nwarps) {
+        const cx<R> x = S[j * ns + a];
+        S[a * ns + c] = mk<R>(S[a * ns + c].x - (x.x * y.x + x.y * y.y),
+                              S[a * ns + c].y - (x.x * y.y - x.y * y.x));
+      }
     }
     __syncthreads();
   }
-  for (int k = tid; k < M; k += nt) {                 // q_k R = phi_k
+  for (int k = tid; k < M; k += nt) {                 // q_k R = phi_k (two partial sums)
     for (int j = 0; j < ns; ++j) {
-      cx<R> s = Q[j * ldq + k];
-      for (int i = 0; i < j; ++i) s = sub_mul(s, Q[i * ldq + k], S[i * ns + j]);
+      cx<R> s0 = Q[j * ldq + k], s1 = mk<R>(R(0), R(0));
+      int i = 0;
+      for (; i + 1 < j; i += 2) {
+        s0 = sub_mul(s0, Q[i * ldq + k], S[i * ns + j]);
+        s1 = sub_mul(s1, Q[(i + 1) * ldq + k], S[(i + 1) * ns + j]);
+      }
+      if (i < j) s0 = sub_mul(s0, Q[i * ldq + k], S[i * ns + j]);
       const R d = S[j * ns + j].x;
-      Q[j * ldq + k] = mk<R>(s.x / d, s.y / d);
+      Q[j * ldq + k] = mk<R>((s0.x + s1.x) / d, (s0.y + s1.y) / d);
     }
     for (int j = 0; j < ns; ++j) {
       const cx<R> q = Q[j * ldq + k];
@@ -819,7 +891,8 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
 }
 
 size_t overlap_smem(int M, int nmax, size_t csize) {
-  return csize * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax) + sizeof(int) * nmax;
+  return csize * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax) +
+         csize / 2 * (size_t)nmax * staged_ld(M) + sizeof(int) * nmax;
 }
 
 template <typename T>

@@ -2,9 +2,11 @@
 
 The reduced-precision paths must reproduce the FP64 GPU path's mixed
 estimate (Sec. II, sum_w W Re E_L / sum_w W, measured every 0.1 Ha^-1 as in
-Sec. IV.A) within 0.5 mHa. The FP64 path itself agrees with the FP64 oracle
-walker by walker over the first 20 shared-draw steps (test_gpu_step.py), so
-it stands in for the oracle at lengths the oracle cannot follow.
+Sec. IV.A): the error the precision adds must stay within 0.5 mHa, and
+independent long runs must agree within their combined error bar. The FP64
+path itself agrees with the FP64 oracle walker by walker over the first 20
+shared-draw steps (test_gpu_step.py), so it stands in for the oracle at
+lengths the oracle cannot follow.
 
 Two checks, both on the plain 10-orbital system (5+5 electrons, 40 dense
 fields, trial of h1 eigenvectors), whose mixed estimate is stationary after
@@ -14,12 +16,13 @@ ground state and keep drifting for longer than a test can follow):
 * paired: both runs draw the same fields and the comb is off, so walker i of
   one run is walker i of the other for the whole run; the difference of the
   two mixed estimates, measurement by measurement, is the precision error
-  alone, free of statistical noise;
+  alone, free of statistical noise: it must stay within 0.5 mHa;
 * independent: with the comb on, the runs part ways after a few hundred
   steps (a tooth of the comb lands on the other side of a walker boundary),
-  so their long-run means are compared through their reblocked error bars:
-  within 0.5 mHa and within twice the combined error bar. These runs use the
-  weight cap option (below).
+  so their long-run means differ by statistical noise of about 1 mHa at this
+  length (50 million walker-steps each); they must agree within twice the
+  combined reblocked error bar. These runs use the weight cap option
+  (below).
 """
 import numpy as np
 import pytest
@@ -94,5 +97,4 @@ def test_long_run_energy_matches_fp64(fp64_indep, prec):
     combined = float(np.hypot(ea, eb))
     print(f"long run c1 {prec}: E_fp64 = {np.mean(a):.6f} +- {ea:.6f}, E = {np.mean(b):.6f} "
           f"+- {eb:.6f}, diff = {diff / MHA:.4f} mHa, combined bar {combined / MHA:.4f} mHa")
-    assert abs(diff) <= 0.5 * MHA
     assert abs(diff) <= 2.0 * combined
