@@ -347,20 +347,18 @@ __device__ __forceinline__ void put_operand(unsigned char* hi, unsigned char* lo
   }
 }
 
-// D (+)= A B with both operands in shared memory (the half-step image); B is
-// N x 128 K-major with K blocks of 32 values `bkb` bytes apart.
+// D (+)= A B with both operands in shared memory (the half-step image).
 template <bool SPLIT3>
 __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint32_t Alo,
-                                               uint32_t Bhi, uint32_t Blo, uint32_t bkb,
-                                               uint32_t id) {
+                                               uint32_t Bhi, uint32_t Blo, uint32_t id) {
 #pragma unroll
   for (int ks = 0; ks < 16; ++ks) {
     const int kb = ks >> 2, koff = (ks & 3) * 32;
     const uint64_t ad = desc_sw128(Ahi + kb * 16384 + koff);
-    const uint64_t bd = desc_sw128(Bhi + kb * bkb + koff);
+    const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
     mma_tf32(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
     if (SPLIT3) {
-      mma_tf32(tmem, ad, desc_sw128(Blo + kb * bkb + koff), id, 1u);
+      mma_tf32(tmem, ad, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
       mma_tf32(tmem, desc_sw128(Alo + kb * 16384 + koff), bd, id, 1u);
     }
   }
@@ -369,15 +367,14 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint
 // D = A B with A in tensor memory (the operator) and B in shared memory.
 template <bool SPLIT3>
 __device__ __forceinline__ void issue_products_ts(uint32_t tD, uint32_t tAhi, uint32_t tAlo,
-                                                  uint32_t Bhi, uint32_t Blo, uint32_t bkb,
-                                                  uint32_t id) {
+                                                  uint32_t Bhi, uint32_t Blo, uint32_t id) {
 #pragma unroll
   for (int ks = 0; ks < 16; ++ks) {
     const int kb = ks >> 2, koff = (ks & 3) * 32;
-    const uint64_t bd = desc_sw128(Bhi + kb * bkb + koff);
+    const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
     mma_tf32_ts(tD, tAhi + 8 * ks, bd, id, ks > 0 ? 1u : 0u);
     if (SPLIT3) {
-      mma_tf32_ts(tD, tAhi + 8 * ks, desc_sw128(Blo + kb * bkb + koff), id, 1u);
+      mma_tf32_ts(tD, tAhi + 8 * ks, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
       mma_tf32_ts(tD, tAlo + 8 * ks, bd, id, 1u);
     }
   }
@@ -393,21 +390,17 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   // image hi and lo are adjacent so one bulk copy fills both
   unsigned char* Ihi = base;
   unsigned char* Ilo = base + TY_A_BYTES;
-  // the term t as two 32-column halves (chunks), each 32 x 128 K-major:
-  // hi of chunk c at Bhi + c * TY_BC_BYTES, lo at Blo + c * TY_BC_BYTES
   unsigned char* Bhi = base + TY_A_BYTES * (SPLIT3 ? 2 : 1);
   unsigned char* Blo = Bhi + TY_B_BYTES;
   uint64_t* bar = (uint64_t*)(base + (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1));
-  uint64_t* lbar = bar + 2;
-  uint64_t* vbar = bar + 3;
-  uint32_t* tslot = (uint32_t*)(bar + 4);
+  uint64_t* lbar = bar + 1;
+  uint64_t* vbar = bar + 2;
+  uint32_t* tslot = (uint32_t*)(bar + 3);
   // TF32X3 with M even: the next walker's V (2 M^2 floats, contiguous) is
   // bulk-copied into the spare shared memory while this walker's series runs
   float* vst = (float*)(base + (TY_A_BYTES + TY_B_BYTES) * 2 + 128);
   __shared__ int s_fail;
   constexpr uint32_t kCols = SPLIT3 ? 512 : 256;
-  constexpr uint32_t TY_BC_BYTES = TY_B_BYTES / 2;   // one 32-column chunk
-  constexpr uint32_t BKB = 32 * 128;                 // bytes per K block of a chunk
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -417,8 +410,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   const uint32_t img_bytes = (uint32_t)TY_A_BYTES * (SPLIT3 ? 2u : 1u);
   if (tid == 0) {
     s_fail = 0;
-    mbar_init(smem_u32(&bar[0]), 1);
-    mbar_init(smem_u32(&bar[1]), 1);
+    mbar_init(smem_u32(bar), 1);
     mbar_init(smem_u32(lbar), 1);
     mbar_init(smem_u32(vbar), 1);
     mbar_fence_init();
@@ -427,21 +419,21 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const uint32_t tmem = *tslot;              // chunk c accumulates in columns 32c .. 32c+31
+  const uint32_t tmem = *tslot;
   const uint32_t tAhi = tmem + TY_TMEM_AHI, tAlo = tmem + TY_TMEM_ALO;
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  const uint32_t id = idesc_tf32(128, 32);
-  uint32_t phase[2] = {0u, 0u};
+  const uint32_t id = idesc_tf32(128, 64);
+  uint32_t phase = 0;
   const int r = tid;                       // embedded row / K index owned
   const int rc = r >> 6, rr = r & 63;      // component (0 re, 1 im), orbital row
   const uint32_t sIhi = smem_u32(Ihi), sIlo = smem_u32(Ilo);
   const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
   const int MM = M * M;
 
-  // wait for chunk c's MMAs; flags a timeout
-  auto wait_mma = [&](int c) {
-    const bool ok = mbar_wait(smem_u32(&bar[c]), phase[c]);
-    phase[c] ^= 1u;
+  // wait for the MMAs just issued; flags a timeout
+  auto wait_mma = [&]() {
+    const bool ok = mbar_wait(smem_u32(bar), phase);
+    phase ^= 1u;
     if (!ok) {
       flag_timeout(status);
       s_fail = 1;
@@ -453,25 +445,6 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-  };
-  // this thread's element (column j, K = r) of the B operand
-  auto put_t = [&](int j, float x) {
-    put_operand<SPLIT3>(Bhi, Blo, (uint32_t)(j >> 5) * TY_BC_BYTES + sw128_offset(j & 31, r, 32),
-                        x);
-  };
-  auto series_mma = [&](int c) {           // D_c = A t_c, A from tensor memory
-    if (tid == 0) {
-      issue_products_ts<SPLIT3>(tmem + 32u * c, tAhi, tAlo, sBhi + c * TY_BC_BYTES,
-                                sBlo + c * TY_BC_BYTES, BKB, id);
-      mma_commit(smem_u32(&bar[c]));
-    }
-  };
-  auto half_mma = [&](int c) {             // D_c = dB t_c, the image from shared memory
-    if (tid == 0) {
-      issue_products<SPLIT3>(tmem + 32u * c, sIhi, sIlo, sBhi + c * TY_BC_BYTES,
-                             sBlo + c * TY_BC_BYTES, BKB, id);
-      mma_commit(smem_u32(&bar[c]));
-    }
   };
   bool img_pending = false;
   if (fuse_b) {                            // the half-step image, once per CTA
@@ -500,15 +473,15 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     const int j0 = (item - w * nchunk) * 64;
     const int nc = min(64, N - j0);
     const float* Vw = V + (long)w * 2 * MM;
-    // ---- t0 = the item's columns; this thread's row of it seeds the sum
+    // ---- t0 = the chunk's columns; this thread's row of it seeds the sum
     float acc[64];
     const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
 #pragma unroll
     for (int j = 0; j < 64; ++j)
       acc[j] = (j < nc && rr < M) ? Pw[((long)j * 2 + rc) * M + rr] : 0.f;
 #pragma unroll
-    for (int j = 0; j < 64; ++j) put_t(j, acc[j]);
-    if (fuse_b) {                          // t0 = Phi + dB Phi, chunk 1's MMAs under chunk 0's epilogue
+    for (int j = 0; j < 64; ++j) put_operand<SPLIT3>(Bhi, Blo, sw128_offset(j, r, 64), acc[j]);
+    if (fuse_b) {                          // t0 = Phi + dB Phi
       if (img_pending) {
         if (!mbar_wait(smem_u32(lbar), 0)) {
           flag_timeout(status);
@@ -517,17 +490,19 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         img_pending = false;
       }
       sync_for_mma();
-      half_mma(0);
-      half_mma(1);
+      if (tid == 0) {
+        issue_products<SPLIT3>(tmem, sIhi, sIlo, sBhi, sBlo, id);
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        wait_mma(c);
+      for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + lane_base + 32u * c, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          acc[32 * c + j] += v[j];
-          put_t(32 * c + j, acc[32 * c + j]);
+          acc[c0 + j] += v[j];
+          put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64), acc[c0 + j]);
         }
       }
     }
@@ -585,42 +560,41 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
       const int next = item + (int)gridDim.x;
       if (next < items && !s_fail) load_v(next);
     }
-    // ---- the series, the two chunks half a term apart: chunk 1's MMAs run
-    // under chunk 0's epilogue and chunk 0's next MMAs under chunk 1's
-    sync_for_mma();
-    series_mma(0);
-    series_mma(1);
     for (int term = 1; term <= order; ++term) {
+      sync_for_mma();
+      if (tid == 0) {
+        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id);
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
       const float inv = 1.0f / (float)term;
-      const bool more = term < order;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        wait_mma(c);
+      for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + lane_base + 32u * c, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float x = v[j] * inv;
-          acc[32 * c + j] += x;
-          if (more || fuse_b) put_t(32 * c + j, more ? x : acc[32 * c + j]);
-        }
-        if (more) {
-          sync_for_mma();
-          series_mma(c);
+          acc[c0 + j] += x;
+          if (term < order || fuse_b)
+            put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64),
+                                term < order ? x : acc[c0 + j]);
         }
       }
     }
     if (fuse_b) {                          // out = s + dB s
       sync_for_mma();
-      half_mma(0);
-      half_mma(1);
+      if (tid == 0) {
+        issue_products<SPLIT3>(tmem, sIhi, sIlo, sBhi, sBlo, id);
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        wait_mma(c);
+      for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + lane_base + 32u * c, v);
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[32 * c + j] += v[j];
+        for (int j = 0; j < 32; ++j) acc[c0 + j] += v[j];
       }
     }
     float* Ow = Pout + ((long)w * N + j0) * 2 * M;
