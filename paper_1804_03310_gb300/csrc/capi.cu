@@ -66,6 +66,9 @@ struct afqmc_ctx {
   void *Phi, *Phi2, *Phi3, *Theta, *Theta2, *V, *X, *S, *xbar, *Z;
   // precomputed operators in the step precision
   void *L, *Ltil, *Bhalf, *PsiT, *Yx_up, *Yx_dn;
+  // TF32X3: the constant GEMM operands hold their TF32 hi part, these the
+  // remainders (split once at setup)
+  void *Ltil_lo, *LT_lo, *Yx_up_lo, *Yx_dn_lo;
   double* PsiT64;
   double *weight, *scan, *wnew, *escalar, *lr;
   double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
@@ -266,7 +269,8 @@ afqmc_status force_bias_contraction(afqmc_ctx* c) {
   if (c->tc) {
     LK(tc_gemm(c->tc, c->st, 2 * W, G + 1, (int)ld, (const float*)A, ld, (const float*)B, ld,
                (float*)c->X, c->ldx, 1.0f, 0.0f, nullptr, 0, c->split3, c->xsplit,
-               2L * W * c->ldx, c->status, c->bn_fb));
+               2L * W * c->ldx, c->status, c->bn_fb,
+               md ? nullptr : (const float*)c->Ltil_lo));
   } else {
     LK(gemm<T>(c->st, false, true, 2 * W, G + 1, (int)ld, T(1), (const T*)A, ld, 0,
                (const T*)B, ld, 0, T(0), (T*)c->X, c->ldx, 0, 1));
@@ -302,7 +306,8 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
       if (c->tc) {
         LK(tc_gemm(c->tc, c->st, 2 * W, (int)J, (int)J, (const float*)c->Theta + off, c->ldt,
                    (const float*)Y, ldz, (float*)c->Z + zoff, ldz, 1.0f, 0.0f, nullptr, 0,
-                   c->split3, 1, 0, c->status, c->bn_e));
+                   c->split3, 1, 0, c->status, c->bn_e,
+                   (const float*)(sig ? c->Yx_dn_lo : c->Yx_up_lo)));
       } else {
         LK(gemm<T>(c->st, false, false, 2 * W, (int)J, (int)J, T(1),
                    (const T*)c->Theta + off, c->ldt, 0, Y, ldz, 0, T(0), (T*)c->Z + zoff,
@@ -441,7 +446,7 @@ afqmc_status step_T(afqmc_ctx* c) {
     if (c->tc) {
       LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
                  (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
-                 nullptr, 0, c->split3, 1, 0, c->status, c->bn_v));
+                 nullptr, 0, c->split3, 1, 0, c->status, c->bn_v, (const float*)c->LT_lo));
     } else {
       LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, c->ldS, 0,
                  (const T*)c->L, (long)M * M, 0, T(0), (T*)c->V, (long)M * M, 0, 1));
@@ -675,6 +680,12 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     if (c->bimg)
       LK(tc_bhalf_image(st, M, (const float*)c->dB, (float*)c->bimg, c->split3));
   }
+  if (c->split3) {   // the constant operands of the TF32X3 contractions, split once
+    LK(tc_split(st, (long)(G + 1) * c->ldt, (float*)c->Ltil, (float*)c->Ltil_lo));
+    LK(tc_split(st, (long)MM * c->ldS, (float*)c->LT, (float*)c->LT_lo));
+    LK(tc_split(st, (long)c->nu * M * c->Jp[0], (float*)c->Yx_up, (float*)c->Yx_up_lo));
+    LK(tc_split(st, (long)c->nd * M * c->Jp[1], (float*)c->Yx_dn, (float*)c->Yx_dn_lo));
+  }
   LK(launch_convert<T>(st, MM, Bh, (T*)c->Bhalf));
   LK(launch_convert<T>(st, (long)N * M, PsiT, (T*)c->PsiT));
   if (c->md) {   // C_act^T L_g and C_act^T h1 per spin, [G+1][ldg]
@@ -894,7 +905,7 @@ afqmc_status autotune(afqmc_ctx* c) {
       const float ms = best_ms(c, [&]() -> afqmc_status {
         LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
                    (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
-                   nullptr, 0, c->split3, 1, 0, c->status, bn));
+                   nullptr, 0, c->split3, 1, 0, c->status, bn, (const float*)c->LT_lo));
         return AFQMC_OK;
       });
       if (ms < best) { best = ms; v.bn_v = bn; }
@@ -914,7 +925,7 @@ afqmc_status autotune(afqmc_ctx* c) {
           LK(tc_gemm(c->tc, c->st, 2 * W, (int)J, (int)J, (const float*)c->Theta + off,
                      c->ldt, (const float*)(sig ? c->Yx_dn : c->Yx_up), ldz,
                      (float*)c->Z + zoff, ldz, 1.0f, 0.0f, nullptr, 0, c->split3, 1, 0,
-                     c->status, bn));
+                     c->status, bn, (const float*)(sig ? c->Yx_dn_lo : c->Yx_up_lo)));
           zoff += 2L * W * ldz;
         }
         return AFQMC_OK;
@@ -1122,6 +1133,12 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->Yx_up, (size_t)P.nu * M * P.Jp[0] * es);
   add(&c->Yx_dn, (size_t)P.nd * M * P.Jp[1] * es);
   if (P.tcmode) add(&c->LT, MM * P.ldS * es);
+  if (P.split3) {
+    add(&c->Ltil_lo, (G + 1) * P.ldt * es);
+    add(&c->LT_lo, MM * P.ldS * es);
+    add(&c->Yx_up_lo, (size_t)P.nu * M * P.Jp[0] * es);
+    add(&c->Yx_dn_lo, (size_t)P.nd * M * P.Jp[1] * es);
+  }
   if (!P.fp64) add(&c->dB, MM * es);
   if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_floats(P.split3) * sizeof(float));
   add(&c->weight, W * sizeof(double));

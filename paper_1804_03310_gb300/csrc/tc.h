@@ -18,10 +18,15 @@ void tc_destroy(TcCtx* t);
 // partial sums to C + s * split_stride (beta must then be 0). bn is the
 // output tile width (64 or 128; 0 picks 64 for n <= 64, else 128). A
 // device-side wait that times out sets bit 4 of *status.
+// With split3 and Blo, B already holds hi = B rounded to TF32 and Blo the
+// remainder (see tc_split), so only A is split on the fly.
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
                     long lda, const float* B, long ldb, float* C, long ldc, float alpha,
                     float beta, const float* R, long ldr, bool split3, int ksplit,
-                    long split_stride, int* status, int bn = 0);
+                    long split_stride, int* status, int bn = 0, const float* Blo = nullptr);
+
+// x <- x rounded to TF32, lo <- the remainder (exact), n floats.
+cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo);
 
 // Taylor propagation of W walkers (M <= 64): Pout = sum_{n<=order} V^n Pin / n!
 // with V [W][2][M][M] and Pin, Pout [W][N][2][M], on the tensor cores. With a
