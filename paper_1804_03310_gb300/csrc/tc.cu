@@ -76,10 +76,11 @@ struct GemmWork {
   }
 };
 
-template <int BN, bool SPLIT3>
+template <int BN, bool SPLIT3, bool BLO>
 __global__ void __launch_bounds__(GemmCfg<BN, SPLIT3>::THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-               const __grid_constant__ CUtensorMap mapB, int m, int n, GemmWork wk,
+               const __grid_constant__ CUtensorMap mapB,
+               const __grid_constant__ CUtensorMap mapBlo, int m, int n, GemmWork wk,
                float* __restrict__ C, long ldc, float alpha,
                float beta, const float* __restrict__ R, long ldr, long split_stride,
                int* status) {
@@ -138,9 +139,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             *fail = 1;
             break;
           }
-          mbar_arrive_expect_tx(smem_u32(&full[s]), Cfg::A_BYTES + Cfg::B_BYTES);
+          mbar_arrive_expect_tx(smem_u32(&full[s]),
+                                Cfg::A_BYTES + Cfg::B_BYTES * (BLO ? 2 : 1));
           tma_load_2d(smem_u32(a_hi(s)), &mapA, (kt0 + k) * BK, m0, smem_u32(&full[s]));
           tma_load_2d(smem_u32(b_hi(s)), &mapB, (kt0 + k) * BK, n0, smem_u32(&full[s]));
+          if (BLO)   // the constant operand arrives already split (hi, lo)
+            tma_load_2d(smem_u32(b_lo(s)), &mapBlo, (kt0 + k) * BK, n0, smem_u32(&full[s]));
         }
       }
     }
@@ -268,14 +272,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
           ah[e] = h;
           al[e] = l;
         }
-        float4* bh = (float4*)b_hi(s);
-        float4* bl = (float4*)b_lo(s);
-        for (int e = t; e < Cfg::B_BYTES / 16; e += 128) {
-          float4 x = bh[e], h, l;
-          h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
-          l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
-          bh[e] = h;
-          bl[e] = l;
+        if (!BLO) {
+          float4* bh = (float4*)b_hi(s);
+          float4* bl = (float4*)b_lo(s);
+          for (int e = t; e < Cfg::B_BYTES / 16; e += 128) {
+            float4 x = bh[e], h, l;
+            h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
+            l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+            bh[e] = h;
+            bl[e] = l;
+          }
         }
         fence_proxy_async();
         mbar_arrive(smem_u32(&conv[s]));
@@ -364,21 +370,30 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint
   }
 }
 
-// D = A B with A in tensor memory (the operator) and B in shared memory.
+// D = A B with A in tensor memory (the operator) and B in shared memory;
+// `split` selects the three-product form (TF32X3).
 template <bool SPLIT3>
 __device__ __forceinline__ void issue_products_ts(uint32_t tD, uint32_t tAhi, uint32_t tAlo,
-                                                  uint32_t Bhi, uint32_t Blo, uint32_t id) {
+                                                  uint32_t Bhi, uint32_t Blo, uint32_t id,
+                                                  bool split) {
 #pragma unroll
   for (int ks = 0; ks < 16; ++ks) {
     const int kb = ks >> 2, koff = (ks & 3) * 32;
     const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
     mma_tf32_ts(tD, tAhi + 8 * ks, bd, id, ks > 0 ? 1u : 0u);
-    if (SPLIT3) {
+    if (SPLIT3 && split) {
       mma_tf32_ts(tD, tAhi + 8 * ks, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
       mma_tf32_ts(tD, tAlo + 8 * ks, bd, id, 1u);
     }
   }
 }
+
+// A term of the series takes one product instead of three once the term it
+// multiplies has shrunk below 2^-10 of the series' first term (block-wide
+// maxima): its rounding error, 2^-10 |V| |t_{n-1}| / n, is then below 2^-20
+// of |t_0| for |V| <= 1 in the max-row-sum norm, the level of the FP32
+// accumulation itself.
+constexpr float kTaylorPlainRel = 1.0f / 1024.0f;
 
 template <bool SPLIT3>
 __global__ void __launch_bounds__(128, 1)
@@ -400,6 +415,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   // bulk-copied into the spare shared memory while this walker's series runs
   float* vst = (float*)(base + (TY_A_BYTES + TY_B_BYTES) * 2 + 128);
   __shared__ int s_fail;
+  __shared__ float s_max[2][4];           // per-warp max |t|: [0] of t_0, [1] of the last term
   constexpr uint32_t kCols = SPLIT3 ? 512 : 256;
 
   const int tid = threadIdx.x;
@@ -445,6 +461,15 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
+  };
+  // warp maximum of a non-negative value into s_max[slot][warp] (NaN wins,
+  // which keeps the three-product form)
+  auto warp_max = [&](float v, int slot) {
+    const uint32_t u = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+    if ((tid & 31) == 0) s_max[slot][warp] = __uint_as_float(u);
+  };
+  auto block_max = [&](int slot) {
+    return fmaxf(fmaxf(s_max[slot][0], s_max[slot][1]), fmaxf(s_max[slot][2], s_max[slot][3]));
   };
   bool img_pending = false;
   if (fuse_b) {                            // the half-step image, once per CTA
@@ -506,6 +531,12 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         }
       }
     }
+    if (SPLIT3) {
+      float m = 0.f;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) m = fmaxf(m, fabsf(acc[j]));
+      warp_max(m, 0);
+    }
     // ---- the operator into tensor memory: row r of [[Vr, -Vi], [Vi, Vr]],
     // columns 0..63 from plane rc of V, columns 64..127 from the other plane
     // (negated for the real rows), zero beyond M in each half
@@ -563,11 +594,14 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     for (int term = 1; term <= order; ++term) {
       sync_for_mma();
       if (tid == 0) {
-        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id);
+        bool split = true;
+        if (SPLIT3 && term >= 2) split = !(block_max(1) <= kTaylorPlainRel * block_max(0));
+        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id, split);
         mma_commit(smem_u32(bar));
       }
       wait_mma();
       const float inv = 1.0f / (float)term;
+      float m = 0.f;
 #pragma unroll
       for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
@@ -576,11 +610,13 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         for (int j = 0; j < 32; ++j) {
           const float x = v[j] * inv;
           acc[c0 + j] += x;
+          m = fmaxf(m, fabsf(x));
           if (term < order || fuse_b)
             put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64),
                                 term < order ? x : acc[c0 + j]);
         }
       }
+      if (SPLIT3) warp_max(m, 1);
     }
     if (fuse_b) {                          // out = s + dB s
       sync_for_mma();
@@ -638,19 +674,25 @@ cudaError_t make_map(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, lo
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, bool SPLIT3>
+template <int BN, bool SPLIT3, bool BLO>
 cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
-                        long lda, const float* B, long ldb, float* C, long ldc, float alpha,
-                        float beta, const float* R, long ldr, int ksplit, long split_stride,
-                        int* status) {
+                        long lda, const float* B, const float* Blo, long ldb, float* C,
+                        long ldc, float alpha, float beta, const float* R, long ldr,
+                        int ksplit, long split_stride, int* status) {
   using Cfg = GemmCfg<BN, SPLIT3>;
-  static const cudaError_t attr = set_smem(tc_gemm_kernel<BN, SPLIT3>, Cfg::SMEM);
+  static const cudaError_t attr = set_smem(tc_gemm_kernel<BN, SPLIT3, BLO>, Cfg::SMEM);
   if (attr != cudaSuccess) return attr;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mbl;
   cudaError_t e = make_map(t, &ma, A, m, k, lda, BM);
   if (e != cudaSuccess) return e;
   e = make_map(t, &mb, B, n, k, ldb, BN);
   if (e != cudaSuccess) return e;
+  if (BLO) {
+    e = make_map(t, &mbl, Blo, n, k, ldb, BN);
+    if (e != cudaSuccess) return e;
+  } else {
+    mbl = mb;
+  }
   GemmWork wk;
   wk.ktiles_total = (k + BK - 1) / BK;
   wk.ktiles_per_split = (wk.ktiles_total + ksplit - 1) / ksplit;
@@ -660,8 +702,8 @@ cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const fl
   if (items > (1L << 30)) return cudaErrorInvalidConfiguration;
   wk.items = (int)items;
   const int grid = wk.items < t->num_sms ? wk.items : t->num_sms;
-  tc_gemm_kernel<BN, SPLIT3><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(
-      ma, mb, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status);
+  tc_gemm_kernel<BN, SPLIT3, BLO><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(
+      ma, mb, mbl, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status);
   return cudaGetLastError();
 }
 
@@ -691,21 +733,39 @@ void tc_destroy(TcCtx* t) { delete t; }
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A, long lda,
                     const float* B, long ldb, float* C, long ldc, float alpha, float beta,
                     const float* R, long ldr, bool split3, int ksplit, long split_stride,
-                    int* status, int bn) {
+                    int* status, int bn, const float* Blo) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ksplit < 1 || (ksplit > 1 && (R || beta != 0.f))) return cudaErrorInvalidValue;
   if (bn != 0 && bn != 64 && bn != 128) return cudaErrorInvalidValue;
+  if (Blo && !split3) return cudaErrorInvalidValue;
   if (bn == 0) bn = n <= 64 ? 64 : 128;
+#define AFQMC_GEMM(BNV, S3, BL)                                                            \
+  return launch_gemm<BNV, S3, BL>(t, st, m, n, k, A, lda, B, Blo, ldb, C, ldc, alpha, beta, \
+                                  R, ldr, ksplit, split_stride, status)
   if (bn == 64) {
-    return split3 ? launch_gemm<64, true>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
-                                          R, ldr, ksplit, split_stride, status)
-                  : launch_gemm<64, false>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha,
-                                           beta, R, ldr, ksplit, split_stride, status);
+    if (!split3) AFQMC_GEMM(64, false, false);
+    if (Blo) AFQMC_GEMM(64, true, true);
+    AFQMC_GEMM(64, true, false);
   }
-  return split3 ? launch_gemm<128, true>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
-                                         R, ldr, ksplit, split_stride, status)
-                : launch_gemm<128, false>(t, st, m, n, k, A, lda, B, ldb, C, ldc, alpha, beta,
-                                          R, ldr, ksplit, split_stride, status);
+  if (!split3) AFQMC_GEMM(128, false, false);
+  if (Blo) AFQMC_GEMM(128, true, true);
+  AFQMC_GEMM(128, true, false);
+#undef AFQMC_GEMM
+}
+
+// hi (in place, x rounded to TF32) and lo = x - hi of n floats.
+__global__ void tf32_split_kernel(long n, float* __restrict__ x, float* __restrict__ lo) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float v = x[e], h = tf32_hi(v);
+  x[e] = h;
+  lo[e] = v - h;
+}
+
+cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo) {
+  if (n <= 0) return cudaSuccess;
+  tf32_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, lo);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
