@@ -372,7 +372,7 @@ afqmc_status overlap_T(afqmc_ctx* c, double2* logO_out) {
     LK(launch_md_step<T>(c->st, c->mdt, c->W, c->M, c->nu, c->nd, (const T*)c->Theta, c->ldt,
                          c->dn_off, c->logdet, logO_out, (T*)c->Gamma, c->ldg, c->gdn_off,
                          c->fp64_islands));
-  } else {
+  } else if (logO_out != c->logO_new) {   // the step's weight update sums the two spins itself
     LK(launch_logdet_sum(c->st, c->W, c->logdet, logO_out));
   }
   return AFQMC_OK;
@@ -464,7 +464,8 @@ afqmc_status step_T(afqmc_ctx* c) {
   }
   {
     KTimer t(c, 5);
-    LK(launch_weights(c->st, W, c->logO_new, c->lw, dt, c->e_shift, (double)c->p.weight_cap,
+    LK(launch_weights(c->st, W, c->md ? c->logO_new : nullptr, c->md ? nullptr : c->logdet,
+                      c->lw, dt, c->e_shift, (double)c->p.weight_cap,
                       c->wnew, c->weight, c->logO,
                       c->ctr));
   }

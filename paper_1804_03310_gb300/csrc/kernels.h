@@ -54,11 +54,13 @@ cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
                            double2* logdet, double2* Ainv, bool fp64_compute);
 
-// K7: hybrid weight and phaseless cut from the new log-overlap; ends the
-// step (ctr[0] += 1). With cap > 0 a weight is capped at cap * (*wref) when
-// *wref > 0.
+// K7: hybrid weight and phaseless cut from the new log-overlap (logO_new, or
+// with logO_new NULL the sum of the two spins' log-determinants in
+// logdet [W][2]); ends the step (ctr[0] += 1). With cap > 0 a weight is
+// capped at cap * (*wref) when *wref > 0.
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
-                           const double2* lw, double dtau, double e_shift, double cap,
+                           const double2* logdet, const double2* lw, double dtau,
+                           double e_shift, double cap,
                            const double* wref, double* weight, double2* logO,
                            long long* ctr);
 

@@ -370,30 +370,21 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint
   }
 }
 
-// D = A B with A in tensor memory (the operator) and B in shared memory;
-// `split` selects the three-product form (TF32X3).
+// D = A B with A in tensor memory (the operator) and B in shared memory.
 template <bool SPLIT3>
 __device__ __forceinline__ void issue_products_ts(uint32_t tD, uint32_t tAhi, uint32_t tAlo,
-                                                  uint32_t Bhi, uint32_t Blo, uint32_t id,
-                                                  bool split) {
+                                                  uint32_t Bhi, uint32_t Blo, uint32_t id) {
 #pragma unroll
   for (int ks = 0; ks < 16; ++ks) {
     const int kb = ks >> 2, koff = (ks & 3) * 32;
     const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
     mma_tf32_ts(tD, tAhi + 8 * ks, bd, id, ks > 0 ? 1u : 0u);
-    if (SPLIT3 && split) {
+    if (SPLIT3) {
       mma_tf32_ts(tD, tAhi + 8 * ks, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
       mma_tf32_ts(tD, tAlo + 8 * ks, bd, id, 1u);
     }
   }
 }
-
-// A term of the series takes one product instead of three once the term it
-// multiplies has shrunk below 2^-10 of the series' first term (block-wide
-// maxima): its rounding error, 2^-10 |V| |t_{n-1}| / n, is then below 2^-20
-// of |t_0| for |V| <= 1 in the max-row-sum norm, the level of the FP32
-// accumulation itself.
-constexpr float kTaylorPlainRel = 1.0f / 1024.0f;
 
 template <bool SPLIT3>
 __global__ void __launch_bounds__(128, 1)
@@ -415,7 +406,6 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   // bulk-copied into the spare shared memory while this walker's series runs
   float* vst = (float*)(base + (TY_A_BYTES + TY_B_BYTES) * 2 + 128);
   __shared__ int s_fail;
-  __shared__ float s_max[2][4];           // per-warp max |t|: [0] of t_0, [1] of the last term
   constexpr uint32_t kCols = SPLIT3 ? 512 : 256;
 
   const int tid = threadIdx.x;
@@ -461,15 +451,6 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-  };
-  // warp maximum of a non-negative value into s_max[slot][warp] (NaN wins,
-  // which keeps the three-product form)
-  auto warp_max = [&](float v, int slot) {
-    const uint32_t u = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
-    if ((tid & 31) == 0) s_max[slot][warp] = __uint_as_float(u);
-  };
-  auto block_max = [&](int slot) {
-    return fmaxf(fmaxf(s_max[slot][0], s_max[slot][1]), fmaxf(s_max[slot][2], s_max[slot][3]));
   };
   bool img_pending = false;
   if (fuse_b) {                            // the half-step image, once per CTA
@@ -531,12 +512,6 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         }
       }
     }
-    if (SPLIT3) {
-      float m = 0.f;
-#pragma unroll
-      for (int j = 0; j < 64; ++j) m = fmaxf(m, fabsf(acc[j]));
-      warp_max(m, 0);
-    }
     // ---- the operator into tensor memory: row r of [[Vr, -Vi], [Vi, Vr]],
     // columns 0..63 from plane rc of V, columns 64..127 from the other plane
     // (negated for the real rows), zero beyond M in each half
@@ -594,14 +569,11 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     for (int term = 1; term <= order; ++term) {
       sync_for_mma();
       if (tid == 0) {
-        bool split = true;
-        if (SPLIT3 && term >= 2) split = !(block_max(1) <= kTaylorPlainRel * block_max(0));
-        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id, split);
+        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id);
         mma_commit(smem_u32(bar));
       }
       wait_mma();
       const float inv = 1.0f / (float)term;
-      float m = 0.f;
 #pragma unroll
       for (int c0 = 0; c0 < 64; c0 += 32) {
         float v[32];
@@ -610,13 +582,11 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         for (int j = 0; j < 32; ++j) {
           const float x = v[j] * inv;
           acc[c0 + j] += x;
-          m = fmaxf(m, fabsf(x));
           if (term < order || fuse_b)
             put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64),
                                 term < order ? x : acc[c0 + j]);
         }
       }
-      if (SPLIT3) warp_max(m, 1);
     }
     if (fuse_b) {                          // out = s + dB s
       sync_for_mma();

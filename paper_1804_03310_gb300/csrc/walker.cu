@@ -455,6 +455,7 @@ __global__ void logdet_sum_kernel(int W, const double2* __restrict__ ld,
 
 // --------------------------------------------------------------- K7
 __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
+                               const double2* __restrict__ logdet,
                                const double2* __restrict__ lw, double dtau,
                                double e_shift, double cap, const double* __restrict__ wref,
                                double* __restrict__ weight,
@@ -462,7 +463,7 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w == 0) ctr[0] += 1;   // the step is complete once its weights are
   if (w >= W) return;
-  double2 ln = logO_new[w];
+  const double2 ln = logO_new ? logO_new[w] : cadd(logdet[2 * w], logdet[2 * w + 1]);
   double2 lnR = csub(ln, logO[w]);
   double2 l = lw[w];
   double lnI_re = lnR.x + l.x + dtau * e_shift;
@@ -919,11 +920,11 @@ cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
 }
 
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
-                           const double2* lw, double dtau, double e_shift, double cap,
-                           const double* wref, double* weight, double2* logO,
-                           long long* ctr) {
-  weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, lw, dtau, e_shift, cap,
-                                                     wref, weight, logO, ctr);
+                           const double2* logdet, const double2* lw, double dtau,
+                           double e_shift, double cap, const double* wref, double* weight,
+                           double2* logO, long long* ctr) {
+  weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, logdet, lw, dtau, e_shift,
+                                                     cap, wref, weight, logO, ctr);
   return cudaGetLastError();
 }
 
