@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64 GPU comparison run (speed and energy)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-loop measurement (p50/p99 per block)")
     return ap.parse_args()
 
 
@@ -399,6 +401,47 @@ def energy_check(precision, n_steps=600):
             "mean_mHa": round(float(np.mean(d)), 6)}
 
 
+def serving_leg(precision, n_runs=30, rate=20.0, seed=5, blocks=2, steps=50):
+    """The serving loop under a Poisson stream of independent runs (the serving
+    mix's shapes, bounded for a bench: M in 20..96, N per spin M/5..M/3,
+    n_chol 4M..6M, 128..1024 walkers, dt = 0.005, `blocks` blocks of `steps`
+    steps each). Inputs are drawn before the clock starts; submissions follow
+    the arrival times; p50/p99 are the server's own per-block latencies."""
+    import numpy as np
+    from synth.systems import serving_run
+    from paper_1804_03310_gb300 import Inputs, Server
+    rng = np.random.default_rng(seed)
+    runs = [Inputs.from_system(serving_run(rng, k, m_range=(20, 96), w_range=(128, 1024)),
+                               precision=precision) for k in range(n_runs)]
+    gaps = rng.exponential(1.0 / rate, size=n_runs)
+    srv = Server()
+    t0 = time.perf_counter()
+    t_arrive = 0.0
+    ids = []
+    for inp, gap in zip(runs, gaps):
+        now = time.perf_counter() - t0
+        if now < t_arrive:
+            time.sleep(t_arrive - now)
+        ids.append(srv.afqmc_server_submit(inp, blocks, steps))
+        t_arrive += gap
+    srv.afqmc_server_wait(-1, 900)
+    st = srv.afqmc_server_stats()
+    failures = []
+    for i in ids:
+        info = srv.afqmc_server_poll(i)
+        if info["state"] != "done":
+            failures.append(f"run {i}: {info['state']} {info['message']}")
+    srv.close()
+    return {"workload": (f"{n_runs} runs, Poisson arrivals {rate}/s, M 20..96, N/spin M/5..M/3, "
+                         f"n_chol 4M..6M, W 128..1024, {blocks} blocks of {steps} steps "
+                         f"(comb every 10), {precision}"),
+            "completed": int(st["completed"]), "failed": int(st["failed"]),
+            "p50_block_ms": round(st["p50_ms"], 3), "p99_block_ms": round(st["p99_ms"], 3),
+            "walker_steps_per_s": round(st["walker_steps"] / st["elapsed_s"], 1),
+            "elapsed_s": round(st["elapsed_s"], 3), "max_active_seen": int(st["max_active_seen"]),
+            "failures": failures[:4]}
+
+
 def dtype_of(precision):
     return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[precision]
 
@@ -442,6 +485,8 @@ def main():
         f64 = fp64_compare(args, s, hist)
         f64["speedup"] = round(value / f64["value"], 2)
         line["fp64_gpu"] = f64
+    if not args.no_serving and world == 1:
+        line["serving"] = serving_leg(args.precision)
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,

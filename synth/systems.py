@@ -285,7 +285,11 @@ def config_c4(**kw) -> System:
 
 def serving_run(rng: np.random.Generator, run_id: int,
                 m_range=(20, 200), w_range=(128, 2048)) -> System:
-    """One request of the serving mix: sizes drawn as the serving workload states."""
+    """One request of the serving mix: sizes drawn as the serving workload states.
+    Energy once per 50-step block; the comb every 10 steps, since with
+    n_chol ~ 5M fields of this scale the phaseless cut removes a few percent
+    of the walkers per step at the larger M and a 50-step comb interval can
+    lose the whole population."""
     M = int(rng.integers(m_range[0], m_range[1] + 1))
     n = int(rng.integers(math.ceil(M / 5), M // 3 + 1))
     n_chol = int(rng.integers(4 * M, 6 * M + 1))
@@ -295,7 +299,7 @@ def serving_run(rng: np.random.Generator, run_id: int,
                        ham_seed=ham_seed, l_kind="dense",
                        l_sigma=0.05 * math.sqrt(10.0 / M), trial="eig",
                        dtau=0.005, n_walkers=W, n_steps=500, seed=ham_seed,
-                       ortho_every=2, measure_every=50, pc_every=50,
+                       ortho_every=2, measure_every=50, pc_every=10,
                        run_id=run_id)
 
 
