@@ -1,7 +1,7 @@
 // Per-walker kernels of the ph-AFQMC step: field draw and force-bias shift
 // (Sec. II, Eq. 2), Taylor propagation on the CUDA cores (Sec. II, Eq. 3),
 // overlap / inverse / Theta (Sec. III), hybrid weight with the phaseless cut
-// (Sec. II), modified Gram-Schmidt (Sec. IV.A), the local-energy epilogue
+// (Sec. II), the QR orthonormalisation (Sec. IV.A), the local-energy epilogue
 // (Sec. III, Eq. 5), and the comb (Sec. V).
 #include <float.h>
 
@@ -228,11 +228,6 @@ template <typename R>
 __device__ __forceinline__ cx<R> sub_mul(cx<R> a, cx<R> f, cx<R> b) {   // a - f b
   return mk<R>(a.x - (f.x * b.x - f.y * b.y), a.y - (f.x * b.y + f.y * b.x));
 }
-template <typename R>
-__device__ __forceinline__ cx<R> div_c(cx<R> a, cx<R> b) {
-  R d = b.x * b.x + b.y * b.y;
-  return mk<R>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
 
 template <typename R>
 __device__ __forceinline__ cx<R> mul_c(cx<R> a, cx<R> b) {
@@ -244,16 +239,98 @@ __device__ __forceinline__ cx<R> mul_c(cx<R> a, cx<R> b) {
 // distinct banks.
 __host__ __device__ __forceinline__ int staged_ld(int M) { return M | 1; }
 
+// Stage the ns orbital columns of one walker's spin block (2M values each:
+// the real plane, then the imaginary plane) as complex Q[b][k]. Thread r
+// takes plane row r of every column, with kStageU independent loads in
+// flight before their stores, so that a block pays a few memory latencies
+// instead of one per column.
+constexpr int kStageU = 8;
+template <typename T, typename R>
+__device__ __forceinline__ void stage_columns(const T* __restrict__ Pw, int M, int ns, int ldq,
+                                              cx<R>* __restrict__ Q) {
+  for (int r = threadIdx.x; r < 2 * M; r += blockDim.x) {
+    const int k = r < M ? r : r - M;
+    const int part = r < M ? 0 : 1;
+    for (int b0 = 0; b0 < ns; b0 += kStageU) {
+      T v[kStageU];
+#pragma unroll
+      for (int u = 0; u < kStageU; ++u)
+        v[u] = (b0 + u < ns) ? Pw[(long)(b0 + u) * 2 * M + r] : T(0);
+#pragma unroll
+      for (int u = 0; u < kStageU; ++u)
+        if (b0 + u < ns) reinterpret_cast<R*>(&Q[(b0 + u) * ldq + k])[part] = (R)v[u];
+    }
+  }
+}
+
+// Y = Phi X for one staged walker block: Phi is M x ns with column b at
+// Q[b * ldq], X is ns x ns row-major with row stride ldx; store(r, c, y) gets
+// every Y_rc. Each thread accumulates a TR x 4 tile whose rows are nr apart
+// and whose columns are nc apart, so that the lanes of a warp read
+// consecutive rows of Phi (conflict-free) and a few broadcast entries of X.
+template <int TR, typename R, typename F>
+__device__ __forceinline__ void block_phi_times(int M, int ns, const cx<R>* __restrict__ Q,
+                                                int ldq, const cx<R>* __restrict__ X, int ldx,
+                                                F store) {
+  const int nr = (M + TR - 1) / TR, nc = (ns + 3) >> 2;
+  for (int it = threadIdx.x; it < nr * nc; it += blockDim.x) {
+    const int rt = it % nr, ct = it / nr;
+    int rr[TR], cc[4];
+#pragma unroll
+    for (int u = 0; u < TR; ++u) rr[u] = min(rt + u * nr, M - 1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) cc[v] = min(ct + v * nc, ns - 1);
+    R yr[TR][4], yi[TR][4];
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { yr[u][v] = R(0); yi[u][v] = R(0); }
+    for (int i = 0; i < ns; ++i) {
+      cx<R> q[TR], x[4];
+#pragma unroll
+      for (int u = 0; u < TR; ++u) q[u] = Q[i * ldq + rr[u]];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) x[v] = X[i * ldx + cc[v]];
+#pragma unroll
+      for (int u = 0; u < TR; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          yr[u][v] = fma(q[u].x, x[v].x, fma(-q[u].y, x[v].y, yr[u][v]));
+          yi[u][v] = fma(q[u].x, x[v].y, fma(q[u].y, x[v].x, yi[u][v]));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (rt + u * nr < M && ct + v * nc < ns)
+          store(rt + u * nr, ct + v * nc, mk<R>(yr[u][v], yi[u][v]));
+  }
+}
+
+// Shared-memory bytes of one overlap block: the staged walker columns, two
+// ns x ns elimination buffers (the second shares its space with the staged
+// trial rows), the pivots and the row permutation.
+__host__ __device__ __forceinline__ size_t overlap_region(int M, int ns) {
+  const size_t a = (size_t)ns * (ns | 1), d = ((size_t)ns * staged_ld(M) + 1) / 2;
+  return a > d ? a : d;
+}
+
 // One block per (walker, spin), with the walker's columns of that spin
 // staged in shared memory as Q[b][k] (orbital column b, basis row k).
 //  1. A = D^T Phi (real trial orbitals), ns x ns.
-//  2. LU with partial pivoting, P A = L U, in the compute type R; the
+//  2. Gauss-Jordan elimination with partial pivoting gives (P A)^-1 and the
+//     pivots, which are the diagonal of the U in P A = L U; the
 //     log-determinant sum_k ln U_kk (+ i pi per odd row-swap count) is
-//     accumulated in FP64.
-//  3. Theta = Phi A^-1 = Phi U^-1 L^-1 P row by row: thread k solves
-//     z U = phi_k, then y L = z, and scatters theta_k[perm[i]] = y_i.
-template <typename T, typename R>
-__global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
+//     accumulated in FP64. Step k reads one buffer and writes the other, so
+//     it needs a single block barrier; the warp that owns column k + 1 picks
+//     the next pivot from the values it has just written.
+//  3. Theta = Phi A^-1 = (Phi (P A)^-1) P: a block product scattered to the
+//     permuted columns. A^-1 itself (for the multi-determinant ratios) is
+//     (P A)^-1 with the same column permutation.
+template <typename T, typename R, int NT>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (NT == 128 ? 7 : 3) : 1)
+overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
                                const T* __restrict__ PsiT, T* __restrict__ Theta,
                                long ldt, long dn_off, double2* __restrict__ logdet,
                                double2* __restrict__ Ainv_out, int nmax) {
@@ -267,22 +344,27 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
     if (tid == 0) logdet[2 * w + sig] = make_double2(0.0, 0.0);
     return;
   }
-  const int ldq = staged_ld(M);
+  const int ldq = staged_ld(M), lda = ns | 1;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);      // [ns][ldq]
-  cx<R>* A = Q + (long)ns * ldq;                      // [ns][ns], L and U in place
-  R* D = reinterpret_cast<R*>(A + (long)ns * ns);     // [ns][ldq] trial rows
-  int* perm = reinterpret_cast<int*>(D + (long)ns * ldq);
-  __shared__ int piv, singular, nswap;
+  cx<R>* A0 = Q + (long)ns * ldq;                     // [ns][lda]
+  cx<R>* A1 = A0 + (long)ns * lda;                    // [ns][lda]
+  R* D = reinterpret_cast<R*>(A1);                    // [ns][ldq] trial rows, until step 0
+  cx<R>* pvs = A1 + overlap_region(M, ns);            // [ns] pivots
+  int* perm = reinterpret_cast<int*>(pvs + ns);       // [ns]
+  __shared__ int piv[2], singular, nswap;
   const T* Pw = Phi + ((long)w * N + j0) * 2 * M;
-  for (int b = 0; b < ns; ++b) {                      // column b, both planes
-    const T* col = Pw + (long)b * 2 * M;
-    for (int r = tid; r < 2 * M; r += nt) {
-      const R v = (R)col[r];
-      if (r < M) Q[b * ldq + r].x = v;
-      else Q[b * ldq + r - M].y = v;
+  stage_columns<T, R>(Pw, M, ns, ldq, Q);
+  for (int k = tid; k < M; k += nt) {                 // trial rows, kStageU loads in flight
+    for (int b0 = 0; b0 < ns; b0 += kStageU) {
+      T v[kStageU];
+#pragma unroll
+      for (int u = 0; u < kStageU; ++u)
+        v[u] = (b0 + u < ns) ? PsiT[(long)(j0 + b0 + u) * M + k] : T(0);
+#pragma unroll
+      for (int u = 0; u < kStageU; ++u)
+        if (b0 + u < ns) D[(b0 + u) * ldq + k] = (R)v[u];
     }
-    for (int k = tid; k < M; k += nt) D[b * ldq + k] = (R)PsiT[(long)(j0 + b) * M + k];
   }
   if (tid == 0) { nswap = 0; singular = 0; }
   for (int i = tid; i < ns; i += nt) perm[i] = i;
@@ -316,64 +398,98 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
       for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v)
-          if (a0 + u < ns && b0 + v < ns) A[(a0 + u) * ns + b0 + v] = mk<R>(sr[u][v], si[u][v]);
+          if (a0 + u < ns && b0 + v < ns) A0[(a0 + u) * lda + b0 + v] = mk<R>(sr[u][v], si[u][v]);
     }
   }
   __syncthreads();
-  for (int k = 0; k < ns; ++k) {
-    if (tid < 32) {
-      R best = R(-1);
-      int bi = k;
-      for (int i = k + tid; i < ns; i += 32) {
-        const cx<R> v = A[i * ns + k];
-        const R m = v.x * v.x + v.y * v.y;
-        if (m > best) { best = m; bi = i; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) {
-        piv = bi;
-        if (!(best > R(0))) singular = 1;
-      }
+  if (warp == 0) {                                    // first pivot: column 0
+    R best = R(-1);
+    int bi = 0;
+    for (int i = lane; i < ns; i += 32) {
+      const cx<R> v = A0[i * lda];
+      const R m = v.x * v.x + v.y * v.y;
+      if (m > best) { best = m; bi = i; }
     }
-    __syncthreads();
-    if (singular) break;
-    const int p = piv;
-    if (p != k) {
-      for (int c = tid; c < ns; c += nt) {
-        const cx<R> t = A[k * ns + c];
-        A[k * ns + c] = A[p * ns + c];
-        A[p * ns + c] = t;
-      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+      piv[0] = bi;
+      if (!(best > R(0))) singular = 1;
+    }
+  }
+  __syncthreads();
+  cx<R>* cur = A0;
+  cx<R>* nxt = A1;
+  if (!singular) {
+    for (int k = 0; k < ns; ++k) {
+      const int p = piv[k & 1];
+      const cx<R>* prow = cur + p * lda;
+      const cx<R> pv = prow[k];
+      const R pd = pv.x * pv.x + pv.y * pv.y;
+      const cx<R> ipv = mk<R>(pv.x / pd, -pv.y / pd);
       if (tid == 0) {
-        const int t = perm[k];
-        perm[k] = perm[p];
-        perm[p] = t;
-        nswap ^= 1;
+        pvs[k] = pv;
+        if (p != k) {
+          const int t = perm[k];
+          perm[k] = perm[p];
+          perm[p] = t;
+          nswap ^= 1;
+        }
+      }
+      // rows k and p trade places: row i of the result comes from row src(i)
+      // (the new pivot row k is row p scaled: p - (1 - 1/pv) p, one formula for all rows)
+      for (int i = lane; i < ns; i += 32) {
+        const cx<R>* irow = cur + (i == k ? p : (i == p ? k : i)) * lda;
+        cx<R> f, colk;
+        if (i == k) {
+          f = mk<R>(R(1) - ipv.x, -ipv.y);
+          colk = ipv;
+        } else {
+          f = mul_c(irow[k], ipv);
+          colk = mk<R>(-f.x, -f.y);
+        }
+        cx<R>* orow = nxt + i * lda;
+        for (int j = warp; j < ns; j += nwarps)
+          orow[j] = (j == k) ? colk : sub_mul(irow[j], f, prow[j]);
+      }
+      const int jn = k + 1;
+      if (jn < ns && jn % nwarps == warp) {           // next pivot, from this warp's own writes
+        R best = R(-1);
+        int bi = jn;
+        for (int i = lane; i < ns; i += 32) {
+          if (i < jn) continue;
+          const cx<R> v = nxt[i * lda + jn];
+          const R m = v.x * v.x + v.y * v.y;
+          if (m > best) { best = m; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          piv[jn & 1] = bi;
+          if (!(best > R(0))) singular = 1;
+        }
       }
       __syncthreads();
+      cx<R>* t = cur;
+      cur = nxt;
+      nxt = t;
+      if (singular) break;
     }
-    const cx<R> pv = A[k * ns + k];
-    for (int i = k + 1 + tid; i < ns; i += nt) A[i * ns + k] = div_c(A[i * ns + k], pv);
-    __syncthreads();
-    // trailing update: lane = column, warp = every nwarps-th row
-    for (int j = k + 1 + lane; j < ns; j += 32) {
-      const cx<R> ukj = A[k * ns + j];
-      for (int i = k + 1 + warp; i < ns; i += nwarps)
-        A[i * ns + j] = sub_mul(A[i * ns + j], A[i * ns + k], ukj);
-    }
-    __syncthreads();
   }
   const int sing = singular;
   if (tid < 32) {
     double lre = 0.0, lim = 0.0;
     if (!sing) {
       for (int k = tid; k < ns; k += 32) {
-        const double px = (double)A[k * ns + k].x, py = (double)A[k * ns + k].y;
+        const double px = (double)pvs[k].x, py = (double)pvs[k].y;
         lre += 0.5 * log(px * px + py * py);
         lim += atan2(py, px);
       }
@@ -389,59 +505,24 @@ __global__ void overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ 
   }
   T* Tr = Theta + ((long)w * 2 + 0) * ldt + (sig ? dn_off : 0);
   T* Ti = Theta + ((long)w * 2 + 1) * ldt + (sig ? dn_off : 0);
-  for (int k = tid; k < M; k += nt) {
-    if (sing) {
-      for (int a = 0; a < ns; ++a) {
-        Tr[(long)a * M + k] = T(0);
-        Ti[(long)a * M + k] = T(0);
-      }
-      continue;
+  if (sing) {
+    for (int e = tid; e < ns * M; e += nt) {
+      Tr[e] = T(0);
+      Ti[e] = T(0);
     }
-    for (int j = 0; j < ns; ++j) {              // z U = phi_k (two partial sums)
-      cx<R> s0 = Q[j * ldq + k], s1 = mk<R>(R(0), R(0));
-      int i = 0;
-      for (; i + 1 < j; i += 2) {
-        s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
-        s1 = sub_mul(s1, Q[(i + 1) * ldq + k], A[(i + 1) * ns + j]);
-      }
-      if (i < j) s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
-      Q[j * ldq + k] = div_c(mk<R>(s0.x + s1.x, s0.y + s1.y), A[j * ns + j]);
-    }
-    for (int j = ns - 2; j >= 0; --j) {         // y L = z (unit lower L)
-      cx<R> s0 = Q[j * ldq + k], s1 = mk<R>(R(0), R(0));
-      int i = j + 1;
-      for (; i + 1 < ns; i += 2) {
-        s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
-        s1 = sub_mul(s1, Q[(i + 1) * ldq + k], A[(i + 1) * ns + j]);
-      }
-      if (i < ns) s0 = sub_mul(s0, Q[i * ldq + k], A[i * ns + j]);
-      Q[j * ldq + k] = mk<R>(s0.x + s1.x, s0.y + s1.y);
-    }
-    for (int i = 0; i < ns; ++i) {              // theta_k[perm[i]] = y_i
-      const cx<R> y = Q[i * ldq + k];
-      Tr[(long)perm[i] * M + k] = (T)y.x;
-      Ti[(long)perm[i] * M + k] = (T)y.y;
-    }
+  } else {
+    block_phi_times<2>(M, ns, Q, ldq, cur, lda, [&](int r, int c, cx<R> y) {
+      const long o = (long)perm[c] * M + r;
+      Tr[o] = (T)y.x;
+      Ti[o] = (T)y.y;
+    });
   }
-  if (Ainv_out) {                               // rows of A^-1 = e_r U^-1 L^-1 P
-    __syncthreads();
+  if (Ainv_out) {                                     // A^-1 [r][perm[i]] = (P A)^-1 [r][i]
     double2* Ao = Ainv_out + ((long)w * 2 + sig) * nmax * nmax;
-    cx<R>* rowbuf = Q;                          // reuse: [ns][ldq] as [i][r]
-    for (int r = tid; r < ns; r += nt) {
-      for (int j = 0; j < ns; ++j) {
-        cx<R> s = mk<R>(j == r ? R(1) : R(0), R(0));
-        for (int i = 0; i < j; ++i) s = sub_mul(s, rowbuf[i * ldq + r], A[i * ns + j]);
-        rowbuf[j * ldq + r] = sing ? mk<R>(R(0), R(0)) : div_c(s, A[j * ns + j]);
-      }
-      for (int j = ns - 2; j >= 0; --j) {
-        cx<R> s = rowbuf[j * ldq + r];
-        for (int i = j + 1; i < ns; ++i) s = sub_mul(s, rowbuf[i * ldq + r], A[i * ns + j]);
-        rowbuf[j * ldq + r] = s;
-      }
-      for (int i = 0; i < ns; ++i) {
-        const cx<R> y = rowbuf[i * ldq + r];
-        Ao[(long)r * nmax + perm[i]] = make_double2((double)y.x, (double)y.y);
-      }
+    for (int e = tid; e < ns * ns; e += nt) {
+      const int r = e / ns, i = e - r * ns;
+      const cx<R> y = sing ? mk<R>(R(0), R(0)) : cur[r * lda + i];
+      Ao[(long)r * nmax + perm[i]] = make_double2((double)y.x, (double)y.y);
     }
   }
 }
@@ -507,14 +588,7 @@ __global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
   cx<R>* Q = reinterpret_cast<cx<R>*>(smem_raw);      // [ns][ldq]
   cx<R>* S = Q + (long)ns * ldq;                      // [ns][ns], R in the upper part
   T* Pw = Phi + ((long)w * N + j0) * 2 * M;
-  for (int b = 0; b < ns; ++b) {                      // column b, both planes
-    const T* col = Pw + (long)b * 2 * M;
-    for (int r = tid; r < 2 * M; r += nt) {
-      const R v = (R)col[r];
-      if (r < M) Q[b * ldq + r].x = v;
-      else Q[b * ldq + r - M].y = v;
-    }
-  }
+  stage_columns<T, R>(Pw, M, ns, ldq, Q);
   __syncthreads();
   {                                                   // S_ab = q_a^H q_b, a <= b, 2 x 4 tiles
     const int na = (ns + 1) >> 1, nb = (ns + 3) >> 2;
@@ -892,31 +966,43 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
 }
 
 size_t overlap_smem(int M, int nmax, size_t csize) {
-  return csize * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax) +
-         csize / 2 * (size_t)nmax * staged_ld(M) + sizeof(int) * nmax;
+  return csize * ((size_t)nmax * staged_ld(M) + (size_t)nmax * (nmax | 1) +
+                  overlap_region(M, nmax) + nmax) +
+         sizeof(int) * nmax;
+}
+
+size_t qr_smem(int M, int nmax, size_t csize) {
+  return csize * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
+}
+
+template <typename T, typename R, int NT>
+cudaError_t launch_overlap_nt(cudaStream_t st, int W, int M, int n_up, int n_dn,
+                              const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
+                              double2* logdet, double2* Ainv) {
+  const int nmax = n_up > n_dn ? n_up : n_dn;
+  static const size_t cap = allow_big_smem(overlap_kernel<T, R, NT>);
+  const size_t smem = overlap_smem(M, nmax, sizeof(cx<R>));
+  if (smem > cap) return cudaErrorInvalidValue;
+  overlap_kernel<T, R, NT><<<dim3(W, 2), NT, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta, ldt,
+                                                       dn_off, logdet, Ainv, nmax);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
                            double2* logdet, double2* Ainv, bool fp64_compute) {
-  const int nmax = n_up > n_dn ? n_up : n_dn;
-  const int threads = M > 96 ? 256 : 128;
-  dim3 grid(W, 2);
-  static const size_t cap64 = allow_big_smem(overlap_kernel<T, double>);
-  const size_t smem64 = overlap_smem(M, nmax, sizeof(double2));
-  if (fp64_compute) {
-    if (smem64 > cap64) return cudaErrorInvalidValue;
-    overlap_kernel<T, double><<<grid, threads, smem64, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                            ldt, dn_off, logdet, Ainv, nmax);
-  } else {
-    static const size_t cap = allow_big_smem(overlap_kernel<T, float>);
-    const size_t smem = overlap_smem(M, nmax, sizeof(float2));
-    if (smem > cap) return cudaErrorInvalidValue;
-    overlap_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta,
-                                                         ldt, dn_off, logdet, Ainv, nmax);
-  }
-  return cudaGetLastError();
+  if (M > 96)
+    return fp64_compute
+               ? launch_overlap_nt<T, double, 256>(st, W, M, n_up, n_dn, Phi, PsiT, Theta, ldt,
+                                                   dn_off, logdet, Ainv)
+               : launch_overlap_nt<T, float, 256>(st, W, M, n_up, n_dn, Phi, PsiT, Theta, ldt,
+                                                  dn_off, logdet, Ainv);
+  return fp64_compute
+             ? launch_overlap_nt<T, double, 128>(st, W, M, n_up, n_dn, Phi, PsiT, Theta, ldt,
+                                                 dn_off, logdet, Ainv)
+             : launch_overlap_nt<T, float, 128>(st, W, M, n_up, n_dn, Phi, PsiT, Theta, ldt,
+                                                dn_off, logdet, Ainv);
 }
 
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
@@ -942,12 +1028,12 @@ cudaError_t launch_qr(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
   dim3 grid(W, 2);
   if (fp64_compute) {
     static const size_t cap = allow_big_smem(qr_kernel<T, double>);
-    const size_t smem = sizeof(double2) * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
+    const size_t smem = qr_smem(M, nmax, sizeof(double2));
     if (smem > cap) return cudaErrorInvalidValue;
     qr_kernel<T, double><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   } else {
     static const size_t cap = allow_big_smem(qr_kernel<T, float>);
-    const size_t smem = sizeof(float2) * ((size_t)nmax * staged_ld(M) + (size_t)nmax * nmax);
+    const size_t smem = qr_smem(M, nmax, sizeof(float2));
     if (smem > cap) return cudaErrorInvalidValue;
     qr_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   }
