@@ -353,6 +353,21 @@ overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
   cx<R>* pvs = A1 + overlap_region(M, ns);            // [ns] pivots
   int* perm = reinterpret_cast<int*>(pvs + ns);       // [ns]
   __shared__ int piv[2], singular, nswap;
+  __shared__ cx<R> ipv_s[2];                          // 1 / pivot of the next step
+  // lane 0 of the warp that found pivot row bi of column col publishes it
+  auto publish = [&](const cx<R>* buf, int col, int bi, R best) {
+    if (lane == 0) {
+      piv[col & 1] = bi;
+      if (!(best > R(0))) {
+        singular = 1;
+      } else {
+        const cx<R> pv = buf[bi * lda + col];
+        const R pd = pv.x * pv.x + pv.y * pv.y;
+        pvs[col] = pv;
+        ipv_s[col & 1] = mk<R>(pv.x / pd, -pv.y / pd);
+      }
+    }
+  };
   const T* Pw = Phi + ((long)w * N + j0) * 2 * M;
   stage_columns<T, R>(Pw, M, ns, ldq, Q);
   for (int k = tid; k < M; k += nt) {                 // trial rows, kStageU loads in flight
@@ -416,10 +431,7 @@ overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (lane == 0) {
-      piv[0] = bi;
-      if (!(best > R(0))) singular = 1;
-    }
+    publish(A0, 0, bi, best);
   }
   __syncthreads();
   cx<R>* cur = A0;
@@ -428,11 +440,8 @@ overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
     for (int k = 0; k < ns; ++k) {
       const int p = piv[k & 1];
       const cx<R>* prow = cur + p * lda;
-      const cx<R> pv = prow[k];
-      const R pd = pv.x * pv.x + pv.y * pv.y;
-      const cx<R> ipv = mk<R>(pv.x / pd, -pv.y / pd);
+      const cx<R> ipv = ipv_s[k & 1];
       if (tid == 0) {
-        pvs[k] = pv;
         if (p != k) {
           const int t = perm[k];
           perm[k] = perm[p];
@@ -472,10 +481,8 @@ overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (lane == 0) {
-          piv[jn & 1] = bi;
-          if (!(best > R(0))) singular = 1;
-        }
+        __syncwarp();                                  // the lanes' writes of column jn
+        publish(nxt, jn, bi, best);
       }
       __syncthreads();
       cx<R>* t = cur;
