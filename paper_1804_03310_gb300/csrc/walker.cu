@@ -74,6 +74,19 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
   C lre = 0, lim = 0;
   const int nq = (n_chol + 3) >> 2;
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    // X summed over the K-split partials, in order; the loads are issued
+    // before the draw so that their latency overlaps the Philox rounds
+    C xr[4] = {0, 0, 0, 0}, xi[4] = {0, 0, 0, 0};
+    for (int sp = 0; sp < nsplit; ++sp) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int g = 4 * q + j;
+        if (g < n_chol) {
+          xr[j] += (C)Xr[sp * split_stride + g];
+          xi[j] += (C)Xi[sp * split_stride + g];
+        }
+      }
+    }
     U4 c = {(uint32_t)q, (uint32_t)w, step, (uint32_t)(4 * run_id + kStreamFields)};
     U4 r = philox4x32_10(c, k0, k1);
     C z[4];
@@ -92,14 +105,9 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
     for (int j = 0; j < 4; ++j) {
       const int g = 4 * q + j;
       if (g >= n_chol) break;
-      C xr = 0, xi = 0;   // X summed over the K-split partials, in order
-      for (int sp = 0; sp < nsplit; ++sp) {
-        xr += (C)Xr[sp * split_stride + g];
-        xi += (C)Xi[sp * split_stride + g];
-      }
       // xbar = -i sqrt(dt) X
-      C br = sqdt * xi;
-      C bi = -sqdt * xr;
+      C br = sqdt * xi[j];
+      C bi = -sqdt * xr[j];
       if (!isfinite(br) || !isfinite(bi)) { br = 0; bi = 0; }
       if (cap > 0) {
         const C a = sqrt(br * br + bi * bi);
