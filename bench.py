@@ -52,6 +52,8 @@ def parse():
                     help="skip the FP64 GPU comparison run (speed and energy)")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-loop measurement (p50/p99 per block)")
+    ap.add_argument("--no-shapes", action="store_true",
+                    help="skip the other workload shapes (TM-atom, multi-determinant)")
     return ap.parse_args()
 
 
@@ -442,6 +444,50 @@ def serving_leg(precision, n_runs=30, rate=20.0, seed=5, blocks=2, steps=50):
             "failures": failures[:4]}
 
 
+def _blocks(s, precision, n_blocks):
+    """Mean device ms per 20-step block after one warm-up block, and the
+    per-kernel-group totals over the timed blocks."""
+    import torch
+    from paper_1804_03310_gb300 import Afqmc, KERNEL_IDS
+    stream = torch.cuda.Stream()
+    ctx = Afqmc.from_system(s, precision=precision, stream=stream.cuda_stream)
+    ctx.afqmc_propagate(BLOCK)
+    stream.synchronize()
+    ctx.afqmc_set_kernel_timing(True)
+    total = 0.0
+    for _ in range(n_blocks):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.afqmc_propagate(BLOCK)
+        e.record(stream)
+        e.synchronize()
+        total += a.elapsed_time(e)
+    ks = {k: ctx.afqmc_kernel_stats(k) for k in KERNEL_IDS}
+    ctx.close()
+    return total / n_blocks, {k: round(v["total_ms"], 3) for k, v in ks.items() if v["launches"]}
+
+
+def shapes_leg(precision):
+    """The other workload shapes of the scope, each in the measured mode and
+    in FP64 on the GPU (same walkers and seed): the TM-atom shape (M = 150,
+    where the Taylor series runs on the CUDA cores) and the
+    multi-determinant shape (200 determinants, batched SMW ratios)."""
+    from synth import CONFIGS
+    out = {}
+    for name in ("c3", "c4"):
+        s = CONFIGS[name]().replace(measure_every=BLOCK, pc_every=BLOCK, ortho_every=2)
+        ms, kms = _blocks(s, precision, 2)
+        ms64, _ = _blocks(s, "fp64", 1)
+        v = s.n_walkers * BLOCK / (ms / 1e3)
+        v64 = s.n_walkers * BLOCK / (ms64 / 1e3)
+        out[name] = {"workload": describe(s), "precision": precision,
+                     "value": round(v, 1), "unit": METRIC, "ms_per_block": round(ms, 3),
+                     "fp64_value": round(v64, 1), "speedup": round(v / v64, 2),
+                     "kernels_ms_2_blocks": kms}
+    return out
+
+
 def dtype_of(precision):
     return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[precision]
 
@@ -487,6 +533,8 @@ def main():
         line["fp64_gpu"] = f64
     if not args.no_serving and world == 1:
         line["serving"] = serving_leg(args.precision)
+    if not args.no_shapes and world == 1 and args.precision != "fp64":
+        line["shapes"] = shapes_leg(args.precision)
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,
