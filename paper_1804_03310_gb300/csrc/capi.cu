@@ -1266,6 +1266,9 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     c->mdt.ndet = c->ndet;
     c->mdt.nact[0] = c->nact[0];
     c->mdt.nact[1] = c->nact[1];
+    c->mdt.emax[0] = c->mdt.emax[1] = 0;
+    for (const MdDet& d : dets_h)
+      for (int sg = 0; sg < 2; ++sg) c->mdt.emax[sg] = std::max(c->mdt.emax[sg], d.E[sg]);
     c->mdt.dets = (const MdDet*)c->md_dets;
     c->mdt.cconj = (const double2*)c->md_cc;
     c->mdt.ract[0] = (const int*)c->md_r0;

@@ -442,6 +442,221 @@ __global__ void md_energy_kernel(MdTables tb, int M, int nu, int nd, int G,
   if (tid == 0) eloc[w] = make_double2(sr, si);
 }
 
+// One spin's contribution to E_i for one Cholesky vector, with E = the
+// determinant's excitation count as a compile-time constant (the arrays stay
+// in registers) and C = K_i^-1 (Omega[p] - E_h^T) precomputed ([E][ns]).
+// Same quantities as md_energy_kernel: tr M, and (when !last) tr M^2 =
+// tr B0^2 - 2 tr(C B0 B1) + tr((C B1)^2). The differences
+// D[m][l] = P[p_m][h_l] - P[r_{h_m}][h_l] do not depend on the position a.
+template <int E, typename R>
+__device__ __forceinline__ void md_spin_terms(const int* __restrict__ h,
+                                              const int* __restrict__ p,
+                                              const cplx<R>* __restrict__ C,
+                                              const cplx<R>* __restrict__ P,
+                                              const cplx<R>* __restrict__ Vm,
+                                              const int* __restrict__ ract, int ns, bool last,
+                                              cplx<R>& trM, cplx<R>& sq) {
+  constexpr int E1 = E > 0 ? E : 1;
+  int hh[E1], pp[E1], rh[E1];
+#pragma unroll
+  for (int m = 0; m < E; ++m) { hh[m] = h[m]; pp[m] = p[m]; rh[m] = ract[h[m]]; }
+  cplx<R> D[E1][E1];
+#pragma unroll
+  for (int m = 0; m < E; ++m)
+#pragma unroll
+    for (int l = 0; l < E; ++l) D[m][l] = csub(P[pp[m] * ns + hh[l]], P[rh[m] * ns + hh[l]]);
+  cplx<R> tm = cm<R>(R(0), R(0)), b0 = cm<R>(R(0), R(0)), t2 = cm<R>(R(0), R(0));
+  cplx<R> CB1[E1][E1];
+#pragma unroll
+  for (int l = 0; l < E; ++l)
+#pragma unroll
+    for (int m = 0; m < E; ++m) CB1[l][m] = cm<R>(R(0), R(0));
+  for (int a = 0; a < ns; ++a) {
+    int ra = ract[a];                               // rho(a)
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+      if (a == hh[m]) ra = pp[m];
+    const cplx<R>* Pra = P + ra * ns;
+    cplx<R> ph[E1], Ca[E1];
+#pragma unroll
+    for (int m = 0; m < E; ++m) { ph[m] = Pra[hh[m]]; Ca[m] = C[m * ns + a]; }
+    cplx<R> v = Pra[a];
+#pragma unroll
+    for (int l = 0; l < E; ++l) v = csub(v, cmul(ph[l], Ca[l]));
+    tm = cadd(tm, v);
+    if (last) continue;
+    cplx<R> b2 = Vm[ra * ns + a];
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+      b2 = cadd(b2, cmul(ph[m], csub(P[pp[m] * ns + a], P[rh[m] * ns + a])));
+    b0 = cadd(b0, b2);
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      cplx<R> bb = Vm[ra * ns + hh[l]];
+#pragma unroll
+      for (int m = 0; m < E; ++m) bb = cadd(bb, cmul(ph[m], D[m][l]));
+      t2 = cadd(t2, cmul(Ca[l], bb));
+#pragma unroll
+      for (int m = 0; m < E; ++m) CB1[l][m] = cadd(CB1[l][m], cmul(Ca[l], ph[m]));
+    }
+  }
+  trM = tm;
+  if (!last) {
+    cplx<R> s = csub(b0, cm<R>(R(2) * t2.x, R(2) * t2.y));
+#pragma unroll
+    for (int l = 0; l < E; ++l)
+#pragma unroll
+      for (int m = 0; m < E; ++m) s = cadd(s, cmul(CB1[l][m], CB1[m][l]));
+    sq = s;
+  } else {
+    sq = cm<R>(R(0), R(0));
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void md_spin_dispatch(int E, const int* h, const int* p,
+                                                 const cplx<R>* C, const cplx<R>* P,
+                                                 const cplx<R>* Vm, const int* ract, int ns,
+                                                 bool last, cplx<R>& trM, cplx<R>& sq) {
+  switch (E) {
+    case 0: md_spin_terms<0, R>(h, p, C, P, Vm, ract, ns, last, trM, sq); break;
+    case 1: md_spin_terms<1, R>(h, p, C, P, Vm, ract, ns, last, trM, sq); break;
+    case 2: md_spin_terms<2, R>(h, p, C, P, Vm, ract, ns, last, trM, sq); break;
+    case 3: md_spin_terms<3, R>(h, p, C, P, Vm, ract, ns, last, trM, sq); break;
+    default: md_spin_terms<4, R>(h, p, C, P, Vm, ract, ns, last, trM, sq); break;
+  }
+}
+
+// Shared bytes the hoisted energy kernel adds: the C_i table
+// ([ndet][emax_up nu + emax_dn nd]) and one FP64 complex accumulator per
+// determinant.
+__host__ __device__ __forceinline__ size_t md_ctab_bytes(int nu, int nd, int e_u, int e_d,
+                                                         int ndet, size_t csize) {
+  const size_t c = csize * (size_t)ndet * ((size_t)e_u * nu + (size_t)e_d * nd);
+  return ((c + 15) & ~(size_t)15) + 16 * (size_t)ndet;
+}
+
+// The local energy of md_energy_kernel with the Cholesky-independent parts
+// taken out of the loop over g: C_i = K_i^-1 (Omega[p] - E_h^T) per
+// determinant and spin is formed once per walker into shared memory, and the
+// per-g work runs with the excitation count as a compile-time constant.
+template <typename T, typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted_kernel(MdTables tb, int M, int nu, int nd, int G,
+                                         const T* __restrict__ Theta, long ldt, long dn_off,
+                                         const double2* __restrict__ logdet0,
+                                         const T* __restrict__ LtilA, long ldg, long gdn_off,
+                                         double2* __restrict__ eloc) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double red[32];
+  MdSmem<R> sm;
+  sm.carve(smem_raw, M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet);
+  const int w = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red);
+  cplx<R>* P0 = reinterpret_cast<cplx<R>*>(smem_raw + MdSmem<R>::bytes(M, nu, nd, tb.nact[0],
+                                                                       tb.nact[1], tb.ndet));
+  cplx<R>* Ps[2] = {P0, P0 + (long)tb.nact[0] * nu};
+  cplx<R>* V0 = P0 + (long)tb.nact[0] * nu + (long)tb.nact[1] * nd;
+  cplx<R>* Vs[2] = {V0, V0 + (long)tb.nact[0] * nu};
+  cplx<R>* Ctab = V0 + (long)tb.nact[0] * nu + (long)tb.nact[1] * nd;
+  const long cst = (long)tb.emax[0] * nu + (long)tb.emax[1] * nd;
+  const long coff[2] = {0, (long)tb.emax[0] * nu};
+  const size_t cbytes = sizeof(cplx<R>) * (size_t)tb.ndet * cst;
+  double2* eacc = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(Ctab) +
+                                             ((cbytes + 15) & ~(size_t)15));
+  const int nsv[2] = {nu, nd};
+  const int ldq = stage_ld(M);
+  for (int i = tid; i < tb.ndet; i += nt) {        // C_i, once per walker
+    const MdDet* dp = tb.dets + i;
+    eacc[i] = make_double2(0.0, 0.0);
+    for (int sg = 0; sg < 2; ++sg) {
+      const int ns = nsv[sg], E = dp->E[sg];
+      if (ns == 0 || E == 0) continue;
+      cplx<R> inv[EMAX][EMAX];
+      det_k<R>(E, dp->p[sg], dp->h[sg], sm.Om[sg], ns, inv);
+      cplx<R>* C = Ctab + (long)i * cst + coff[sg];
+      for (int l = 0; l < E; ++l)
+        for (int a = 0; a < ns; ++a) {
+          cplx<R> s = cm<R>(R(0), R(0));
+          for (int m = 0; m < E; ++m) {
+            cplx<R> r = sm.Om[sg][dp->p[sg][m] * ns + a];
+            if (a == dp->h[sg][m]) r.x -= R(1);
+            s = cadd(s, cmul(inv[l][m], r));
+          }
+          C[l * ns + a] = s;
+        }
+    }
+  }
+  for (int g = 0; g <= G; ++g) {
+    __syncthreads();
+    for (int sg = 0; sg < 2; ++sg) {               // P = L^act_g Theta_0
+      const int ns = nsv[sg], na = tb.nact[sg];
+      const T* Lg = LtilA + (long)g * ldg + (sg ? gdn_off : 0);
+      for (int e = tid; e < na * ns; e += nt) {
+        const int q = e / ns, a = e - q * ns;
+        const T* lq = Lg + (long)q * M;
+        const cplx<R>* th = sm.Q[sg] + a * ldq;
+        R sr = 0, si = 0;
+        for (int k = 0; k < M; ++k) {
+          const R l = (R)lq[k];
+          sr = fma(l, th[k].x, sr);
+          si = fma(l, th[k].y, si);
+        }
+        Ps[sg][q * ns + a] = cm<R>(sr, si);
+      }
+    }
+    __syncthreads();
+    if (g < G) {
+      for (int sg = 0; sg < 2; ++sg) {             // V[q][c] = sum_b P[q][b] P[r_b][c]
+        const int ns = nsv[sg], na = tb.nact[sg];
+        const cplx<R>* P = Ps[sg];
+        const int* ract = tb.ract[sg];
+        for (int e = tid; e < na * ns; e += nt) {
+          const int q = e / ns, cc = e - q * ns;
+          cplx<R> s = cm<R>(R(0), R(0));
+          for (int b = 0; b < ns; ++b) s = cadd(s, cmul(P[q * ns + b], P[ract[b] * ns + cc]));
+          Vs[sg][q * ns + cc] = s;
+        }
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < tb.ndet; i += nt) {
+      const MdDet* dp = tb.dets + i;
+      cplx<R> tr_tot = cm<R>(R(0), R(0)), sq_tot = cm<R>(R(0), R(0));
+      for (int sg = 0; sg < 2; ++sg) {
+        const int ns = nsv[sg];
+        if (ns == 0) continue;
+        cplx<R> trM, sq;
+        md_spin_dispatch<R>(dp->E[sg], dp->h[sg], dp->p[sg], Ctab + (long)i * cst + coff[sg],
+                            Ps[sg], Vs[sg], tb.ract[sg], ns, g == G, trM, sq);
+        tr_tot = cadd(tr_tot, trM);
+        sq_tot = cadd(sq_tot, sq);
+      }
+      double2 acc = eacc[i];
+      if (g == G) {
+        acc.x += (double)tr_tot.x;
+        acc.y += (double)tr_tot.y;
+      } else {
+        const double xr = tr_tot.x, xi = tr_tot.y;
+        acc.x += 0.5 * ((xr * xr - xi * xi) - (double)sq_tot.x);
+        acc.y += 0.5 * (2.0 * xr * xi - (double)sq_tot.y);
+      }
+      eacc[i] = acc;
+    }
+  }
+  // E_L = sum_i w_i E_i, in determinant order per thread, then the block
+  double sr = 0.0, si = 0.0;
+  for (int i = tid; i < tb.ndet; i += nt) {
+    const cplx<R> wi = sm.wt[i];
+    const double2 e = eacc[i];
+    sr += (double)wi.x * e.x - (double)wi.y * e.y;
+    si += (double)wi.x * e.y + (double)wi.y * e.x;
+  }
+  sr = block_sum(sr, red);
+  si = block_sum(si, red);
+  if (tid == 0) eloc[w] = make_double2(sr, si);
+}
+
 template <typename K>
 size_t smem_opt_in(K kernel) {
   int dev = 0, optin = 48 * 1024;
@@ -497,6 +712,24 @@ cudaError_t launch_md_energy(cudaStream_t st, const MdTables& tb, int W, int M, 
                              double2* eloc, bool f64) {
   const size_t smem = md_energy_smem(M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet, f64);
   const int threads = 256;
+  // the hoisted kernel when its C_i table fits in shared memory
+  const size_t smem_h = smem + md_ctab_bytes(nu, nd, tb.emax[0], tb.emax[1], tb.ndet,
+                                             f64 ? 16 : 8);
+  if (f64) {
+    static const size_t cap_h = smem_opt_in(md_energy_hoisted_kernel<T, double>);
+    if (smem_h <= cap_h) {
+      md_energy_hoisted_kernel<T, double><<<W, threads, smem_h, st>>>(
+          tb, M, nu, nd, G, Theta, ldt, dn_off, logdet0, LtilA, ldg, gdn_off, eloc);
+      return cudaGetLastError();
+    }
+  } else {
+    static const size_t cap_h = smem_opt_in(md_energy_hoisted_kernel<T, float>);
+    if (smem_h <= cap_h) {
+      md_energy_hoisted_kernel<T, float><<<W, threads, smem_h, st>>>(
+          tb, M, nu, nd, G, Theta, ldt, dn_off, logdet0, LtilA, ldg, gdn_off, eloc);
+      return cudaGetLastError();
+    }
+  }
   if ((tb.ndet + threads - 1) / threads > MD_MAX_DET_PER_THREAD) return cudaErrorInvalidValue;
   if (f64) {
     static const size_t cap = smem_opt_in(md_energy_kernel<T, double>);

@@ -20,6 +20,7 @@ struct MdDet {
 struct MdTables {
   int ndet;
   int nact[2];              // active orbitals per spin
+  int emax[2];              // largest excitation count per spin over the determinants
   const MdDet* dets;        // [ndet], device
   const double2* cconj;     // [ndet] c_i^* (sign of the column order folded in), device
   const int* ract[2];       // [ns] active index of the reference orbital at each position
