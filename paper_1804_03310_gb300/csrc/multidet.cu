@@ -533,7 +533,7 @@ __device__ __forceinline__ void md_spin_dispatch(int E, const int* h, const int*
 __host__ __device__ __forceinline__ size_t md_ctab_bytes(int nu, int nd, int e_u, int e_d,
                                                          int ndet, size_t csize) {
   const size_t c = csize * (size_t)ndet * ((size_t)e_u * nu + (size_t)e_d * nd);
-  return ((c + 15) & ~(size_t)15) + 16 * (size_t)ndet;
+  return c + 15 + 16 * (size_t)ndet;   // 15: the accumulators start on a 16-byte address
 }
 
 // The local energy of md_energy_kernel with the Cholesky-independent parts
@@ -562,8 +562,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted
   const long cst = (long)tb.emax[0] * nu + (long)tb.emax[1] * nd;
   const long coff[2] = {0, (long)tb.emax[0] * nu};
   const size_t cbytes = sizeof(cplx<R>) * (size_t)tb.ndet * cst;
-  double2* eacc = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(Ctab) +
-                                             ((cbytes + 15) & ~(size_t)15));
+  double2* eacc = reinterpret_cast<double2*>(
+      ((uintptr_t)reinterpret_cast<unsigned char*>(Ctab) + cbytes + 15) & ~(uintptr_t)15);
   const int nsv[2] = {nu, nd};
   const int ldq = stage_ld(M);
   for (int i = tid; i < tb.ndet; i += nt) {        // C_i, once per walker

@@ -128,103 +128,6 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
   if (threadIdx.x == 0) lw[w] = make_double2(tre, tim);
 }
 
-// --------------------------------------------------------------- K5 (SIMT)
-constexpr int kTaylorThreads = 256;
-constexpr int kTaylorKC = 16;
-constexpr int kTaylorMaxR = 16;   // outputs per thread: M * NC <= 4096
-
-template <typename T>
-__global__ void __launch_bounds__(kTaylorThreads)
-taylor_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
-              const T* __restrict__ Pin, T* __restrict__ Pout) {
-  extern __shared__ unsigned char smem_raw[];
-  T* tc = reinterpret_cast<T*>(smem_raw);            // [NC][2][M]
-  T* vs = tc + (long)NC * 2 * M;                      // [2][KC][M]
-  const int w = blockIdx.x;
-  const int j0 = blockIdx.y * NC;
-  const int nc = min(NC, N - j0);
-  const T* Vw = V + (long)w * 2 * M * M;
-  const T* Pw = Pin + ((long)w * N + j0) * 2 * M;
-  T* Ow = Pout + ((long)w * N + j0) * 2 * M;
-  const int tid = threadIdx.x;
-  const int nout = M * nc;
-  for (int e = tid; e < NC * 2 * M; e += blockDim.x)
-    tc[e] = (e < nc * 2 * M) ? Pw[e] : T(0);
-  __syncthreads();
-  T ar[kTaylorMaxR], ai[kTaylorMaxR];
-#pragma unroll
-  for (int r = 0; r < kTaylorMaxR; ++r) {
-    int o = tid + r * kTaylorThreads;
-    if (o < nout) {
-      int i = o % M, jj = o / M;
-      ar[r] = tc[(jj * 2 + 0) * M + i];
-      ai[r] = tc[(jj * 2 + 1) * M + i];
-    } else {
-      ar[r] = T(0);
-      ai[r] = T(0);
-    }
-  }
-  for (int n = 1; n <= order; ++n) {
-    T tr[kTaylorMaxR], ti[kTaylorMaxR];
-#pragma unroll
-    for (int r = 0; r < kTaylorMaxR; ++r) { tr[r] = T(0); ti[r] = T(0); }
-    for (int k0 = 0; k0 < M; k0 += kTaylorKC) {
-      const int kc = min(kTaylorKC, M - k0);
-      __syncthreads();
-      // V is complex symmetric: row k of V is column k.
-      for (int e = tid; e < 2 * kTaylorKC * M; e += blockDim.x) {
-        int c = e / (kTaylorKC * M);
-        int rem = e - c * kTaylorKC * M;
-        int kk = rem / M, i = rem - kk * M;
-        vs[e] = (kk < kc) ? Vw[((long)c * M + (k0 + kk)) * M + i] : T(0);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < kTaylorMaxR; ++r) {
-        int o = tid + r * kTaylorThreads;
-        if (o >= nout) break;
-        int i = o % M, jj = o / M;
-        const T* tre = tc + (jj * 2 + 0) * M + k0;
-        const T* tim = tc + (jj * 2 + 1) * M + k0;
-        T sr = tr[r], si = ti[r];
-        for (int kk = 0; kk < kc; ++kk) {
-          T vr = vs[kk * M + i], vi = vs[(kTaylorKC + kk) * M + i];
-          T xr = tre[kk], xi = tim[kk];
-          sr = fma(vr, xr, sr);
-          sr = fma(-vi, xi, sr);
-          si = fma(vr, xi, si);
-          si = fma(vi, xr, si);
-        }
-        tr[r] = sr;
-        ti[r] = si;
-      }
-    }
-    __syncthreads();
-    const T inv_n = T(1) / T(n);
-#pragma unroll
-    for (int r = 0; r < kTaylorMaxR; ++r) {
-      int o = tid + r * kTaylorThreads;
-      if (o >= nout) break;
-      int i = o % M, jj = o / M;
-      T xr = tr[r] * inv_n, xi = ti[r] * inv_n;
-      tc[(jj * 2 + 0) * M + i] = xr;
-      tc[(jj * 2 + 1) * M + i] = xi;
-      ar[r] += xr;
-      ai[r] += xi;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < kTaylorMaxR; ++r) {
-    int o = tid + r * kTaylorThreads;
-    if (o >= nout) break;
-    int i = o % M, jj = o / M;
-    Ow[(jj * 2 + 0) * M + i] = ar[r];
-    Ow[(jj * 2 + 1) * M + i] = ai[r];
-  }
-}
-
-// --------------------------------------------------------------- K6
 // Complex value of the elimination's compute type R (double or float).
 template <typename R>
 struct __align__(2 * sizeof(R)) cx {
@@ -241,6 +144,153 @@ template <typename R>
 __device__ __forceinline__ cx<R> mul_c(cx<R> a, cx<R> b) {
   return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+
+// --------------------------------------------------------------- K5 (SIMT, tiled)
+// Asynchronous global -> shared copy of one element (4 or 8 bytes).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gsrc), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kTayKC = 16;           // rows of V per shared-memory chunk
+constexpr int kTayMaxThreads = 512;
+
+// Per walker and chunk of NC orbital columns: t_0 = Phi, t_n = V t_{n-1} / n,
+// out = sum_n t_n (Sec. II). One thread owns a TR x 4 tile of the M x NC
+// output (rows nr apart, columns nc4 apart) for the whole series: the term's
+// accumulator and the running sum stay in registers. V (complex symmetric, so
+// row k of V is column k) streams through two shared chunks of kTayKC rows
+// with cp.async, the next chunk in flight while the current one is used;
+// the terms alternate between two shared buffers.
+template <typename T, int TR>
+__global__ void __launch_bounds__(kTayMaxThreads)
+taylor_tiled_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
+                    const T* __restrict__ Pin, T* __restrict__ Pout) {
+  extern __shared__ unsigned char smem_raw[];
+  const int ldt = M | 1;
+  cx<T>* tb0 = reinterpret_cast<cx<T>*>(smem_raw);    // [NC][ldt]
+  cx<T>* tb1 = tb0 + (long)NC * ldt;                  // [NC][ldt]
+  T* vbuf = reinterpret_cast<T*>(tb1 + (long)NC * ldt);   // [2 buffers][2 planes][KC][M]
+  const int w = blockIdx.x;
+  const int j0 = blockIdx.y * NC;
+  const int nc = min(NC, N - j0);
+  const T* Vw = V + (long)w * 2 * M * M;
+  const T* Pw = Pin + ((long)w * N + j0) * 2 * M;
+  T* Ow = Pout + ((long)w * N + j0) * 2 * M;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nr = (M + TR - 1) / TR, nc4 = (nc + 3) >> 2;
+  const bool owner = tid < nr * nc4;
+  const int rt = owner ? tid % nr : 0, ct = owner ? tid / nr : 0;
+  int rr[TR], cc[4];
+#pragma unroll
+  for (int u = 0; u < TR; ++u) rr[u] = min(rt + u * nr, M - 1);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) cc[v] = min(ct + v * nc4, nc - 1);
+  const int nchunk = (M + kTayKC - 1) / kTayKC;
+  const int total = order * nchunk;
+  // copy chunk q % nchunk of V into buffer q & 1 (this thread's share)
+  const int per = kTayKC * M;
+  auto issue = [&](int q) {
+    const int k0 = (q % nchunk) * kTayKC;
+    const int kc = min(kTayKC, M - k0);
+    T* dst = vbuf + (long)(q & 1) * 2 * per;
+    for (int e = tid; e < kc * M; e += nt) {
+      cp_async_elem<sizeof(T)>(dst + e, Vw + (long)k0 * M + e);
+      cp_async_elem<sizeof(T)>(dst + per + e, Vw + (long)(M + k0) * M + e);
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  for (int e = tid; e < nc * 2 * M; e += nt) {        // t_0 from Phi
+    const int j = e / (2 * M), r = e - j * 2 * M;
+    reinterpret_cast<T*>(&tb0[j * ldt + (r < M ? r : r - M)])[r < M ? 0 : 1] = Pw[e];
+  }
+  __syncthreads();
+  T sr[TR][4], si[TR][4], ar[TR][4], ai[TR][4];
+#pragma unroll
+  for (int u = 0; u < TR; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const cx<T> x = tb0[cc[v] * ldt + rr[u]];
+      sr[u][v] = x.x; si[u][v] = x.y;
+      ar[u][v] = T(0); ai[u][v] = T(0);
+    }
+  cx<T>* tin = tb0;
+  cx<T>* tout = tb1;
+  for (int q = 0; q < total; ++q) {
+    if (q + 1 < total) {
+      issue(q + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();                                  // chunk q and the last term are visible
+    const int k0 = (q % nchunk) * kTayKC;
+    const int kc = min(kTayKC, M - k0);
+    const T* vr = vbuf + (long)(q & 1) * 2 * per;
+    const T* vi = vr + per;
+    if (owner) {
+      for (int kk = 0; kk < kc; ++kk) {
+        T qr[TR], qi[TR];
+        cx<T> x[4];
+#pragma unroll
+        for (int u = 0; u < TR; ++u) { qr[u] = vr[kk * M + rr[u]]; qi[u] = vi[kk * M + rr[u]]; }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v] = tin[cc[v] * ldt + k0 + kk];
+#pragma unroll
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            ar[u][v] = fma(qr[u], x[v].x, fma(-qi[u], x[v].y, ar[u][v]));
+            ai[u][v] = fma(qr[u], x[v].y, fma(qi[u], x[v].x, ai[u][v]));
+          }
+      }
+    }
+    if (q % nchunk == nchunk - 1) {                   // term n = q / nchunk + 1 complete
+      const T inv_n = T(1) / T(q / nchunk + 1);
+      if (owner) {
+#pragma unroll
+        for (int u = 0; u < TR; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const T xr = ar[u][v] * inv_n, xi = ai[u][v] * inv_n;
+            sr[u][v] += xr;
+            si[u][v] += xi;
+            ar[u][v] = T(0);
+            ai[u][v] = T(0);
+            tout[cc[v] * ldt + rr[u]] = mk<T>(xr, xi);
+          }
+      }
+      cx<T>* t = tin;
+      tin = tout;
+      tout = t;
+    }
+    __syncthreads();                                  // buffer q & 1 free for chunk q + 2
+  }
+  if (owner) {
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = rt + u * nr, j = ct + v * nc4;
+        if (r < M && j < nc) {
+          Ow[(long)j * 2 * M + r] = sr[u][v];
+          Ow[(long)j * 2 * M + M + r] = si[u][v];
+        }
+      }
+  }
+}
+
+// --------------------------------------------------------------- K6
 
 // Row stride (in complex values) of a walker block staged as [column][row]:
 // odd, so that lanes reading the same row of consecutive columns hit
@@ -968,15 +1018,25 @@ cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long l
 template <typename T>
 cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
                           const T* V, const T* Phi_in, T* Phi_out) {
-  static const size_t smem_cap = allow_big_smem(taylor_kernel<T>);
-  int NC = 4096 / M;
-  if (NC > 16) NC = 16;
-  if (NC < 1) return cudaErrorInvalidValue;
-  if (NC > N) NC = N;
-  size_t smem = sizeof(T) * ((size_t)NC * 2 * M + 2 * (size_t)kTaylorKC * M);
-  if (smem > smem_cap) return cudaErrorInvalidValue;
-  dim3 grid(W, (N + NC - 1) / NC);
-  taylor_kernel<T><<<grid, kTaylorThreads, smem, st>>>(M, N, NC, order, V, Phi_in, Phi_out);
+  constexpr int TR = sizeof(T) == 4 ? 4 : 2;
+  static const size_t cap = allow_big_smem(taylor_tiled_kernel<T, TR>);
+  if (M < 1 || N < 1) return cudaErrorInvalidValue;
+  const int nr = (M + TR - 1) / TR;
+  const int ldt = M | 1;
+  auto smem_for = [&](int nc) {
+    return sizeof(T) * (4 * (size_t)nc * ldt + 4 * (size_t)kTayKC * M);
+  };
+  int ncmax = 4 * (kTayMaxThreads / nr);             // tiles within one block
+  if (ncmax > N) ncmax = N;
+  while (ncmax > 1 && smem_for(ncmax) > cap) --ncmax;
+  if (ncmax < 1 || nr > kTayMaxThreads || smem_for(ncmax) > cap) return cudaErrorInvalidValue;
+  const int pieces = (N + ncmax - 1) / ncmax;        // balanced column chunks
+  const int NC = (N + pieces - 1) / pieces;
+  const int tiles = nr * ((NC + 3) / 4);
+  const int threads = (tiles + 31) / 32 * 32;
+  dim3 grid(W, pieces);
+  taylor_tiled_kernel<T, TR><<<grid, threads, smem_for(NC), st>>>(M, N, NC, order, V, Phi_in,
+                                                                  Phi_out);
   return cudaGetLastError();
 }
 
