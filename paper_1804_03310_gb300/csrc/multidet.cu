@@ -131,12 +131,32 @@ struct MdSmem {
   }
 };
 
+// C = K^-1 (Omega[p] - E_h^T) for one determinant and spin, rows l < E of
+// length ns, from the inverse det_k wrote.
+template <typename R>
+__device__ void fill_c(int E, const int* p, const int* h, const cplx<R>* Om, int ns,
+                       const cplx<R> (&inv)[EMAX][EMAX], cplx<R>* C) {
+  for (int l = 0; l < E; ++l)
+    for (int a = 0; a < ns; ++a) {
+      cplx<R> s = cm<R>(R(0), R(0));
+      for (int m = 0; m < E; ++m) {
+        cplx<R> r = Om[p[m] * ns + a];
+        if (a == h[m]) r.x -= R(1);
+        s = cadd(s, cmul(inv[l][m], r));
+      }
+      C[l * ns + a] = s;
+    }
+}
+
 // Phases shared by the step kernel and the energy kernel: stage Theta_0,
 // form Omega, the ratios, O_T and the normalised weights. Returns ln O_T.
+// With ctab, also the C table: determinant i's rows for the up spin at
+// ctab + i cst, for the down spin at ctab + i cst + coff1.
 template <typename T, typename R>
 __device__ double2 md_weights(const MdTables& tb, int M, int nu, int nd, const T* Theta,
                               long ldt, long dn_off, const double2* logdet0, int w,
-                              MdSmem<R>& sm, double* red) {
+                              MdSmem<R>& sm, double* red, cplx<R>* ctab = nullptr,
+                              long cst = 0, long coff1 = 0) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ldq = stage_ld(M);
   const int nsv[2] = {nu, nd};
@@ -172,7 +192,10 @@ __device__ double2 md_weights(const MdTables& tb, int M, int nu, int nd, const T
     const MdDet d = tb.dets[i];
     cplx<R> inv[EMAX][EMAX];
     const cplx<R> ru = nu ? det_k<R>(d.E[0], d.p[0], d.h[0], sm.Om[0], nu, inv) : cm<R>(R(1), R(0));
+    if (ctab && nu) fill_c<R>(d.E[0], d.p[0], d.h[0], sm.Om[0], nu, inv, ctab + (long)i * cst);
     const cplx<R> rd = nd ? det_k<R>(d.E[1], d.p[1], d.h[1], sm.Om[1], nd, inv) : cm<R>(R(1), R(0));
+    if (ctab && nd)
+      fill_c<R>(d.E[1], d.p[1], d.h[1], sm.Om[1], nd, inv, ctab + (long)i * cst + coff1);
     const double ax = (double)ru.x * rd.x - (double)ru.y * rd.y;
     const double ay = (double)ru.x * rd.y + (double)ru.y * rd.x;
     const double2 cc = tb.cconj[i];
@@ -200,7 +223,9 @@ __device__ double2 md_weights(const MdTables& tb, int M, int nu, int nd, const T
 }
 
 // ------------------------------------------------------------------ step
-template <typename T, typename R>
+// HC: the C_i table fits in shared memory (after Lambda) and the Lambda rows
+// read it instead of inverting K_i per row and determinant.
+template <typename T, typename R, bool HC>
 __global__ void md_step_kernel(MdTables tb, int M, int nu, int nd, const T* __restrict__ Theta,
                                long ldt, long dn_off, const double2* __restrict__ logdet0,
                                double2* __restrict__ logO_new, T* __restrict__ Gamma,
@@ -211,19 +236,58 @@ __global__ void md_step_kernel(MdTables tb, int M, int nu, int nd, const T* __re
   sm.carve(smem_raw, M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet);
   const int w = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double2 lo = md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red);
-  if (tid == 0) logO_new[w] = lo;
   // Lambda rows are accumulated warp by warp (one row of one spin per warp
   // pass, lanes over positions); every entry has a single owning lane, and
   // determinants are visited in order, so the sums are deterministic.
   cplx<R>* Lam = reinterpret_cast<cplx<R>*>(smem_raw + MdSmem<R>::bytes(M, nu, nd, tb.nact[0],
                                                                          tb.nact[1], tb.ndet));
   cplx<R>* Lams[2] = {Lam, Lam + (long)nu * tb.nact[0]};
+  cplx<R>* Ctab = Lam + (long)nu * tb.nact[0] + (long)nd * tb.nact[1];
+  const long cst = (long)tb.emax[0] * nu + (long)tb.emax[1] * nd;
+  const long coff1 = (long)tb.emax[0] * nu;
+  const double2 lo = md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red,
+                                      HC ? Ctab : nullptr, cst, coff1);
+  if (tid == 0) logO_new[w] = lo;
   const int nsv[2] = {nu, nd};
   for (int e = tid; e < nu * tb.nact[0] + nd * tb.nact[1]; e += nt) Lam[e] = cm<R>(R(0), R(0));
   __syncthreads();
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int row = wid; row < nu + nd; row += nw) {
+  if (HC) {
+    for (int row = wid; row < nu + nd; row += nw) {
+      const int sg = row >= nu;
+      const int h = row - (sg ? nu : 0);
+      const int ns = nsv[sg], na = tb.nact[sg];
+      cplx<R>* Lr = Lams[sg] + (long)h * na;
+      const int* ract = tb.ract[sg];
+      // determinants without a hole at h add w_i at the reference orbital,
+      // an entry no other determinant touches for this row
+      cplx<R> wsum = cm<R>(R(0), R(0));
+      for (int i = 0; i < tb.ndet; ++i) {
+        const MdDet* dp = tb.dets + i;
+        const int E = dp->E[sg];
+        int l = -1;
+        for (int t = 0; t < E; ++t)
+          if (dp->h[sg][t] == h) l = t;
+        const cplx<R> wi = sm.wt[i];
+        if (l < 0) {
+          wsum = cadd(wsum, wi);
+          continue;
+        }
+        const cplx<R>* C = Ctab + (long)i * cst + (sg ? coff1 : 0) + (long)l * ns;
+        for (int a = lane; a < ns; a += 32) {
+          int q = ract[a];
+          for (int m = 0; m < E; ++m)
+            if (a == dp->h[sg][m]) q = dp->p[sg][m];
+          cplx<R> v = cm<R>(R(0), R(0));
+          if (a == h) v = wi;
+          v = csub(v, cmul(wi, C[a]));
+          Lr[q] = cadd(Lr[q], v);
+        }
+      }
+      if (lane == 0) Lr[ract[h]] = cadd(Lr[ract[h]], wsum);
+    }
+  }
+  for (int row = HC ? nu + nd : wid; row < nu + nd; row += nw) {
     const int sg = row >= nu;
     const int h = row - (sg ? nu : 0);
     const int ns = nsv[sg], na = tb.nact[sg];
@@ -552,7 +616,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted
   sm.carve(smem_raw, M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet);
   const int w = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
-  md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red);
   cplx<R>* P0 = reinterpret_cast<cplx<R>*>(smem_raw + MdSmem<R>::bytes(M, nu, nd, tb.nact[0],
                                                                        tb.nact[1], tb.ndet));
   cplx<R>* Ps[2] = {P0, P0 + (long)tb.nact[0] * nu};
@@ -566,27 +629,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted
       ((uintptr_t)reinterpret_cast<unsigned char*>(Ctab) + cbytes + 15) & ~(uintptr_t)15);
   const int nsv[2] = {nu, nd};
   const int ldq = stage_ld(M);
-  for (int i = tid; i < tb.ndet; i += nt) {        // C_i, once per walker
-    const MdDet* dp = tb.dets + i;
-    eacc[i] = make_double2(0.0, 0.0);
-    for (int sg = 0; sg < 2; ++sg) {
-      const int ns = nsv[sg], E = dp->E[sg];
-      if (ns == 0 || E == 0) continue;
-      cplx<R> inv[EMAX][EMAX];
-      det_k<R>(E, dp->p[sg], dp->h[sg], sm.Om[sg], ns, inv);
-      cplx<R>* C = Ctab + (long)i * cst + coff[sg];
-      for (int l = 0; l < E; ++l)
-        for (int a = 0; a < ns; ++a) {
-          cplx<R> s = cm<R>(R(0), R(0));
-          for (int m = 0; m < E; ++m) {
-            cplx<R> r = sm.Om[sg][dp->p[sg][m] * ns + a];
-            if (a == dp->h[sg][m]) r.x -= R(1);
-            s = cadd(s, cmul(inv[l][m], r));
-          }
-          C[l * ns + a] = s;
-        }
-    }
-  }
+  // the weights, and C_i = K_i^-1 (Omega[p] - E_h^T) once per walker
+  md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red, Ctab, cst, coff[1]);
+  for (int i = tid; i < tb.ndet; i += nt) eacc[i] = make_double2(0.0, 0.0);
   for (int g = 0; g <= G; ++g) {
     __syncthreads();
     for (int sg = 0; sg < 2; ++sg) {               // P = L^act_g Theta_0
@@ -686,23 +731,35 @@ size_t md_energy_smem(int M, int nu, int nd, int na_u, int na_d, int ndet, bool 
          c * ((size_t)nu * na_u + (size_t)nd * na_d);
 }
 
+template <typename T, typename R>
+cudaError_t launch_md_step_r(cudaStream_t st, const MdTables& tb, int W, int M, int nu, int nd,
+                             const T* Theta, long ldt, long dn_off, const double2* logdet0,
+                             double2* logO_new, T* Gamma, long ldg, long gdn_off) {
+  const bool f64 = sizeof(R) == 8;
+  const size_t smem = md_step_smem(M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet, f64);
+  const size_t smem_h = smem + md_ctab_bytes(nu, nd, tb.emax[0], tb.emax[1], tb.ndet,
+                                             sizeof(cplx<R>));
+  static const size_t cap_h = smem_opt_in(md_step_kernel<T, R, true>);
+  if (smem_h <= cap_h) {
+    md_step_kernel<T, R, true><<<W, 256, smem_h, st>>>(tb, M, nu, nd, Theta, ldt, dn_off,
+                                                       logdet0, logO_new, Gamma, ldg, gdn_off);
+    return cudaGetLastError();
+  }
+  static const size_t cap = smem_opt_in(md_step_kernel<T, R, false>);
+  if (smem > cap) return cudaErrorInvalidValue;
+  md_step_kernel<T, R, false><<<W, 256, smem, st>>>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0,
+                                                    logO_new, Gamma, ldg, gdn_off);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_md_step(cudaStream_t st, const MdTables& tb, int W, int M, int nu, int nd,
                            const T* Theta, long ldt, long dn_off, const double2* logdet0,
                            double2* logO_new, T* Gamma, long ldg, long gdn_off, bool f64) {
-  const size_t smem = md_step_smem(M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet, f64);
-  if (f64) {
-    static const size_t cap = smem_opt_in(md_step_kernel<T, double>);
-    if (smem > cap) return cudaErrorInvalidValue;
-    md_step_kernel<T, double><<<W, 256, smem, st>>>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0,
-                                                    logO_new, Gamma, ldg, gdn_off);
-  } else {
-    static const size_t cap = smem_opt_in(md_step_kernel<T, float>);
-    if (smem > cap) return cudaErrorInvalidValue;
-    md_step_kernel<T, float><<<W, 256, smem, st>>>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0,
-                                                   logO_new, Gamma, ldg, gdn_off);
-  }
-  return cudaGetLastError();
+  return f64 ? launch_md_step_r<T, double>(st, tb, W, M, nu, nd, Theta, ldt, dn_off, logdet0,
+                                           logO_new, Gamma, ldg, gdn_off)
+             : launch_md_step_r<T, float>(st, tb, W, M, nu, nd, Theta, ldt, dn_off, logdet0,
+                                          logO_new, Gamma, ldg, gdn_off);
 }
 
 template <typename T>
