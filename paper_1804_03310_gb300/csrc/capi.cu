@@ -1243,6 +1243,12 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     std::vector<int> ract_u(c->nu + 1), ract_d(c->nd + 1);
     for (int a = 0; a <= c->nu; ++a) ract_u[a] = a;
     for (int a = 0; a <= c->nd; ++a) ract_d[a] = a;
+    long ctot = 0;                       // compact C table offsets
+    for (MdDet& d : dets_h) {
+      d.coff = (int)ctot;
+      ctot += (long)d.E[0] * c->nu + (long)d.E[1] * c->nd;
+    }
+    c->mdt.ctot = (int)ctot;
     CK(cudaMemcpyAsync(c->md_dets, dets_h.data(), sizeof(MdDet) * c->ndet,
                        cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->md_cc, cconj_h.data(), sizeof(double2) * c->ndet,
@@ -1266,9 +1272,6 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     c->mdt.ndet = c->ndet;
     c->mdt.nact[0] = c->nact[0];
     c->mdt.nact[1] = c->nact[1];
-    c->mdt.emax[0] = c->mdt.emax[1] = 0;
-    for (const MdDet& d : dets_h)
-      for (int sg = 0; sg < 2; ++sg) c->mdt.emax[sg] = std::max(c->mdt.emax[sg], d.E[sg]);
     c->mdt.dets = (const MdDet*)c->md_dets;
     c->mdt.cconj = (const double2*)c->md_cc;
     c->mdt.ract[0] = (const int*)c->md_r0;

@@ -151,12 +151,11 @@ __device__ void fill_c(int E, const int* p, const int* h, const cplx<R>* Om, int
 // Phases shared by the step kernel and the energy kernel: stage Theta_0,
 // form Omega, the ratios, O_T and the normalised weights. Returns ln O_T.
 // With ctab, also the C table: determinant i's rows for the up spin at
-// ctab + i cst, for the down spin at ctab + i cst + coff1.
+// ctab + coff_i, for the down spin after them.
 template <typename T, typename R>
 __device__ double2 md_weights(const MdTables& tb, int M, int nu, int nd, const T* Theta,
                               long ldt, long dn_off, const double2* logdet0, int w,
-                              MdSmem<R>& sm, double* red, cplx<R>* ctab = nullptr,
-                              long cst = 0, long coff1 = 0) {
+                              MdSmem<R>& sm, double* red, cplx<R>* ctab = nullptr) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ldq = stage_ld(M);
   const int nsv[2] = {nu, nd};
@@ -192,10 +191,10 @@ __device__ double2 md_weights(const MdTables& tb, int M, int nu, int nd, const T
     const MdDet d = tb.dets[i];
     cplx<R> inv[EMAX][EMAX];
     const cplx<R> ru = nu ? det_k<R>(d.E[0], d.p[0], d.h[0], sm.Om[0], nu, inv) : cm<R>(R(1), R(0));
-    if (ctab && nu) fill_c<R>(d.E[0], d.p[0], d.h[0], sm.Om[0], nu, inv, ctab + (long)i * cst);
+    if (ctab && nu) fill_c<R>(d.E[0], d.p[0], d.h[0], sm.Om[0], nu, inv, ctab + d.coff);
     const cplx<R> rd = nd ? det_k<R>(d.E[1], d.p[1], d.h[1], sm.Om[1], nd, inv) : cm<R>(R(1), R(0));
     if (ctab && nd)
-      fill_c<R>(d.E[1], d.p[1], d.h[1], sm.Om[1], nd, inv, ctab + (long)i * cst + coff1);
+      fill_c<R>(d.E[1], d.p[1], d.h[1], sm.Om[1], nd, inv, ctab + d.coff + (long)d.E[0] * nu);
     const double ax = (double)ru.x * rd.x - (double)ru.y * rd.y;
     const double ay = (double)ru.x * rd.y + (double)ru.y * rd.x;
     const double2 cc = tb.cconj[i];
@@ -243,10 +242,8 @@ __global__ void md_step_kernel(MdTables tb, int M, int nu, int nd, const T* __re
                                                                          tb.nact[1], tb.ndet));
   cplx<R>* Lams[2] = {Lam, Lam + (long)nu * tb.nact[0]};
   cplx<R>* Ctab = Lam + (long)nu * tb.nact[0] + (long)nd * tb.nact[1];
-  const long cst = (long)tb.emax[0] * nu + (long)tb.emax[1] * nd;
-  const long coff1 = (long)tb.emax[0] * nu;
   const double2 lo = md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red,
-                                      HC ? Ctab : nullptr, cst, coff1);
+                                      HC ? Ctab : nullptr);
   if (tid == 0) logO_new[w] = lo;
   const int nsv[2] = {nu, nd};
   for (int e = tid; e < nu * tb.nact[0] + nd * tb.nact[1]; e += nt) Lam[e] = cm<R>(R(0), R(0));
@@ -273,7 +270,7 @@ __global__ void md_step_kernel(MdTables tb, int M, int nu, int nd, const T* __re
           wsum = cadd(wsum, wi);
           continue;
         }
-        const cplx<R>* C = Ctab + (long)i * cst + (sg ? coff1 : 0) + (long)l * ns;
+        const cplx<R>* C = Ctab + dp->coff + (sg ? (long)dp->E[0] * nu : 0) + (long)l * ns;
         for (int a = lane; a < ns; a += 32) {
           int q = ract[a];
           for (int m = 0; m < E; ++m)
@@ -591,13 +588,12 @@ __device__ __forceinline__ void md_spin_dispatch(int E, const int* h, const int*
   }
 }
 
-// Shared bytes the hoisted energy kernel adds: the C_i table
-// ([ndet][emax_up nu + emax_dn nd]) and one FP64 complex accumulator per
-// determinant.
-__host__ __device__ __forceinline__ size_t md_ctab_bytes(int nu, int nd, int e_u, int e_d,
-                                                         int ndet, size_t csize) {
-  const size_t c = csize * (size_t)ndet * ((size_t)e_u * nu + (size_t)e_d * nd);
-  return c + 15 + 16 * (size_t)ndet;   // 15: the accumulators start on a 16-byte address
+// Shared bytes the C_i table takes (determinant i's E_i^up rows of n_up, then
+// E_i^dn rows of n_dn, at its offset coff_i) plus one FP64 complex
+// accumulator per determinant for the energy kernel.
+__host__ __device__ __forceinline__ size_t md_ctab_bytes(int ctot, int ndet, size_t csize) {
+  // 15: the accumulators start on a 16-byte address
+  return csize * (size_t)ctot + 15 + 16 * (size_t)ndet;
 }
 
 // The local energy of md_energy_kernel with the Cholesky-independent parts
@@ -622,16 +618,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted
   cplx<R>* V0 = P0 + (long)tb.nact[0] * nu + (long)tb.nact[1] * nd;
   cplx<R>* Vs[2] = {V0, V0 + (long)tb.nact[0] * nu};
   cplx<R>* Ctab = V0 + (long)tb.nact[0] * nu + (long)tb.nact[1] * nd;
-  const long cst = (long)tb.emax[0] * nu + (long)tb.emax[1] * nd;
-  const long coff[2] = {0, (long)tb.emax[0] * nu};
-  const size_t cbytes = sizeof(cplx<R>) * (size_t)tb.ndet * cst;
+  const size_t cbytes = sizeof(cplx<R>) * (size_t)tb.ctot;
   double2* eacc = reinterpret_cast<double2*>(
       ((uintptr_t)reinterpret_cast<unsigned char*>(Ctab) + cbytes + 15) & ~(uintptr_t)15);
   const int nsv[2] = {nu, nd};
   const int ldq = stage_ld(M);
   // the weights, and C_i = K_i^-1 (Omega[p] - E_h^T) once per walker
-  md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red, Ctab, cst, coff[1]);
+  md_weights<T, R>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0, w, sm, red, Ctab);
   for (int i = tid; i < tb.ndet; i += nt) eacc[i] = make_double2(0.0, 0.0);
+  MdDet* dets = reinterpret_cast<MdDet*>(eacc + tb.ndet);   // the table, read every pass
+  for (int e = tid; e < tb.ndet * (int)(sizeof(MdDet) / sizeof(int)); e += nt)
+    reinterpret_cast<int*>(dets)[e] = reinterpret_cast<const int*>(tb.dets)[e];
   for (int g = 0; g <= G; ++g) {
     __syncthreads();
     for (int sg = 0; sg < 2; ++sg) {               // P = L^act_g Theta_0
@@ -666,13 +663,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted
       __syncthreads();
     }
     for (int i = tid; i < tb.ndet; i += nt) {
-      const MdDet* dp = tb.dets + i;
+      const MdDet* dp = dets + i;
       cplx<R> tr_tot = cm<R>(R(0), R(0)), sq_tot = cm<R>(R(0), R(0));
       for (int sg = 0; sg < 2; ++sg) {
         const int ns = nsv[sg];
         if (ns == 0) continue;
         cplx<R> trM, sq;
-        md_spin_dispatch<R>(dp->E[sg], dp->h[sg], dp->p[sg], Ctab + (long)i * cst + coff[sg],
+        md_spin_dispatch<R>(dp->E[sg], dp->h[sg], dp->p[sg],
+                            Ctab + dp->coff + (sg ? (long)dp->E[0] * nu : 0),
                             Ps[sg], Vs[sg], tb.ract[sg], ns, g == G, trM, sq);
         tr_tot = cadd(tr_tot, trM);
         sq_tot = cadd(sq_tot, sq);
@@ -737,8 +735,7 @@ cudaError_t launch_md_step_r(cudaStream_t st, const MdTables& tb, int W, int M, 
                              double2* logO_new, T* Gamma, long ldg, long gdn_off) {
   const bool f64 = sizeof(R) == 8;
   const size_t smem = md_step_smem(M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet, f64);
-  const size_t smem_h = smem + md_ctab_bytes(nu, nd, tb.emax[0], tb.emax[1], tb.ndet,
-                                             sizeof(cplx<R>));
+  const size_t smem_h = smem + md_ctab_bytes(tb.ctot, tb.ndet, sizeof(cplx<R>));
   static const size_t cap_h = smem_opt_in(md_step_kernel<T, R, true>);
   if (smem_h <= cap_h) {
     md_step_kernel<T, R, true><<<W, 256, smem_h, st>>>(tb, M, nu, nd, Theta, ldt, dn_off,
@@ -770,8 +767,8 @@ cudaError_t launch_md_energy(cudaStream_t st, const MdTables& tb, int W, int M, 
   const size_t smem = md_energy_smem(M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet, f64);
   const int threads = 256;
   // the hoisted kernel when its C_i table fits in shared memory
-  const size_t smem_h = smem + md_ctab_bytes(nu, nd, tb.emax[0], tb.emax[1], tb.ndet,
-                                             f64 ? 16 : 8);
+  const size_t smem_h = smem + md_ctab_bytes(tb.ctot, tb.ndet, f64 ? 16 : 8) +
+                        sizeof(MdDet) * (size_t)tb.ndet;
   if (f64) {
     static const size_t cap_h = smem_opt_in(md_energy_hoisted_kernel<T, double>);
     if (smem_h <= cap_h) {

@@ -15,12 +15,14 @@ struct MdDet {
   int E[2];
   int h[2][MD_EMAX];
   int p[2][MD_EMAX];
+  int coff;   // start of this determinant's C rows in the C table (complex values):
+              // E[0] rows of n_up for the up spin, then E[1] rows of n_dn
 };
 
 struct MdTables {
   int ndet;
   int nact[2];              // active orbitals per spin
-  int emax[2];              // largest excitation count per spin over the determinants
+  int ctot;                 // complex values in the C table: sum_i E_i^up n_up + E_i^dn n_dn
   const MdDet* dets;        // [ndet], device
   const double2* cconj;     // [ndet] c_i^* (sign of the column order folded in), device
   const int* ract[2];       // [ns] active index of the reference orbital at each position
