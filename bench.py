@@ -253,6 +253,20 @@ def cpu_oracle(name, budget_s=20.0):
 
 # ------------------------------------------------------------------ GPU arm
 
+def max_over_ranks(x, device):
+    """The slowest rank's value (every rank gets it): the job's time is the
+    time of its slowest replica."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, max_ms):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -303,9 +317,7 @@ def _timed(args, s, stream, rank, world):
     hist = ctx.afqmc_energy_history()
     ctx.close()
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
     e2e = None if args.no_e2e else run_e2e(args, s)
     return s, total_ms, launches, kstats, clk.summary(), hist, e2e
 
@@ -507,8 +519,7 @@ def main():
     if rank != 0:
         return 0
     peaks, src = load_peaks()
-    ws = s.n_walkers * BLOCK * args.steps * world
-    value = ws / (total_ms / 1e3)
+    value = whole_job_value(s.n_walkers * BLOCK * args.steps, world, total_ms)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
