@@ -79,12 +79,14 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
-def roofline_for(kernel_stats, precision, peaks, src):
-    """Dominant kernel of the timed region against its bound."""
+def roofline_for(kernel_stats, precision, peaks, src, s, workload_name):
+    """Dominant kernel of the timed region against its bound. For M > 64 the
+    Taylor series runs on the CUDA cores (between two half-step GEMMs), so
+    the propagate group is rated against the FP32 CUDA-core peak there."""
     best = max(kernel_stats.items(), key=lambda kv: kv[1]["total_ms"])
     name, st = best
     avg_s = st["total_ms"] / max(1, st["launches"]) / 1e3
-    tensor_groups = ("force_bias", "one_body", "propagate", "energy")
+    tensor_groups = ("force_bias", "one_body", "energy") + (("propagate",) if s.M <= 64 else ())
     if st["is_bytes"]:
         bound, unit = "hbm", "GB/s"
         achieved = st["work"] / avg_s / 1e9
@@ -111,7 +113,7 @@ def roofline_for(kernel_stats, precision, peaks, src):
         achieved = st["work"] / avg_s / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * TF32_OVER_BF16
         peak_src = f"bf16 sustained ({src}) x 0.5 nominal TF32 ratio"
-    traffic = lookup_traffic(name, precision)
+    traffic = lookup_traffic(name, precision, workload_name)
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 3),
             "peak": round(peak, 3), "unit": unit, "frac": round(achieved / peak, 4),
             "peak_source": peak_src,
@@ -120,15 +122,17 @@ def roofline_for(kernel_stats, precision, peaks, src):
             "work_per_launch": st["work"]}
 
 
-def lookup_traffic(kernel, precision):
-    """DRAM bytes per launch from the committed ncu summary, if one matches."""
+def lookup_traffic(kernel, precision, workload_name):
+    """DRAM bytes per launch from the committed ncu summary, if one matches
+    the kernel group, precision and workload."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     for line in open(p):
         t = line.split()
-        if len(t) >= 4 and not line.startswith("#") and t[0] == kernel and t[1] == precision:
-            return float(t[2])
+        if (len(t) >= 5 and not line.startswith("#") and t[0] == kernel and t[1] == precision
+                and t[2] == workload_name):
+            return float(t[3])
     return None
 
 
@@ -531,7 +535,7 @@ def main():
                    "l2": "flushed (256 MB write) between timed iterations",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gpu_launches": int(launches),
-        "roofline": roofline_for(kstats, args.precision, peaks, src),
+        "roofline": roofline_for(kstats, args.precision, peaks, src, s, args.workload),
         "kernels_ms": {k: round(v["total_ms"], 3) for k, v in kstats.items()},
         "clocks": clocks,
         "energy_last": float(hist[-1][1]) if len(hist) else None,
