@@ -79,6 +79,8 @@ def test_c1_twenty_steps_fp64():
     (12, 4, 0, 9, 3),       # no down electrons
     (3, 1, 1, 1, 1),        # one field, one walker
     (70, 5, 9, 130, 40),    # unequal spins, long contraction
+    (100, 34, 14, 40, 4),   # M > 96: 256-thread blocks, a 34-row spin block,
+                            # two column chunks per walker in the CUDA-core Taylor
 ])
 def test_ragged_sizes_fp64(M, nu, nd, G, W):
     s = small_system(M=M, n_up=nu, n_dn=nd, n_chol=G, seed=M + G, l_sigma=0.08,
