@@ -305,6 +305,21 @@ def test_weight_update_phaseless_cut():
     assert abs(out[3] - np.exp(0.5 - 0.01)) < 1e-15
 
 
+def test_phaseless_cut_uses_overlap_phase_only():
+    """Sec. II: the cut is max(0, cos dtheta) with dtheta the phase of the
+    overlap ratio <Psi_T|phi'>/<Psi_T|phi> alone; the importance factor's
+    phase enters the weight only through its modulus."""
+    w = np.array([1.0, 1.0])
+    lo = np.zeros(2, complex)
+    ln = np.array([0.05 + 0.2j, 0.05 - 1.0j])
+    x = np.array([[1.0], [1.0]])
+    xb = np.array([[1.5j], [0.9j]])       # importance phase 1.5 and 0.9
+    out = O.update_weights(w, lo, ln, x, xb, 0.01, -1.0)
+    # |exp(x xbar - xbar^2/2)| = exp(Re(-xbar^2/2)) = exp(xbar_im^2 / 2)
+    assert abs(out[0] - np.exp(0.05 + 1.5 ** 2 / 2 - 0.01) * np.cos(0.2)) < 1e-14
+    assert abs(out[1] - np.exp(0.05 + 0.9 ** 2 / 2 - 0.01) * np.cos(1.0)) < 1e-14
+
+
 def test_weight_cap_option():
     # the cap (an option beside the paper's step) clips at cap * w_ref and
     # changes nothing below it; an unbounded cap is the uncapped update
