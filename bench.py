@@ -393,7 +393,34 @@ def fp64_compare(args, s, hist):
     dgemm = 2.0 * n ** 3 * reps / (a.elapsed_time(e) / 1e3) / 1e12
     return {"value": round(v64, 1), "unit": METRIC, "blocks_timed": len(timed),
             "dgemm_tflops": round(dgemm, 3),
-            "energy_check": energy_check(args.precision)}
+            "energy_check": energy_check(args.precision),
+            "energy_check_shapes": energy_check_shapes(args.precision)}
+
+
+def energy_check_shapes(precision):
+    """Paired energy deviation at the full-size shapes: the H-chain shape
+    (200 steps), the TM-atom shape (100 steps) and the multi-determinant
+    shape (200 steps), each in `precision` and in FP64 on the GPU with the
+    same seed, comb off, one measurement every 20 steps. Walker i of one run
+    is walker i of the other, so the difference of the mixed estimates is
+    the precision error alone, whether or not the energy still drifts."""
+    import numpy as np
+    from synth import CONFIGS
+    from paper_1804_03310_gb300 import Afqmc
+    out = {}
+    for name, n_steps in (("c2", 200), ("c3", 100), ("c4", 200)):
+        s = CONFIGS[name]().replace(pc_every=0, measure_every=20)
+        e = {}
+        for p in ("fp64", precision):
+            with Afqmc.from_system(s, precision=p) as ctx:
+                ctx.afqmc_propagate(n_steps)
+                e[p] = ctx.afqmc_energy_history()[:, 1]
+        d = (e[precision] - e["fp64"]) * 1e3
+        out[name] = {"steps": n_steps, "measurements": int(len(d)),
+                     "max_abs_mHa": round(float(np.max(np.abs(d))), 6),
+                     "mean_mHa": round(float(np.mean(d)), 6),
+                     "e_fp64_last": round(float(e["fp64"][-1]), 6)}
+    return out
 
 
 def energy_check(precision, n_steps=600):
@@ -419,18 +446,22 @@ def energy_check(precision, n_steps=600):
             "mean_mHa": round(float(np.mean(d)), 6)}
 
 
-def serving_leg(precision, n_runs=30, rate=20.0, seed=5, blocks=2, steps=50):
-    """The serving loop under a Poisson stream of independent runs (the serving
-    mix's shapes, bounded for a bench: M in 20..96, N per spin M/5..M/3,
-    n_chol 4M..6M, 128..1024 walkers, dt = 0.005, `blocks` blocks of `steps`
-    steps each). Inputs are drawn before the clock starts; submissions follow
-    the arrival times; p50/p99 are the server's own per-block latencies."""
+def serving_leg(precision, n_runs=20, rate=20.0, seed=5, blocks=10, steps=50):
+    """The serving loop under a Poisson stream of independent runs drawn from
+    the serving mix at its stated ranges: M in 20..200, N per spin M/5..M/3,
+    n_chol 4M..6M, 128..2048 walkers, dt = 0.005, `blocks` blocks of `steps`
+    steps each (energy once per block, comb every 10 steps). Inputs are
+    drawn before the clock starts; submissions follow the arrival times;
+    runs use the fixed launch heuristics (no per-request tuning); p50/p99 are
+    the server's own per-block latencies. Offered load = the submitted runs'
+    walker-steps over the arrival window; served = completed walker-steps
+    over the elapsed time."""
     import numpy as np
     from synth.systems import serving_run
     from paper_1804_03310_gb300 import Inputs, Server
     rng = np.random.default_rng(seed)
-    runs = [Inputs.from_system(serving_run(rng, k, m_range=(20, 96), w_range=(128, 1024)),
-                               precision=precision) for k in range(n_runs)]
+    systems = [serving_run(rng, k) for k in range(n_runs)]
+    runs = [Inputs.from_system(sy, precision=precision, autotune=False) for sy in systems]
     gaps = rng.exponential(1.0 / rate, size=n_runs)
     srv = Server()
     t0 = time.perf_counter()
@@ -442,6 +473,7 @@ def serving_leg(precision, n_runs=30, rate=20.0, seed=5, blocks=2, steps=50):
             time.sleep(t_arrive - now)
         ids.append(srv.afqmc_server_submit(inp, blocks, steps))
         t_arrive += gap
+    window = time.perf_counter() - t0
     srv.afqmc_server_wait(-1, 900)
     st = srv.afqmc_server_stats()
     failures = []
@@ -450,12 +482,15 @@ def serving_leg(precision, n_runs=30, rate=20.0, seed=5, blocks=2, steps=50):
         if info["state"] != "done":
             failures.append(f"run {i}: {info['state']} {info['message']}")
     srv.close()
-    return {"workload": (f"{n_runs} runs, Poisson arrivals {rate}/s, M 20..96, N/spin M/5..M/3, "
-                         f"n_chol 4M..6M, W 128..1024, {blocks} blocks of {steps} steps "
+    offered = sum(sy.n_walkers for sy in systems) * blocks * steps
+    return {"workload": (f"{n_runs} runs, Poisson arrivals {rate}/s, M 20..200, N/spin M/5..M/3, "
+                         f"n_chol 4M..6M, W 128..2048, {blocks} blocks of {steps} steps "
                          f"(comb every 10), {precision}"),
+            "m_drawn": [int(sy.M) for sy in systems],
             "completed": int(st["completed"]), "failed": int(st["failed"]),
             "p50_block_ms": round(st["p50_ms"], 3), "p99_block_ms": round(st["p99_ms"], 3),
             "walker_steps_per_s": round(st["walker_steps"] / st["elapsed_s"], 1),
+            "offered_walker_steps_per_s": round(offered / max(window, 1e-9), 1),
             "elapsed_s": round(st["elapsed_s"], 3), "max_active_seen": int(st["max_active_seen"]),
             "failures": failures[:4]}
 
@@ -482,6 +517,114 @@ def _blocks(s, precision, n_blocks):
     ks = {k: ctx.afqmc_kernel_stats(k) for k in KERNEL_IDS}
     ctx.close()
     return total / n_blocks, {k: round(v["total_ms"], 3) for k, v in ks.items() if v["launches"]}
+
+
+def islands_leg(s, precision, value):
+    """The bench workload with the small inverse and the QR in FP64
+    arithmetic (fp64_islands = 1, the spec form: FP64 only for the
+    orthonormalisation, the log-determinants and the weights) beside the
+    default FP32 arithmetic there."""
+    import torch
+    from paper_1804_03310_gb300 import Afqmc
+    stream = torch.cuda.Stream()
+    ctx = Afqmc.from_system(s, precision=precision, fp64_islands=True,
+                            stream=stream.cuda_stream)
+    ctx.afqmc_propagate(BLOCK)
+    stream.synchronize()
+    total = 0.0
+    n = 3
+    for _ in range(n):
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.afqmc_propagate(BLOCK)
+        e.record(stream)
+        e.synchronize()
+        total += a.elapsed_time(e)
+    ctx.close()
+    v = s.n_walkers * BLOCK * n / (total / 1e3)
+    return {"fp64_islands": 1, "value": round(v, 1), "unit": METRIC,
+            "ms_per_block": round(total / n, 3),
+            "ratio_to_default": round(v / value, 3)}
+
+
+def batch_leg(precision, n_blocks=4):
+    """Multi-system batching: four systems of uneven M, N, n_chol and walker
+    counts advanced by afqmc_batch_propagate (one graph launch per 20-step
+    block, every member a branch of it) against the same systems advanced
+    one after another on one stream."""
+    import torch
+    from synth import make_system
+    from paper_1804_03310_gb300 import Afqmc, Batch
+    shapes = [(24, 8, 8, 100, 512), (40, 10, 9, 180, 384), (60, 20, 20, 260, 256),
+              (90, 15, 15, 400, 256)]
+    systems = [make_system(f"batch_{k}", M=M, n_up=nu, n_dn=nd, n_chol=G, ham_seed=10 + k,
+                           l_kind="dense", l_sigma=0.05 * math.sqrt(10.0 / M), trial="eig",
+                           dtau=0.005, n_walkers=W, seed=10 + k, ortho_every=2,
+                           measure_every=BLOCK, pc_every=BLOCK, run_id=k)
+               for k, (M, nu, nd, G, W) in enumerate(shapes)]
+    ws = sum(s.n_walkers for s in systems) * BLOCK * n_blocks
+
+    def make():
+        return [Afqmc.from_system(s, precision=precision) for s in systems]
+
+    # one after another
+    ctxs = make()
+    for c in ctxs:
+        c.afqmc_propagate(BLOCK)
+        c.afqmc_synchronize()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_blocks):
+        for c in ctxs:
+            c.afqmc_propagate(BLOCK)
+    for c in ctxs:
+        c.afqmc_synchronize()
+    seq = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    # batched
+    ctxs = make()
+    b = Batch(ctxs, BLOCK)
+    b.afqmc_batch_propagate(1)
+    b.afqmc_batch_synchronize()
+    t0 = time.perf_counter()
+    b.afqmc_batch_propagate(n_blocks)
+    b.afqmc_batch_synchronize()
+    bat = time.perf_counter() - t0
+    launches = b.afqmc_batch_launches()
+    b.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "; ".join(f"M={M} N={nu}+{nd} n_chol={G} W={W}"
+                                  for (M, nu, nd, G, W) in shapes) + f", {precision}",
+            "blocks": n_blocks, "batched_value": round(ws / bat, 1),
+            "sequential_value": round(ws / seq, 1), "unit": METRIC,
+            "speedup": round(seq / bat, 3), "graph_launches": int(launches)}
+
+
+def ndet_leg(precision, ndets=(1, 10, 50, 200, 500)):
+    """Cost of the multi-determinant step against the number of
+    determinants (the shape of the paper's N_det study, Sec. III): the
+    multi-determinant workload's system with the trial truncated or extended
+    to N_det determinants, one 20-step block timed after a warm-up block."""
+    from synth import config_c4
+    out = []
+    for nd in ndets:
+        s = config_c4(n_det=nd).replace(measure_every=BLOCK, pc_every=BLOCK, ortho_every=2)
+        try:
+            ms, _ = _blocks(s, precision, 1)
+        except Exception as e:   # e.g. a trial too large for the on-chip energy kernel
+            out.append({"n_det": nd, "error": str(e)[:160]})
+            continue
+        out.append({"n_det": nd, "ms_per_block": round(ms, 3),
+                    "value": round(s.n_walkers * BLOCK / (ms / 1e3), 1)})
+    base = out[0].get("ms_per_block")
+    for r in out:
+        if base and "ms_per_block" in r:
+            r["cost_vs_1_det"] = round(r["ms_per_block"] / base, 3)
+    return {"workload": "M=80 N=10+10 n_chol=400 W=1024, " + precision, "unit": METRIC,
+            "points": out}
 
 
 def shapes_leg(precision):
@@ -527,11 +670,15 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "ms_per_imaginary_step": round(total_ms / args.steps / BLOCK, 5),
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.precision),
         "data": "synthetic (seeded Hamiltonian and trial of the workload's shape)",
         "config": {"workload": describe(s), "precision": args.precision,
-                   "step": f"{BLOCK} imaginary-time steps: ortho every 2, energy + comb at the end",
+                   "step": (f"one bench step = one block of {BLOCK} imaginary-time steps "
+                            "(ortho every 2, energy + comb at the end); ms_per_step is per "
+                            "block, ms_per_imaginary_step per imaginary-time step"),
                    "l2": "flushed (256 MB write) between timed iterations",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gpu_launches": int(launches),
@@ -550,6 +697,9 @@ def main():
         line["serving"] = serving_leg(args.precision)
     if not args.no_shapes and world == 1 and args.precision != "fp64":
         line["shapes"] = shapes_leg(args.precision)
+        line["fp64_islands"] = islands_leg(s, args.precision, value)
+        line["batch"] = batch_leg(args.precision)
+        line["ndet_sweep"] = ndet_leg(args.precision)
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,

@@ -223,9 +223,12 @@ typedef struct {
   int32_t bn_half_step;
   int32_t taylor_fused;   /* propagation path: 0 = series on the CUDA cores,
                              half steps as contractions; 1 = one fused
-                             tensor-core kernel for B_half exp_T(V) B_half;
-                             2 = series on the tensor cores, half steps as
-                             separate contractions (1 and 2 need M <= 64) */
+                             tensor-core kernel for B_half exp_T(V) B_half
+                             with the operator held on chip; 2 = series on
+                             the tensor cores, half steps as separate
+                             contractions (1 and 2 need M <= 64); 3 = one
+                             fused tensor-core kernel with the operator
+                             streamed from memory by TMA (needs M > 64) */
   int32_t reserved[2];    /* zero */
 } afqmc_tuning;
 afqmc_status afqmc_get_tuning(afqmc_ctx* ctx, afqmc_tuning* out);
@@ -375,7 +378,10 @@ void afqmc_server_destroy(afqmc_server* s);
  *            offset (stream 1), as in afqmc_population_control
  *  d_parent  [n_walkers] device, receives the parent index of each new walker
  *  d_wnew    [1] device, receives the common new weight sum(W)/n_walkers, or
- *            -1 (with d_parent the identity) when every weight is zero
+ *            -1 (with d_parent the identity) when there is nothing to comb:
+ *            every weight zero, or a NaN or infinite weight. That -1 is the
+ *            call's only report of it (the kernel's own status word stays
+ *            in the library's scratch array and is cleared by the next call)
  *  stream    cudaStream_t to run on (NULL: the legacy default stream)
  *
  * Asynchronous on `stream`; it calls no cudaMalloc, cudaFree or allocating

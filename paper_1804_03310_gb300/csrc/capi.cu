@@ -85,9 +85,14 @@ struct afqmc_ctx {
   long Jp[2];        // Yx / Z row strides per spin
   int xsplit;        // K splits of the force-bias contraction
   int xsplit_max;    // partial sums the X buffer holds
-  void* LT;          // L transposed [M*M][ldS] (tensor-core operand)
+  void* LT;          // L transposed [M*ldV][ldS] (tensor-core operand; zero rows pad each
+                     // operator row to ldV)
   void* dB;          // B_half - I (tensor-core operand)
   void* bimg;        // (B_half - I) operand image for the fused tensor-core Taylor kernel
+  long ldV;          // row stride of V: M, or M rounded up to 4 where the wide
+                     // tensor-core Taylor kernel streams V by TMA (M > 64)
+  void *Vlo;         // TF32X3, wide kernel: remainders of V (V then holds the TF32 hi parts)
+  void *dBp, *dBp_lo;  // B_half - I with rows of ldV (hi, lo) for the wide kernel
 
   // multi-determinant trial (Sherman-Morrison-Woodbury), unused for one determinant
   bool md;
@@ -105,9 +110,11 @@ struct afqmc_ctx {
   TcCtx* tc;
   bool tc_taylor_ok;  // M <= 64: on-chip tensor-core Taylor kernel
   bool tc_bhalf_ok;   // M % 4 == 0: B_half on the tensor cores
+  bool tc_wide_ok;    // M > 64: the wide tensor-core Taylor kernel (operator streamed by TMA)
   bool split3;
   int taylor_fused;   // 0: CUDA-core series; 1: fused tensor-core kernel with the
-                      // half steps; 2: tensor-core series, half steps as GEMMs
+                      // half steps; 2: tensor-core series, half steps as GEMMs;
+                      // 3: wide tensor-core kernel with the half steps (M > 64)
   int bn_fb, bn_v, bn_e, bn_b;   // tensor-core tile widths per contraction
 
   // CUDA graphs of blocks of steps, keyed by (phase in the cadence period, length)
@@ -384,6 +391,12 @@ template <typename T>
 afqmc_status propagate_T(afqmc_ctx* c, T* out) {
   const int W = c->W, N = c->N, M = c->M;
   const int rows = W * N * 2;
+  if (c->tc && c->taylor_fused == 3) {   // operator streamed by TMA, half steps fused
+    LK(tc_taylor_wide(c->tc, c->st, W, M, N, c->p.taylor_order, c->ldV, (const float*)c->V,
+                      (const float*)c->Vlo, (const float*)c->dBp, (const float*)c->dBp_lo,
+                      (const float*)c->Phi, (float*)out, c->split3, c->status));
+    return AFQMC_OK;
+  }
   if (c->tc && c->taylor_fused == 1) {   // B_half exp(V) B_half in one tensor-core kernel, in place
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
                  (const float*)c->Phi, (float*)out, (const float*)c->bimg, c->split3,
@@ -409,8 +422,8 @@ afqmc_status propagate_T(afqmc_ctx* c, T* out) {
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
                  (const float*)c->Phi2, (float*)c->Phi3, nullptr, c->split3, c->status));
   } else {
-    LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V, (const T*)c->Phi2,
-                        (T*)c->Phi3));
+    LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V, c->ldV,
+                        (const T*)c->Phi2, (T*)c->Phi3));
   }
   // out = B_half Phi3
   if (c->tc && c->tc_bhalf_ok) {
@@ -444,9 +457,11 @@ afqmc_status step_T(afqmc_ctx* c) {
   {
     KTimer t(c, 2);
     if (c->tc) {
-      LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
-                 (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
-                 nullptr, 0, c->split3, 1, 0, c->status, c->bn_v, (const float*)c->LT_lo));
+      const long nv = (long)M * c->ldV;
+      LK(tc_gemm(c->tc, c->st, 2 * W, (int)nv, G, (const float*)c->S, c->ldS,
+                 (const float*)c->LT, c->ldS, (float*)c->V, nv, 1.0f, 0.0f, nullptr, 0,
+                 c->split3, 1, 0, c->status, c->bn_v, (const float*)c->LT_lo,
+                 c->taylor_fused == 3 && c->split3 ? (float*)c->Vlo : nullptr));
     } else {
       LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, c->ldS, 0,
                  (const T*)c->L, (long)M * M, 0, T(0), (T*)c->V, (long)M * M, 0, 1));
@@ -667,12 +682,13 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   LK(launch_pad_rows(st, G + 1, (long)c->nu * M, (long)c->nd * M, Ltil, Ltil_pad, c->ldt,
                      c->dn_off));
   LK(launch_convert<T>(st, (long)(G + 1) * c->ldt, Ltil_pad, (T*)c->Ltil));
-  if (c->LT) {   // L transposed [M*M][ldS] for the tensor cores
+  if (c->LT) {   // L transposed [M*ldV][ldS] for the tensor cores
     double *lt;
-    TM(lt, MM * c->ldS);
-    CK(cudaMemsetAsync(lt, 0, MM * c->ldS * sizeof(double), st));
-    LK(launch_transpose(st, G, (long)MM, L, lt, c->ldS));
-    LK(launch_convert<T>(st, (long)MM * c->ldS, lt, (T*)c->LT));
+    const long nv = (long)M * c->ldV;
+    TM(lt, nv * c->ldS);
+    CK(cudaMemsetAsync(lt, 0, nv * c->ldS * sizeof(double), st));
+    LK(launch_transpose_pad(st, G, M, c->ldV, L, lt, c->ldS));
+    LK(launch_convert<T>(st, nv * c->ldS, lt, (T*)c->LT));
   }
   if (c->dB) {   // B_half - I: the reduced modes add the identity part exactly
     CK(cudaMemcpyAsync(tb, Bh, MM * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -680,10 +696,19 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     LK(launch_convert<T>(st, MM, tb, (T*)c->dB));
     if (c->bimg)
       LK(tc_bhalf_image(st, M, (const float*)c->dB, (float*)c->bimg, c->split3));
+    if (c->dBp) {   // rows padded to ldV (TMA), then split for TF32X3
+      double* pad;
+      TM(pad, (size_t)M * c->ldV);
+      CK(cudaMemsetAsync(pad, 0, (size_t)M * c->ldV * sizeof(double), st));
+      LK(launch_pad_rows(st, M, M, 0, tb, pad, c->ldV, c->ldV));
+      LK(launch_convert<T>(st, (long)M * c->ldV, pad, (T*)c->dBp));
+      if (c->dBp_lo)
+        LK(tc_split(st, (long)M * c->ldV, (float*)c->dBp, (float*)c->dBp_lo));
+    }
   }
   if (c->split3) {   // the constant operands of the TF32X3 contractions, split once
     LK(tc_split(st, (long)(G + 1) * c->ldt, (float*)c->Ltil, (float*)c->Ltil_lo));
-    LK(tc_split(st, (long)MM * c->ldS, (float*)c->LT, (float*)c->LT_lo));
+    LK(tc_split(st, (long)M * c->ldV * c->ldS, (float*)c->LT, (float*)c->LT_lo));
     LK(tc_split(st, (long)c->nu * M * c->Jp[0], (float*)c->Yx_up, (float*)c->Yx_up_lo));
     LK(tc_split(st, (long)c->nd * M * c->Jp[1], (float*)c->Yx_dn, (float*)c->Yx_dn_lo));
   }
@@ -904,9 +929,11 @@ afqmc_status autotune(afqmc_ctx* c) {
     float best = INFINITY;
     for (int bn : bns) {
       const float ms = best_ms(c, [&]() -> afqmc_status {
-        LK(tc_gemm(c->tc, c->st, 2 * W, M * M, G, (const float*)c->S, c->ldS,
-                   (const float*)c->LT, c->ldS, (float*)c->V, (long)M * M, 1.0f, 0.0f,
-                   nullptr, 0, c->split3, 1, 0, c->status, bn, (const float*)c->LT_lo));
+        const long nv = (long)M * c->ldV;
+        LK(tc_gemm(c->tc, c->st, 2 * W, (int)nv, G, (const float*)c->S, c->ldS,
+                   (const float*)c->LT, c->ldS, (float*)c->V, nv, 1.0f, 0.0f, nullptr, 0,
+                   c->split3, 1, 0, c->status, bn, (const float*)c->LT_lo,
+                   c->tc_wide_ok && c->split3 ? (float*)c->Vlo : nullptr));
         return AFQMC_OK;
       });
       if (ms < best) { best = ms; v.bn_v = bn; }
@@ -937,14 +964,16 @@ afqmc_status autotune(afqmc_ctx* c) {
   // propagation path (into the spare walker buffer Phi2)
   {
     float best = INFINITY;
-    for (int fused = c->tc_taylor_ok ? 2 : 0; fused >= 0; --fused) {
+    for (int fused = c->tc_wide_ok ? 3 : (c->tc_taylor_ok ? 2 : 0); fused >= 0; --fused) {
+      if (fused == 3 && !c->tc_wide_ok) continue;
+      if ((fused == 1 || fused == 2) && !c->tc_taylor_ok) continue;
       c->taylor_fused = fused;
       for (int bn : bns) {
-        if (fused == 1 && bn != bns[0]) continue;   // no half-step contraction
+        if ((fused == 1 || fused == 3) && bn != bns[0]) continue;   // no half-step contraction
         if (fused != 1 && (!c->tc_bhalf_ok || M <= 64) && bn != bns[0]) continue;
         c->bn_b = bn;
         const float ms = best_ms(c, [&]() { return propagate_T<float>(c, (float*)c->Phi2); });
-        if (ms < best) { best = ms; v.fused = fused; v.bn_b = fused == 1 ? 0 : bn; }
+        if (ms < best) { best = ms; v.fused = fused; v.bn_b = (fused == 1 || fused == 3) ? 0 : bn; }
       }
     }
   }
@@ -1046,9 +1075,9 @@ void advance_host(afqmc_ctx* c, long len, const GraphEntry* ge) {
 // active-orbital counts of a multi-determinant trial).
 struct Plan {
   int M, nu, nd, N, G, W, ndet, nact[2];
-  bool fp64, tcmode, split3, md, tc_taylor_ok, tc_bhalf_ok;
+  bool fp64, tcmode, split3, md, tc_taylor_ok, tc_bhalf_ok, tc_wide_ok;
   size_t es;
-  long ldS, ldx, dn_off, ldt, Jp[2], gdn_off, ldg;
+  long ldS, ldx, dn_off, ldt, Jp[2], gdn_off, ldg, ldV;
   int xsplit, xsplit_max;
 };
 
@@ -1064,6 +1093,8 @@ Plan make_plan(const afqmc_params* p, int nact_up, int nact_dn) {
   P.split3 = p->precision == AFQMC_TF32X3;
   P.tc_taylor_ok = P.tcmode && P.M <= 64;
   P.tc_bhalf_ok = P.tcmode && P.M % 4 == 0;
+  P.tc_wide_ok = P.tcmode && P.M > 64;
+  P.ldV = P.tc_wide_ok ? round4(P.M) : P.M;
   P.es = P.fp64 ? sizeof(double) : sizeof(float);
   const int M = P.M, G = P.G, W = P.W;
   P.ldS = round4(G);
@@ -1121,7 +1152,7 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->Phi3, phi * es);
   add(&c->Theta, W * 2 * P.ldt * es);
   add(&c->Theta2, W * 2 * P.ldt * es);
-  add(&c->V, W * 2 * MM * es);
+  add(&c->V, W * 2 * M * P.ldV * es);
   add(&c->X, (size_t)P.xsplit_max * W * 2 * P.ldx * es);
   add(&c->S, W * 2 * P.ldS * es);
   add(&c->xbar, W * 2 * G * es);
@@ -1133,15 +1164,22 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->PsiT64, N * M * sizeof(double));
   add(&c->Yx_up, (size_t)P.nu * M * P.Jp[0] * es);
   add(&c->Yx_dn, (size_t)P.nd * M * P.Jp[1] * es);
-  if (P.tcmode) add(&c->LT, MM * P.ldS * es);
+  if (P.tcmode) add(&c->LT, M * P.ldV * P.ldS * es);
   if (P.split3) {
     add(&c->Ltil_lo, (G + 1) * P.ldt * es);
-    add(&c->LT_lo, MM * P.ldS * es);
+    add(&c->LT_lo, M * P.ldV * P.ldS * es);
     add(&c->Yx_up_lo, (size_t)P.nu * M * P.Jp[0] * es);
     add(&c->Yx_dn_lo, (size_t)P.nd * M * P.Jp[1] * es);
   }
   if (!P.fp64) add(&c->dB, MM * es);
   if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_floats(P.split3) * sizeof(float));
+  if (P.tc_wide_ok) {
+    add(&c->dBp, M * P.ldV * es);
+    if (P.split3) {
+      add(&c->dBp_lo, M * P.ldV * es);
+      add(&c->Vlo, W * 2 * M * P.ldV * es);
+    }
+  }
   add(&c->weight, W * sizeof(double));
   add(&c->scan, W * sizeof(double));
   add(&c->lr, 2 * W * sizeof(double));
@@ -1176,7 +1214,8 @@ size_t setup_bytes(const Plan& P) {
     add(J * J);
     add(J * J);
   }
-  if (P.tcmode) add(MM * P.ldS);
+  if (P.tcmode) add(M * P.ldV * P.ldS);
+  if (P.tc_wide_ok) add(M * P.ldV);
   if (P.md) add((G + 1) * P.ldg);
   return n;
 }
@@ -1225,7 +1264,9 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   c->split3 = P.split3;
   c->tc_taylor_ok = P.tc_taylor_ok;
   c->tc_bhalf_ok = P.tc_bhalf_ok;
-  c->taylor_fused = P.tc_taylor_ok ? 1 : 0;
+  c->tc_wide_ok = P.tc_wide_ok;
+  c->ldV = P.ldV;
+  c->taylor_fused = P.tc_taylor_ok ? 1 : (P.tc_wide_ok ? 3 : 0);
   c->bn_fb = c->bn_v = c->bn_e = c->bn_b = 0;
   if (c->md) {
     const bool f64c = c->fp64_islands;
@@ -1284,7 +1325,8 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   CK(cudaMemsetAsync(c->lw, 0, W * sizeof(double2), c->st));
   CK(cudaMemsetAsync(c->xbar, 0, (size_t)W * 2 * G * es, c->st));
   CK(cudaMemsetAsync(c->S, 0, (size_t)W * 2 * c->ldS * es, c->st));
-  CK(cudaMemsetAsync(c->V, 0, (size_t)W * 2 * M * M * es, c->st));
+  CK(cudaMemsetAsync(c->V, 0, (size_t)W * 2 * M * c->ldV * es, c->st));
+  if (c->Vlo) CK(cudaMemsetAsync(c->Vlo, 0, (size_t)W * 2 * M * c->ldV * es, c->st));
   CK(cudaMemsetAsync(c->Theta, 0, (size_t)W * 2 * c->ldt * es, c->st));
   CK(cudaMemsetAsync(c->Theta2, 0, (size_t)W * 2 * c->ldt * es, c->st));
   CK(cudaMemsetAsync(c->X, 0, (size_t)c->xsplit_max * W * 2 * c->ldx * es, c->st));
@@ -1729,10 +1771,12 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* c, const afqmc_tuning* t) {
   if (!bn_ok(t->bn_force_bias) || !bn_ok(t->bn_one_body) || !bn_ok(t->bn_energy) ||
       !bn_ok(t->bn_half_step))
     return fail(c, AFQMC_E_INVALID, "tile widths must be 64 or 128");
-  if (t->taylor_fused < 0 || t->taylor_fused > 2)
-    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0, 1 or 2");
-  if (t->taylor_fused && !c->tc_taylor_ok)
-    return fail(c, AFQMC_E_INVALID, "the tensor-core Taylor kernel needs M <= 64");
+  if (t->taylor_fused < 0 || t->taylor_fused > 3)
+    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0, 1, 2 or 3");
+  if ((t->taylor_fused == 1 || t->taylor_fused == 2) && !c->tc_taylor_ok)
+    return fail(c, AFQMC_E_INVALID, "the on-chip tensor-core Taylor kernel needs M <= 64");
+  if (t->taylor_fused == 3 && !c->tc_wide_ok)
+    return fail(c, AFQMC_E_INVALID, "the streamed tensor-core Taylor kernel needs M > 64");
   CK(cudaStreamSynchronize(c->st));
   drop_graphs(c);
   apply_tune(c, TuneVal{t->xsplit, t->bn_force_bias, t->bn_one_body, t->bn_energy,

@@ -8,7 +8,8 @@
 //                         row holds the up block (n_up*M, column a at a*M)
 //                         at 0 and the down block at dn_off, both 16-byte
 //                         aligned, zeros in the padding
-//   V      [W][2][M][M]   one-body operator per walker (complex symmetric)
+//   V      [W][2][M][ldV] one-body operator per walker (complex symmetric),
+//                         rows padded to ldV >= M
 //   X      [nsplit][W][2][ldx]  force-bias contraction partial sums, ldx =
 //                         n_chol + 1 (last column: tr(h~ Theta))
 //   S      [W][2][ldS]    i sqrt(dt) (x - xbar) per walker, ldS = n_chol
@@ -19,6 +20,13 @@
 #include <stdint.h>
 
 namespace afqmc {
+
+// Opt a kernel in to the largest dynamic shared memory the current device
+// allows beside the kernel's static shared memory, and return that limit in
+// bytes. The attribute belongs to the device, so the opt-in runs once per
+// (kernel, device) pair and is cached; query errors are cleared so they
+// cannot surface at a later launch check.
+size_t smem_optin(const void* kernel);
 
 template <typename T>
 cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, T alpha,
@@ -39,10 +47,11 @@ cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long l
                           uint64_t seed, int run_id, const long long* ctr, T* S, long ldS,
                           T* xbar, double2* lw);
 
-// K5 on the CUDA cores: Phi_out = sum_{n<=order} V^n Phi_in / n!.
+// K5 on the CUDA cores: Phi_out = sum_{n<=order} V^n Phi_in / n!, with V
+// [W][2][M][ldv].
 template <typename T>
 cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
-                          const T* V, const T* Phi_in, T* Phi_out);
+                          const T* V, long ldv, const T* Phi_in, T* Phi_out);
 
 // K6: A = D^H Phi per spin, inverse by elimination with partial pivoting
 // (FP64 arithmetic when fp64_compute, else FP32), ln det A accumulated in
@@ -123,6 +132,10 @@ cudaError_t launch_pad_rows(cudaStream_t st, long rows, long Jup, long Jdn,
                             const double* in, double* out, long ld, long dn_off);
 cudaError_t launch_transpose(cudaStream_t st, long rows, long cols, const double* in,
                              double* out, long ldo);
+// L [G][M*M] -> out [M*ldv][ldo], out[i ldv + k][g] = L[g][i M + k] (other
+// rows untouched).
+cudaError_t launch_transpose_pad(cudaStream_t st, long G, int M, long ldv, const double* in,
+                                 double* out, long ldo);
 template <typename T>
 cudaError_t launch_convert(cudaStream_t st, long n, const double* in, T* out);
 template <typename T>

@@ -14,6 +14,7 @@
 // The local energy is not linear in the Theta_i and is summed determinant by
 // determinant.
 #include "common.cuh"
+#include "kernels.h"
 #include "multidet.h"
 
 namespace afqmc {
@@ -700,20 +701,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) md_energy_hoisted
   if (tid == 0) eloc[w] = make_double2(sr, si);
 }
 
-template <typename K>
-size_t smem_opt_in(K kernel) {
-  int dev = 0, optin = 48 * 1024;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  size_t stat = 0;
-  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
-  const size_t dyn = (size_t)optin > stat ? (size_t)optin - stat : 0;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  cudaGetLastError();
-  return dyn;
-}
-
 }  // namespace
 
 size_t md_step_smem(int M, int nu, int nd, int na_u, int na_d, int ndet, bool f64) {
@@ -736,13 +723,13 @@ cudaError_t launch_md_step_r(cudaStream_t st, const MdTables& tb, int W, int M, 
   const bool f64 = sizeof(R) == 8;
   const size_t smem = md_step_smem(M, nu, nd, tb.nact[0], tb.nact[1], tb.ndet, f64);
   const size_t smem_h = smem + md_ctab_bytes(tb.ctot, tb.ndet, sizeof(cplx<R>));
-  static const size_t cap_h = smem_opt_in(md_step_kernel<T, R, true>);
+  const size_t cap_h = smem_optin((const void*)md_step_kernel<T, R, true>);
   if (smem_h <= cap_h) {
     md_step_kernel<T, R, true><<<W, 256, smem_h, st>>>(tb, M, nu, nd, Theta, ldt, dn_off,
                                                        logdet0, logO_new, Gamma, ldg, gdn_off);
     return cudaGetLastError();
   }
-  static const size_t cap = smem_opt_in(md_step_kernel<T, R, false>);
+  const size_t cap = smem_optin((const void*)md_step_kernel<T, R, false>);
   if (smem > cap) return cudaErrorInvalidValue;
   md_step_kernel<T, R, false><<<W, 256, smem, st>>>(tb, M, nu, nd, Theta, ldt, dn_off, logdet0,
                                                     logO_new, Gamma, ldg, gdn_off);
@@ -770,14 +757,14 @@ cudaError_t launch_md_energy(cudaStream_t st, const MdTables& tb, int W, int M, 
   const size_t smem_h = smem + md_ctab_bytes(tb.ctot, tb.ndet, f64 ? 16 : 8) +
                         sizeof(MdDet) * (size_t)tb.ndet;
   if (f64) {
-    static const size_t cap_h = smem_opt_in(md_energy_hoisted_kernel<T, double>);
+    const size_t cap_h = smem_optin((const void*)md_energy_hoisted_kernel<T, double>);
     if (smem_h <= cap_h) {
       md_energy_hoisted_kernel<T, double><<<W, threads, smem_h, st>>>(
           tb, M, nu, nd, G, Theta, ldt, dn_off, logdet0, LtilA, ldg, gdn_off, eloc);
       return cudaGetLastError();
     }
   } else {
-    static const size_t cap_h = smem_opt_in(md_energy_hoisted_kernel<T, float>);
+    const size_t cap_h = smem_optin((const void*)md_energy_hoisted_kernel<T, float>);
     if (smem_h <= cap_h) {
       md_energy_hoisted_kernel<T, float><<<W, threads, smem_h, st>>>(
           tb, M, nu, nd, G, Theta, ldt, dn_off, logdet0, LtilA, ldg, gdn_off, eloc);
@@ -786,12 +773,12 @@ cudaError_t launch_md_energy(cudaStream_t st, const MdTables& tb, int W, int M, 
   }
   if ((tb.ndet + threads - 1) / threads > MD_MAX_DET_PER_THREAD) return cudaErrorInvalidValue;
   if (f64) {
-    static const size_t cap = smem_opt_in(md_energy_kernel<T, double>);
+    const size_t cap = smem_optin((const void*)md_energy_kernel<T, double>);
     if (smem > cap) return cudaErrorInvalidValue;
     md_energy_kernel<T, double><<<W, threads, smem, st>>>(tb, M, nu, nd, G, Theta, ldt, dn_off,
                                                           logdet0, LtilA, ldg, gdn_off, eloc);
   } else {
-    static const size_t cap = smem_opt_in(md_energy_kernel<T, float>);
+    const size_t cap = smem_optin((const void*)md_energy_kernel<T, float>);
     if (smem > cap) return cudaErrorInvalidValue;
     md_energy_kernel<T, float><<<W, threads, smem, st>>>(tb, M, nu, nd, G, Theta, ldt, dn_off,
                                                          logdet0, LtilA, ldg, gdn_off, eloc);

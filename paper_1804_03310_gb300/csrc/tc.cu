@@ -12,10 +12,15 @@
 //    t_n = V t_{n-1} / n fed back from TMEM into shared memory.
 //
 // TF32X3 mode splits each operand x into hi = x rounded to TF32 and
-// lo = x - hi (exact), and accumulates hi.hi + hi.lo + lo.hi.
+// lo = (x - hi) rounded to TF32, and accumulates hi.hi + hi.lo + lo.hi. The
+// remainder is rounded explicitly: fed to the tensor core unrounded, its low
+// bits would be truncated, an error of up to 2^-21 |x| of one sign that
+// accumulates coherently over long contractions; rounded, x - hi - lo is at
+// most 2^-22 |x| and unbiased.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "kernels.h"
 #include "tc.h"
 #include "umma.cuh"
 
@@ -40,6 +45,8 @@ __device__ __forceinline__ float tf32_hi(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
+// The second term of the split: (x - hi) rounded to TF32.
+__device__ __forceinline__ float tf32_lo(float x, float hi) { return tf32_hi(x - hi); }
 
 __device__ __forceinline__ void flag_timeout(int* status) {
   if (status) atomicOr(status, 4);
@@ -83,7 +90,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                const __grid_constant__ CUtensorMap mapBlo, int m, int n, GemmWork wk,
                float* __restrict__ C, long ldc, float alpha,
                float beta, const float* __restrict__ R, long ldr, long split_stride,
-               int* status) {
+               int* status, float* __restrict__ Clo) {
   using Cfg = GemmCfg<BN, SPLIT3>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -147,11 +154,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             tma_load_2d(smem_u32(b_lo(s)), &mapBlo, (kt0 + k) * BK, n0, smem_u32(&full[s]));
         }
       }
+      // no copy may outlive the CTA: the latest load into each stage has
+      // landed before teardown (on the normal path these have long completed)
+      for (int j = it - 1; j >= 0 && j >= it - S; --j)
+        if (!mbar_wait(smem_u32(&full[j % S]), (uint32_t)(j / S) & 1u)) flag_timeout(status);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t id = idesc_tf32(BM, BN);
       int it = 0, j = 0;
+      uint32_t last_bar = 0, last_par = 0;   // the latest commit, for the drain
       for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x, ++j) {
         int m0, tn, z, kt0, nkt;
         wk.item(i, m0, tn, z, kt0, nkt);
@@ -184,9 +196,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             }
           }
           mma_commit(smem_u32(&empty[s]));
+          last_bar = smem_u32(&empty[s]);
+          last_par = ph;
         }
         mma_commit(smem_u32(&tfull[acc]));
+        last_bar = smem_u32(&tfull[acc]);
+        last_par = aph;
       }
+      // no MMA may outlive the TMEM allocation: a commit arrives once every
+      // earlier MMA of this thread has completed
+      if (last_bar && !mbar_wait(last_bar, last_par)) flag_timeout(status);
     }
   } else if (warp < 6) {
     // epilogue: TMEM lane quadrant q = warp % 4 holds rows 32q .. 32q + 31
@@ -207,6 +226,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       fence_after_sync();
       const int row = m0 + 32 * q + lane;
       float* crow = C + (long)z * split_stride + (long)row * ldc;
+      float* lrow = Clo ? Clo + (long)row * ldc : nullptr;
       const float* rrow = R ? R + (long)row * ldr : nullptr;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -220,6 +240,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
           const int cb = n0 + c0;
           if (cb + 32 <= n && (ldc & 3) == 0 && (!rrow || (ldr & 3) == 0) &&
               ((uintptr_t)(crow + cb) & 15) == 0 &&
+              (!lrow || ((uintptr_t)(lrow + cb) & 15) == 0) &&
               (!rrow || ((uintptr_t)(rrow + cb) & 15) == 0)) {
 #pragma unroll
             for (int jj = 0; jj < 32; jj += 4) {
@@ -230,6 +251,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                 float4 r = *(const float4*)(rrow + cb + jj);
                 o.x += beta * r.x; o.y += beta * r.y; o.z += beta * r.z; o.w += beta * r.w;
               }
+              if (lrow) {   // split output: TF32 hi part here, the remainder in Clo
+                float4 h;
+                h.x = tf32_hi(o.x); h.y = tf32_hi(o.y); h.z = tf32_hi(o.z); h.w = tf32_hi(o.w);
+                float4 l;
+                l.x = tf32_lo(o.x, h.x); l.y = tf32_lo(o.y, h.y); l.z = tf32_lo(o.z, h.z); l.w = tf32_lo(o.w, h.w);
+                *(float4*)(lrow + cb + jj) = l;
+                o = h;
+              }
               *(float4*)(crow + cb + jj) = o;
             }
           } else {
@@ -238,6 +267,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
               if (col < n) {
                 float o = alpha * v[jj];
                 if (rrow) o += beta * rrow[col];
+                if (lrow) {
+                  const float h = tf32_hi(o);
+                  lrow[col] = tf32_lo(o, h);
+                  o = h;
+                }
                 crow[col] = o;
               }
             }
@@ -268,7 +302,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
         for (int e = t; e < Cfg::A_BYTES / 16; e += 128) {
           float4 x = ah[e], h, l;
           h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
-          l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+          l.x = tf32_lo(x.x, h.x); l.y = tf32_lo(x.y, h.y); l.z = tf32_lo(x.z, h.z); l.w = tf32_lo(x.w, h.w);
           ah[e] = h;
           al[e] = l;
         }
@@ -278,7 +312,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
           for (int e = t; e < Cfg::B_BYTES / 16; e += 128) {
             float4 x = bh[e], h, l;
             h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
-            l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+            l.x = tf32_lo(x.x, h.x); l.y = tf32_lo(x.y, h.y); l.z = tf32_lo(x.z, h.z); l.w = tf32_lo(x.w, h.w);
             bh[e] = h;
             bl[e] = l;
           }
@@ -335,7 +369,7 @@ __global__ void bhalf_image_kernel(int M, const float* __restrict__ dB, float* _
   if (split3) {
     const float h = tf32_hi(x);
     img[off] = h;
-    img[128 * 128 + off] = x - h;
+    img[128 * 128 + off] = tf32_lo(x, h);
   } else {
     img[off] = x;
   }
@@ -347,7 +381,7 @@ __device__ __forceinline__ void put_operand(unsigned char* hi, unsigned char* lo
   if (SPLIT3) {
     const float h = tf32_hi(x);
     *(float*)(hi + off) = h;
-    *(float*)(lo + off) = x - h;
+    *(float*)(lo + off) = tf32_lo(x, h);
   } else {
     *(float*)(hi + off) = x;
   }
@@ -549,7 +583,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
             h[u] = tf32_hi(sgn * x[u]);
-            l[u] = sgn * x[u] - h[u];
+            l[u] = tf32_lo(sgn * x[u], h[u]);
           }
           tmem_st16(tAhi + lane_base + (uint32_t)c0, h);
           tmem_st16(tAlo + lane_base + (uint32_t)c0, l);
@@ -622,11 +656,298 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ------------------------------------------------------------ wide Taylor
+// B_half exp_T(V) B_half Phi for 64 < M <= 256 (Sec. II, Thouless propagation
+// by matrix products), where the operator no longer fits on chip: each CTA
+// takes one (walker, column chunk) item at a time and runs it through
+// R = order + 2 rounds of products D = A t, A streamed from L2 by TMA in
+// 128-row x 32-K tiles and t (the current term) resident in shared memory as
+// the B operand:
+//   round 0          A = B_half - I (real):   t0 = Phi + D
+//   rounds 1..order  A = V (complex):         t_n = D / n, s += t_n
+//   round order + 1  A = B_half - I:          out = s + D
+// The complex product uses two accumulators per 128-row tile,
+// P = Vr [tr | ti] and Q = Vi [tr | ti] (B rows: the chunk's real parts, then
+// its imaginary parts), combined in the epilogue as Dr = Pr - Qi,
+// Di = Pi + Qr. Rows and K indices past M are zero-filled by the TMA.
+// TF32X3: A arrives pre-split (hi and lo planes in global memory); the
+// epilogue writes t as hi and lo planes; three products per MMA step.
+// Warps: 0 TMA producer, 1 MMA issuer, 2..9 epilogue (TMEM lane quadrant =
+// warp % 4; group (warp - 2) / 4 takes the second row tile, or the second
+// half of the columns when there is one row tile).
+constexpr int TW_THREADS = 320;
+constexpr int TW_TILE_BYTES = 128 * 32 * 4;   // one 128 x 32 fp32 operand tile
+
+template <bool SPLIT3>
+__global__ void __launch_bounds__(TW_THREADS, 1)
+tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
+                      const __grid_constant__ CUtensorMap mapVlo,
+                      const __grid_constant__ CUtensorMap mapB,
+                      const __grid_constant__ CUtensorMap mapBlo, int W, int M, int N,
+                      int order, int n16, int S, const float* Pin, float* Pout, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int MT = (M + 127) / 128, KB = (M + 31) / 32;
+  const int P = SPLIT3 ? 2 : 1;
+  const int kb_bytes = 2 * n16 * 128;                 // one K block of B
+  const int b_bytes = KB * kb_bytes;
+  unsigned char* Bhi = base;
+  unsigned char* Blo = base + b_bytes;                // TF32X3 only
+  unsigned char* stages = base + b_bytes * P;
+  const int stage_bytes = TW_TILE_BYTES * P;
+  uint64_t* bars = (uint64_t*)(stages + S * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* bready = bars + 2 * S;   // t for the next round is in shared memory
+  uint64_t* aready = bars + 2 * S + 1;   // the round's accumulators are complete
+  uint32_t* tslot = (uint32_t*)(bars + 2 * S + 2);
+  __shared__ int s_fail;
+  volatile int* fail = &s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunk = (N + n16 - 1) / n16;
+  const int items = W * nchunk;
+  const int R = order + 2;
+  int cols = 32;
+  while (cols < MT * 4 * n16) cols *= 2;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(bready), 8);
+    mbar_init(smem_u32(aready), 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tslot), (uint32_t)cols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  // accumulator (row tile mt, plane p) starts at column (2 mt + p) * 2 n16
+  auto acc_col = [&](int mt, int p) { return (uint32_t)((2 * mt + p) * 2 * n16); };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int item = blockIdx.x; item < items && !*fail; item += gridDim.x) {
+        const int w = item / nchunk;
+        for (int r = 0; r < R && !*fail; ++r) {
+          const bool half = (r == 0 || r == R - 1);
+          const int planes = half ? 1 : 2;
+          for (int mt = 0; mt < MT && !*fail; ++mt)
+            for (int kb = 0; kb < KB && !*fail; ++kb)
+              for (int pl = 0; pl < planes; ++pl, ++it) {
+                const int s = it % S;
+                const uint32_t ph = (uint32_t)(it / S) & 1u;
+                if (it >= S && !mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
+                  flag_timeout(status);
+                  *fail = 1;
+                  break;
+                }
+                unsigned char* st = stages + s * stage_bytes;
+                mbar_arrive_expect_tx(smem_u32(&full[s]), (uint32_t)stage_bytes);
+                const int z = half ? 0 : 2 * w + pl;
+                tma_load_3d(smem_u32(st), half ? (const void*)&mapB : (const void*)&mapV,
+                            kb * 32, mt * 128, z, smem_u32(&full[s]));
+                if (SPLIT3)
+                  tma_load_3d(smem_u32(st + TW_TILE_BYTES),
+                              half ? (const void*)&mapBlo : (const void*)&mapVlo, kb * 32,
+                              mt * 128, z, smem_u32(&full[s]));
+              }
+        }
+      }
+      // no copy may outlive the CTA
+      for (int j = it - 1; j >= 0 && j >= it - S; --j)
+        if (!mbar_wait(smem_u32(&full[j % S]), (uint32_t)(j / S) & 1u)) flag_timeout(status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc_tf32(128, 2 * n16);
+      const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+      int it = 0;
+      uint32_t pb = 0, pa = 0;
+      uint32_t last_bar = 0, last_par = 0;
+      for (int item = blockIdx.x; item < items && !*fail; item += gridDim.x) {
+        for (int r = 0; r < R && !*fail; ++r) {
+          if (!mbar_wait(smem_u32(bready), pb)) {
+            flag_timeout(status);
+            *fail = 1;
+            break;
+          }
+          pb ^= 1u;
+          fence_after_sync();
+          const bool half = (r == 0 || r == R - 1);
+          const int planes = half ? 1 : 2;
+          for (int mt = 0; mt < MT && !*fail; ++mt)
+            for (int kb = 0; kb < KB && !*fail; ++kb)
+              for (int pl = 0; pl < planes; ++pl, ++it) {
+                const int s = it % S;
+                const uint32_t ph = (uint32_t)(it / S) & 1u;
+                if (!mbar_wait(smem_u32(&full[s]), ph)) {
+                  flag_timeout(status);
+                  *fail = 1;
+                  break;
+                }
+                fence_after_sync();
+                const uint32_t sa = smem_u32(stages + s * stage_bytes);
+                const uint32_t td = tmem + acc_col(mt, pl);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                  const uint64_t ad = desc_sw128(sa + ks * 32);
+                  const uint64_t bd = desc_sw128(sBhi + kb * kb_bytes + ks * 32);
+                  mma_tf32(td, ad, bd, id, (kb > 0 || ks > 0) ? 1u : 0u);
+                  if (SPLIT3) {
+                    mma_tf32(td, ad, desc_sw128(sBlo + kb * kb_bytes + ks * 32), id, 1u);
+                    mma_tf32(td, desc_sw128(sa + TW_TILE_BYTES + ks * 32), bd, id, 1u);
+                  }
+                }
+                mma_commit(smem_u32(&empty[s]));
+                last_bar = smem_u32(&empty[s]);
+                last_par = ph;
+              }
+          if (*fail) break;
+          mma_commit(smem_u32(aready));
+          last_bar = smem_u32(aready);
+          last_par = pa;
+          pa ^= 1u;
+        }
+      }
+      if (last_bar && !mbar_wait(last_bar, last_par)) flag_timeout(status);
+    }
+  } else {
+    // epilogue: rows 32 q + lane of row tile mt, columns [c0, c0 + cp)
+    const int g = (warp - 2) >> 2, q = warp & 3;
+    const int mt = MT == 2 ? g : 0;
+    const int cp = MT == 2 ? n16 : n16 / 2;
+    const int c0 = MT == 2 ? 0 : g * cp;
+    const int i = mt * 128 + 32 * q + lane;             // orbital row (= K index of B)
+    const bool in_b = i < KB * 32;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+    uint32_t pa = 0;
+    float sr[32], si[32];
+    // t into the B operand: real part of column c at B row c, imaginary at
+    // B row n16 + c, K index i. Columns go in groups of 8 rows (one swizzle
+    // atom): within a group, row u's offset is offu[u]; groups are 1024
+    // bytes apart, and K block i / 32 sits at kb * 2 n16 * 128.
+    uint32_t offu[8];
+    {
+      const int kk = i & 31;
+      const uint32_t base_i = (uint32_t)((i >> 5) * 2 * n16 * 128 + (kk & 3) * 4);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        offu[u] = base_i + (uint32_t)(u * 128) + (uint32_t)((((kk >> 2) ^ u) & 7) << 4);
+    }
+    const uint32_t im_off = (uint32_t)(n16 >> 3) * 1024u;
+    const uint32_t sBh = smem_u32(Bhi), sBl = smem_u32(Blo);
+    // group gi (columns 8 gi .. 8 gi + 7), member u
+    auto put_b = [&](int gi, int u, float xr, float xi) {
+      if (!in_b) return;
+      const uint32_t o_r = (uint32_t)gi * 1024u + offu[u], o_i = o_r + im_off;
+      if (SPLIT3) {
+        const float hr = tf32_hi(xr), hi_ = tf32_hi(xi);
+        st_shared_f32(sBh + o_r, hr);
+        st_shared_f32(sBl + o_r, tf32_lo(xr, hr));
+        st_shared_f32(sBh + o_i, hi_);
+        st_shared_f32(sBl + o_i, tf32_lo(xi, hi_));
+      } else {
+        st_shared_f32(sBh + o_r, xr);
+        st_shared_f32(sBh + o_i, xi);
+      }
+    };
+    auto signal_b = [&]() {
+      fence_proxy_async();          // generic shared-memory writes -> tensor core
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(bready));
+    };
+    for (int item = blockIdx.x; item < items && !*fail; item += gridDim.x) {
+      const int w = item / nchunk;
+      const int j0 = (item - w * nchunk) * n16;
+      const int nc = min(n16, N - j0);
+      const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < cp) {
+          const int col = c0 + c;
+          const bool ok = col < nc && i < M;
+          sr[c] = ok ? Pw[((long)col * 2 + 0) * M + i] : 0.f;
+          si[c] = ok ? Pw[((long)col * 2 + 1) * M + i] : 0.f;
+          put_b(col >> 3, c & 7, sr[c], si[c]);
+        }
+      }
+      signal_b();
+      for (int r = 0; r < R; ++r) {
+        if (!mbar_wait(smem_u32(aready), pa)) {
+          flag_timeout(status);
+          *fail = 1;
+          break;
+        }
+        pa ^= 1u;
+        fence_after_sync();
+        const bool half = (r == 0 || r == R - 1);
+        const float inv = half ? 1.f : 1.f / (float)r;
+#pragma unroll
+        for (int cb = 0; cb < 32; cb += 8) {
+          if (cb < cp) {
+            float pr[8], pi[8], qr[8], qi[8];
+            const uint32_t a0 = lane_addr + acc_col(mt, 0) + (uint32_t)(c0 + cb);
+            tmem_ld8_nowait(a0, pr);
+            tmem_ld8_nowait(a0 + (uint32_t)n16, pi);
+            if (!half) {
+              const uint32_t a1 = lane_addr + acc_col(mt, 1) + (uint32_t)(c0 + cb);
+              tmem_ld8_nowait(a1, qr);
+              tmem_ld8_nowait(a1 + (uint32_t)n16, qi);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int c = cb + u;
+              float dr = pr[u], di = pi[u];
+              if (!half) {                      // t_r = V t_{r-1} / r
+                dr = (pr[u] - qi[u]) * inv;
+                di = (pi[u] + qr[u]) * inv;
+              }
+              sr[c] += dr;                      // r = 0: t0 = Phi + (B_half - I) Phi;
+              si[c] += di;                      // last: out = s + (B_half - I) s
+              // the next round's operand: t_r, or the sum before the last half step
+              const bool term = !half && r < order;
+              pr[u] = term ? dr : sr[c];
+              pi[u] = term ? di : si[c];
+            }
+            if (r < R - 1) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) put_b((c0 + cb) >> 3, u, pr[u], pi[u]);
+            }
+          }
+        }
+        if (r < R - 1) {
+          signal_b();
+        } else {
+          fence_before_sync();
+        }
+      }
+      if (*fail) break;
+      float* Ow = Pout + ((long)w * N + j0) * 2 * M;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int col = c0 + c;
+        if (c < cp && col < nc && i < M) {
+          Ow[((long)col * 2 + 0) * M + i] = sr[c];
+          Ow[((long)col * 2 + 1) * M + i] = si[c];
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, (uint32_t)cols);
+}
+
 template <typename K>
 cudaError_t set_smem(K kernel, int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) cudaGetLastError();
-  return e;
+  return smem_optin((const void*)kernel) >= (size_t)bytes ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t make_map(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, long k,
@@ -644,13 +965,30 @@ cudaError_t make_map(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, lo
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 3-D map of `planes` row-major matrices (rows x k, row stride ld floats,
+// plane stride rows * ld floats) with 128-row x 32-K boxes.
+cudaError_t make_map3(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, long k, long ld,
+                      long planes) {
+  if (((uintptr_t)ptr & 15) != 0 || (ld & 3) != 0 || k < 1 || rows < 1 || planes < 1)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)(rows * ld) * 4};
+  cuuint32_t box[3] = {32u, 128u, 1u};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = t->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int BN, bool SPLIT3, bool BLO>
 cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
                         long lda, const float* B, const float* Blo, long ldb, float* C,
                         long ldc, float alpha, float beta, const float* R, long ldr,
-                        int ksplit, long split_stride, int* status) {
+                        int ksplit, long split_stride, int* status, float* Clo) {
   using Cfg = GemmCfg<BN, SPLIT3>;
-  static const cudaError_t attr = set_smem(tc_gemm_kernel<BN, SPLIT3, BLO>, Cfg::SMEM);
+  const cudaError_t attr = set_smem(tc_gemm_kernel<BN, SPLIT3, BLO>, Cfg::SMEM);
   if (attr != cudaSuccess) return attr;
   CUtensorMap ma, mb, mbl;
   cudaError_t e = make_map(t, &ma, A, m, k, lda, BM);
@@ -673,7 +1011,7 @@ cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const fl
   wk.items = (int)items;
   const int grid = wk.items < t->num_sms ? wk.items : t->num_sms;
   tc_gemm_kernel<BN, SPLIT3, BLO><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(
-      ma, mb, mbl, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status);
+      ma, mb, mbl, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status, Clo);
   return cudaGetLastError();
 }
 
@@ -703,15 +1041,16 @@ void tc_destroy(TcCtx* t) { delete t; }
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A, long lda,
                     const float* B, long ldb, float* C, long ldc, float alpha, float beta,
                     const float* R, long ldr, bool split3, int ksplit, long split_stride,
-                    int* status, int bn, const float* Blo) {
+                    int* status, int bn, const float* Blo, float* Clo) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ksplit < 1 || (ksplit > 1 && (R || beta != 0.f))) return cudaErrorInvalidValue;
+  if (Clo && ksplit != 1) return cudaErrorInvalidValue;
   if (bn != 0 && bn != 64 && bn != 128) return cudaErrorInvalidValue;
   if (Blo && !split3) return cudaErrorInvalidValue;
   if (bn == 0) bn = n <= 64 ? 64 : 128;
 #define AFQMC_GEMM(BNV, S3, BL)                                                            \
   return launch_gemm<BNV, S3, BL>(t, st, m, n, k, A, lda, B, Blo, ldb, C, ldc, alpha, beta, \
-                                  R, ldr, ksplit, split_stride, status)
+                                  R, ldr, ksplit, split_stride, status, Clo)
   if (bn == 64) {
     if (!split3) AFQMC_GEMM(64, false, false);
     if (Blo) AFQMC_GEMM(64, true, true);
@@ -723,13 +1062,13 @@ cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float*
 #undef AFQMC_GEMM
 }
 
-// hi (in place, x rounded to TF32) and lo = x - hi of n floats.
+// hi (in place, x rounded to TF32) and lo = (x - hi) rounded to TF32.
 __global__ void tf32_split_kernel(long n, float* __restrict__ x, float* __restrict__ lo) {
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const float v = x[e], h = tf32_hi(v);
   x[e] = h;
-  lo[e] = v - h;
+  lo[e] = tf32_lo(v, h);
 }
 
 cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo) {
@@ -745,17 +1084,61 @@ cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
   if (bhalf_img && ((uintptr_t)bhalf_img & 15)) return cudaErrorInvalidValue;
   const int items = W * ((N + 63) / 64);
   if (split3) {
-    static const cudaError_t attr = set_smem(tc_taylor_kernel<true>, taylor_smem<true>());
+    const cudaError_t attr = set_smem(tc_taylor_kernel<true>, taylor_smem<true>());
     if (attr != cudaSuccess) return attr;
     int grid = items < t->num_sms ? items : t->num_sms;
     tc_taylor_kernel<true><<<grid, 128, taylor_smem<true>(), st>>>(W, M, N, order, V, Pin,
                                                                   Pout, bhalf_img, status);
   } else {
-    static const cudaError_t attr = set_smem(tc_taylor_kernel<false>, taylor_smem<false>());
+    const cudaError_t attr = set_smem(tc_taylor_kernel<false>, taylor_smem<false>());
     if (attr != cudaSuccess) return attr;
     int grid = items < 2 * t->num_sms ? items : 2 * t->num_sms;
     tc_taylor_kernel<false><<<grid, 128, taylor_smem<false>(), st>>>(W, M, N, order, V, Pin,
                                                                     Pout, bhalf_img, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t tc_taylor_wide(TcCtx* t, cudaStream_t st, int W, int M, int N, int order, long ldV,
+                           const float* V, const float* Vlo, const float* dB, const float* dBlo,
+                           const float* Pin, float* Pout, bool split3, int* status) {
+  if (M < 1 || M > 256 || N < 1 || W < 1 || order < 1 || ldV < M || (ldV & 3))
+    return cudaErrorInvalidValue;
+  if (split3 && (!Vlo || !dBlo)) return cudaErrorInvalidValue;
+  const int MT = (M + 127) / 128, KB = (M + 31) / 32, P = split3 ? 2 : 1;
+  const int stage = TW_TILE_BYTES * P;
+  const int budget = 227 * 1024 - 1024 - 256;
+  int n16 = ((N + 15) / 16) * 16;
+  const int n16max = MT == 2 ? 32 : 64;
+  if (n16 > n16max) n16 = n16max;
+  while (n16 > 16 && KB * 2 * n16 * 128 * P + 3 * stage > budget) n16 -= 16;
+  const int b = KB * 2 * n16 * 128 * P;
+  int S = (budget - b) / stage;
+  if (S > 8) S = 8;
+  if (S < 2) return cudaErrorInvalidValue;
+  const int smem = 1024 + b + S * stage + 256;
+  CUtensorMap mv, mvl, mb, mbl;
+  cudaError_t e = make_map3(t, &mv, V, M, M, ldV, 2L * W);
+  if (e == cudaSuccess) e = make_map3(t, &mb, dB, M, M, ldV, 1);
+  if (e == cudaSuccess && split3) e = make_map3(t, &mvl, Vlo, M, M, ldV, 2L * W);
+  if (e == cudaSuccess && split3) e = make_map3(t, &mbl, dBlo, M, M, ldV, 1);
+  if (e != cudaSuccess) return e;
+  if (!split3) {
+    mvl = mv;
+    mbl = mb;
+  }
+  const long items = (long)W * ((N + n16 - 1) / n16);
+  const int grid = items < t->num_sms ? (int)items : t->num_sms;
+  if (split3) {
+    e = set_smem(tc_taylor_wide_kernel<true>, smem);
+    if (e != cudaSuccess) return e;
+    tc_taylor_wide_kernel<true><<<grid, TW_THREADS, smem, st>>>(mv, mvl, mb, mbl, W, M, N, order,
+                                                               n16, S, Pin, Pout, status);
+  } else {
+    e = set_smem(tc_taylor_wide_kernel<false>, smem);
+    if (e != cudaSuccess) return e;
+    tc_taylor_wide_kernel<false><<<grid, TW_THREADS, smem, st>>>(mv, mvl, mb, mbl, W, M, N,
+                                                                order, n16, S, Pin, Pout, status);
   }
   return cudaGetLastError();
 }

@@ -19,13 +19,16 @@ void tc_destroy(TcCtx* t);
 // output tile width (64 or 128; 0 picks 64 for n <= 64, else 128). A
 // device-side wait that times out sets bit 4 of *status.
 // With split3 and Blo, B already holds hi = B rounded to TF32 and Blo the
-// remainder (see tc_split), so only A is split on the fly.
+// remainder (see tc_split), so only A is split on the fly. With Clo (ksplit
+// 1), the result leaves split the same way: C receives its TF32 hi part and
+// Clo (same layout) the remainder.
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
                     long lda, const float* B, long ldb, float* C, long ldc, float alpha,
                     float beta, const float* R, long ldr, bool split3, int ksplit,
-                    long split_stride, int* status, int bn = 0, const float* Blo = nullptr);
+                    long split_stride, int* status, int bn = 0, const float* Blo = nullptr,
+                    float* Clo = nullptr);
 
-// x <- x rounded to TF32, lo <- the remainder (exact), n floats.
+// x <- x rounded to TF32, lo <- the remainder x - hi rounded to TF32, n floats.
 cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo);
 
 // Taylor propagation of W walkers (M <= 64): Pout = sum_{n<=order} V^n Pin / n!
@@ -37,6 +40,16 @@ cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo);
 cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
                       const float* V, const float* Pin, float* Pout, const float* bhalf_img,
                       bool split3, int* status);
+
+// B_half exp_T(V) B_half for 64 < M <= 256 (any M <= 256 works), W walkers,
+// Pin -> Pout ([W][N][2][M], Pout may be Pin), on the tensor cores with the
+// operator streamed from global memory: V [W][2][M][ldV] and dB = B_half - I
+// [M][ldV] (ldV a multiple of 4, >= M). TF32X3 (split3): V and dB hold the
+// TF32 hi parts and Vlo, dBlo the remainders. A device-side wait that times
+// out sets bit 4 of *status.
+cudaError_t tc_taylor_wide(TcCtx* t, cudaStream_t st, int W, int M, int N, int order, long ldV,
+                           const float* V, const float* Vlo, const float* dB, const float* dBlo,
+                           const float* Pin, float* Pout, bool split3, int* status);
 
 // Operand image of (B_half - I) (M x M, row-major fp32 in dB) for tc_taylor:
 // tc_bhalf_image_floats(split3) floats, 16-byte aligned.

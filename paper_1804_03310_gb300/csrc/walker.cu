@@ -5,30 +5,45 @@
 // (Sec. III, Eq. 5), and the comb (Sec. V).
 #include <float.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace afqmc {
 
-namespace {
-
-
-// Opt the kernel in to the largest dynamic shared memory the device allows
-// beside its static shared memory; returns that limit in bytes. Errors of
-// these queries are cleared so they cannot surface at a later launch check.
-template <typename K>
-size_t allow_big_smem(K kernel) {
-  int dev = 0, optin = 48 * 1024;
-  cudaGetDevice(&dev);
+size_t smem_optin(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, dev);
+  const auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int optin = 48 * 1024;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
   size_t stat = 0;
   if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
   size_t dyn = (size_t)optin > stat ? (size_t)optin - stat : 0;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+      cudaSuccess) {
+    const size_t def = 48 * 1024;
+    dyn = def > stat ? def - stat : 0;   // the limit without an opt-in
+  }
   cudaGetLastError();
+  cache[key] = dyn;
   return dyn;
 }
+
+namespace {
+
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
   return make_double2(a.x + b.x, a.y + b.y);
@@ -166,7 +181,7 @@ constexpr int kTayMaxThreads = 512;
 // the terms alternate between two shared buffers.
 template <typename T, int TR>
 __global__ void __launch_bounds__(kTayMaxThreads)
-taylor_tiled_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
+taylor_tiled_kernel(int M, int N, int NC, int order, const T* __restrict__ V, long ldv,
                     const T* __restrict__ Pin, T* __restrict__ Pout) {
   extern __shared__ unsigned char smem_raw[];
   const int ldt = M | 1;
@@ -176,7 +191,7 @@ taylor_tiled_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
   const int w = blockIdx.x;
   const int j0 = blockIdx.y * NC;
   const int nc = min(NC, N - j0);
-  const T* Vw = V + (long)w * 2 * M * M;
+  const T* Vw = V + (long)w * 2 * M * ldv;
   const T* Pw = Pin + ((long)w * N + j0) * 2 * M;
   T* Ow = Pout + ((long)w * N + j0) * 2 * M;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -197,8 +212,10 @@ taylor_tiled_kernel(int M, int N, int NC, int order, const T* __restrict__ V,
     const int kc = min(kTayKC, M - k0);
     T* dst = vbuf + (long)(q & 1) * 2 * per;
     for (int e = tid; e < kc * M; e += nt) {
-      cp_async_elem<sizeof(T)>(dst + e, Vw + (long)k0 * M + e);
-      cp_async_elem<sizeof(T)>(dst + per + e, Vw + (long)(M + k0) * M + e);
+      const int rk = e / M, ck = e - rk * M;          // V symmetric: rows stand for columns
+      const long src = (long)(k0 + rk) * ldv + ck;
+      cp_async_elem<sizeof(T)>(dst + e, Vw + src);
+      cp_async_elem<sizeof(T)>(dst + per + e, Vw + (long)M * ldv + src);
     }
     cp_async_commit();
   };
@@ -953,6 +970,18 @@ __global__ void pad_rows_kernel(long rows, long Jup, long Jdn, const double* __r
   out[r * ld + (c < Jup ? c : dn_off + (c - Jup))] = in[e];
 }
 
+// L [G][M*M] -> out [M*ldv][ldo]: out[i ldv + k][g] = L[g][i M + k]; the
+// rows i ldv + k with k >= M are left as they are (zero).
+__global__ void transpose_pad_kernel(long G, int M, long ldv, const double* __restrict__ in,
+                                     double* __restrict__ out, long ldo) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long MM = (long)M * M;
+  if (e >= G * MM) return;
+  const long g = e / MM, r = e - g * MM;
+  const long i = r / M, k = r - i * M;
+  out[(i * ldv + k) * ldo + g] = in[e];
+}
+
 // out[i][j] = in[j][i] for an rows x cols matrix, into leading dimension ldo.
 __global__ void transpose_kernel(long rows, long cols, const double* __restrict__ in,
                                  double* __restrict__ out, long ldo) {
@@ -1010,9 +1039,9 @@ cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long l
 
 template <typename T>
 cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
-                          const T* V, const T* Phi_in, T* Phi_out) {
+                          const T* V, long ldv, const T* Phi_in, T* Phi_out) {
   constexpr int TR = sizeof(T) == 4 ? 4 : 2;
-  static const size_t cap = allow_big_smem(taylor_tiled_kernel<T, TR>);
+  const size_t cap = smem_optin((const void*)taylor_tiled_kernel<T, TR>);
   if (M < 1 || N < 1) return cudaErrorInvalidValue;
   const int nr = (M + TR - 1) / TR;
   const int ldt = M | 1;
@@ -1028,8 +1057,9 @@ cudaError_t launch_taylor(cudaStream_t st, int W, int M, int N, int order,
   const int tiles = nr * ((NC + 3) / 4);
   const int threads = (tiles + 31) / 32 * 32;
   dim3 grid(W, pieces);
-  taylor_tiled_kernel<T, TR><<<grid, threads, smem_for(NC), st>>>(M, N, NC, order, V, Phi_in,
-                                                                  Phi_out);
+  if (ldv < M) return cudaErrorInvalidValue;
+  taylor_tiled_kernel<T, TR><<<grid, threads, smem_for(NC), st>>>(M, N, NC, order, V, ldv,
+                                                                  Phi_in, Phi_out);
   return cudaGetLastError();
 }
 
@@ -1048,7 +1078,7 @@ cudaError_t launch_overlap_nt(cudaStream_t st, int W, int M, int n_up, int n_dn,
                               const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
                               double2* logdet, double2* Ainv) {
   const int nmax = n_up > n_dn ? n_up : n_dn;
-  static const size_t cap = allow_big_smem(overlap_kernel<T, R, NT>);
+  const size_t cap = smem_optin((const void*)overlap_kernel<T, R, NT>);
   const size_t smem = overlap_smem(M, nmax, sizeof(cx<R>));
   if (smem > cap) return cudaErrorInvalidValue;
   overlap_kernel<T, R, NT><<<dim3(W, 2), NT, smem, st>>>(M, n_up, n_dn, Phi, PsiT, Theta, ldt,
@@ -1095,12 +1125,12 @@ cudaError_t launch_qr(cudaStream_t st, int W, int M, int n_up, int n_dn, T* Phi,
   const int threads = M > 96 ? 256 : 128;
   dim3 grid(W, 2);
   if (fp64_compute) {
-    static const size_t cap = allow_big_smem(qr_kernel<T, double>);
+    const size_t cap = smem_optin((const void*)qr_kernel<T, double>);
     const size_t smem = qr_smem(M, nmax, sizeof(double2));
     if (smem > cap) return cudaErrorInvalidValue;
     qr_kernel<T, double><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
   } else {
-    static const size_t cap = allow_big_smem(qr_kernel<T, float>);
+    const size_t cap = smem_optin((const void*)qr_kernel<T, float>);
     const size_t smem = qr_smem(M, nmax, sizeof(float2));
     if (smem > cap) return cudaErrorInvalidValue;
     qr_kernel<T, float><<<grid, threads, smem, st>>>(M, n_up, n_dn, Phi, lr);
@@ -1132,7 +1162,7 @@ cudaError_t launch_mixed_energy(cudaStream_t st, int W, const double* weight,
 cudaError_t launch_comb(cudaStream_t st, int W, const double* weight, uint64_t seed,
                         int run_id, const long long* ctr, long step, int* parent,
                         double* scratch, double* wnew, int* status) {
-  static const size_t smem_cap = allow_big_smem(comb_kernel);
+  const size_t smem_cap = smem_optin((const void*)comb_kernel);
   int nb = (W + kScanBlock - 1) / kScanBlock;
   size_t smem = sizeof(double) * 2 * (size_t)nb;
   if (smem > smem_cap) return cudaErrorInvalidValue;
@@ -1192,6 +1222,12 @@ cudaError_t launch_pad_rows(cudaStream_t st, long rows, long Jup, long Jdn,
   return cudaGetLastError();
 }
 
+cudaError_t launch_transpose_pad(cudaStream_t st, long G, int M, long ldv, const double* in,
+                                 double* out, long ldo) {
+  transpose_pad_kernel<<<blocks_for(G * M * M, 256), 256, 0, st>>>(G, M, ldv, in, out, ldo);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_transpose(cudaStream_t st, long rows, long cols, const double* in,
                              double* out, long ldo) {
   transpose_kernel<<<blocks_for(rows * cols, 256), 256, 0, st>>>(rows, cols, in, out, ldo);
@@ -1226,7 +1262,7 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
   template cudaError_t launch_fields<T>(cudaStream_t, int, int, const T*, long, int,    \
                                         long, double, double, uint64_t, int,            \
                                         const long long*, T*, long, T*, double2*);      \
-  template cudaError_t launch_taylor<T>(cudaStream_t, int, int, int, int, const T*,     \
+  template cudaError_t launch_taylor<T>(cudaStream_t, int, int, int, int, const T*, long,\
                                         const T*, T*);                                  \
   template cudaError_t launch_overlap<T>(cudaStream_t, int, int, int, int, const T*,    \
                                          const T*, T*, long, long, double2*, double2*,  \

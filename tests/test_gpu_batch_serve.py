@@ -116,9 +116,14 @@ def test_tuning_rejects_invalid_shapes():
     with pytest.raises(AfqmcError):
         c.afqmc_set_tuning(taylor_fused=2)           # M > 64
     with pytest.raises(AfqmcError):
-        c.afqmc_set_tuning(taylor_fused=3)
+        c.afqmc_set_tuning(taylor_fused=4)
     with pytest.raises(AfqmcError):
         c.afqmc_set_tuning(bn_energy=96)
+    c.afqmc_set_tuning(taylor_fused=3)               # streamed operator: M > 64
+    c.close()
+    c = ctx(mixed_system(M=40, n_chol=20, W=8), precision="tf32")
+    with pytest.raises(AfqmcError):
+        c.afqmc_set_tuning(taylor_fused=3)           # M <= 64
     c.close()
     f = ctx(mixed_system(W=8), precision="fp64")
     assert f.afqmc_get_tuning()["xsplit"] == 1

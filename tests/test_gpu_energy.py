@@ -8,16 +8,19 @@ path itself agrees with the FP64 oracle walker by walker over the first 20
 shared-draw steps (test_gpu_step.py), so it stands in for the oracle at
 lengths the oracle cannot follow.
 
-Two checks, both on the plain 10-orbital system (5+5 electrons, 40 dense
-fields, trial of h1 eigenvectors), whose mixed estimate is stationary after
-about 1 Ha^-1 (the larger synthetic shapes start tens of Ha above their
-ground state and keep drifting for longer than a test can follow):
+Checks:
 
-* paired: both runs draw the same fields and the comb is off, so walker i of
-  one run is walker i of the other for the whole run; the difference of the
-  two mixed estimates, measurement by measurement, is the precision error
-  alone, free of statistical noise: it must stay within 0.5 mHa;
-* independent: with the comb on, the runs part ways after a few hundred
+* paired, at every workload shape (the plain 10-orbital system, the
+  H-chain, TM-atom and multi-determinant shapes at full size): both runs
+  draw the same fields and the comb is off, so walker i of one run is
+  walker i of the other for the whole run; the difference of the two mixed
+  estimates, measurement by measurement, is the precision error alone, free
+  of statistical noise, whether or not the energy is still drifting: it
+  must stay within 0.5 mHa;
+* independent, on the plain 10-orbital system, whose mixed estimate is
+  stationary after about 1 Ha^-1 (the larger synthetic shapes start tens of
+  Ha above their ground state and keep drifting for longer than a test can
+  follow): with the comb on, the runs part ways after a few hundred
   steps (a tooth of the comb lands on the other side of a walker boundary),
   so their long-run means differ by statistical noise of about 1 mHa at this
   length (50 million walker-steps each); they must agree within twice the
@@ -27,7 +30,7 @@ ground state and keep drifting for longer than a test can follow):
 import numpy as np
 import pytest
 
-from synth import config_c1
+from synth import config_c1, config_c2, config_c3, config_c4
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +88,35 @@ def test_paired_energy_matches_fp64(fp64_paired, prec):
     d = red - fp64_paired
     print(f"paired c1 {prec}: max |dE| = {np.max(np.abs(d)) / MHA:.5f} mHa, "
           f"mean dE = {np.mean(d) / MHA:.5f} mHa over {len(d)} measurements")
+    assert np.max(np.abs(d)) <= 0.5 * MHA
+
+
+# full-size shapes, comb off, one measurement every 20 steps
+SHAPES = {
+    "c2": (config_c2(pc_every=0), 200),
+    "c3": (config_c3(pc_every=0), 100),
+    "c4": (config_c4(pc_every=0), 200),
+}
+_FP64_SHAPES = {}
+
+
+def fp64_shape(name):
+    if name not in _FP64_SHAPES:
+        s, n = SHAPES[name]
+        _FP64_SHAPES[name] = run_energies(s, "fp64", n)
+    return _FP64_SHAPES[name]
+
+
+@pytest.mark.parametrize("name,prec", [("c2", "tf32x3"), ("c2", "fp32"),
+                                       ("c3", "tf32x3"), ("c4", "tf32x3"),
+                                       ("c4", "fp32")])
+def test_paired_energy_at_workload_shapes(name, prec):
+    s, n = SHAPES[name]
+    ref = fp64_shape(name)
+    red = run_energies(s, prec, n)
+    d = red - ref
+    print(f"paired {name} {prec}: max |dE| = {np.max(np.abs(d)) / MHA:.5f} mHa over "
+          f"{len(d)} measurements (E = {ref[-1]:.4f} Ha at step {n})")
     assert np.max(np.abs(d)) <= 0.5 * MHA
 
 

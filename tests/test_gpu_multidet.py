@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from fock import FockSpace
-from gpu_helpers import compare_energy, compare_green, compare_state
+from gpu_helpers import side_by_side
 from oracle import afqmc as O
 from synth import config_c4, small_system
 
@@ -22,26 +22,14 @@ def gpu_ctx(system, **kw):
     return Afqmc.from_system(system, **kw)
 
 
-def run_pair(system, precision, n_steps, rtol, walkers=None, energy_at=(), green_at=()):
-    gpu = gpu_ctx(system, precision=precision)
-    orc = O.OracleRun(system, walker_ids=walkers)
+def run_pair(system, precision, n_steps, rtol, walkers=None, energy_at=()):
     # at tau = 0 every walker is the reference determinant, whose overlap
     # with the excited determinants vanishes (a 0/0 local energy); the first
     # comparisons come after one step
-    worst = {}
-    for s in range(1, n_steps + 1):
-        gpu.afqmc_propagate(1)
-        orc.step()
-        for k, v in compare_state(gpu, orc, rtol=rtol, walkers=walkers,
-                                  label=f"step {s}").items():
-            worst[k] = max(worst.get(k, 0.0), v)
-        if s in energy_at:
-            worst["energy"] = max(worst.get("energy", 0.0),
-                                  compare_energy(gpu, orc, rtol=rtol, walkers=walkers,
-                                                 label=f"step {s}"))
-        if s in green_at:
-            compare_green(gpu, orc, len(orc.walker_ids) - 1, orc.walker_ids[-1],
-                          rtol=rtol * 10, label=f"step {s}")
+    gpu = gpu_ctx(system, precision=precision)
+    orc = O.OracleRun(system, walker_ids=walkers)
+    worst = side_by_side(gpu, orc, n_steps, rtol, walkers=walkers, energy_at=energy_at,
+                         label=precision)
     gpu.close()
     return worst
 
@@ -64,7 +52,7 @@ def test_small_multidet_fp64(n_det):
                      n_walkers=16, dtau=0.01, l_sigma=0.08, ortho_every=2,
                      measure_every=4, pc_every=4)
     s = scrambled(s, np.random.default_rng(n_det))
-    w = run_pair(s, "fp64", 8, 1e-10, energy_at=(1, 4, 8), green_at=(3, 8))
+    w = run_pair(s, "fp64", 8, 1e-10, energy_at=(1, 4, 8))
     print(f"multidet n_det={n_det} fp64 worst", w)
 
 
@@ -73,7 +61,7 @@ def test_unequal_spins_multidet_fp64():
                      dtau=0.01, l_sigma=0.08, ortho_every=2, measure_every=3,
                      pc_every=0)
     s = scrambled(s, np.random.default_rng(2))
-    run_pair(s, "fp64", 6, 1e-10, energy_at=(3, 6), green_at=(6,))
+    run_pair(s, "fp64", 6, 1e-10, energy_at=(3, 6))
 
 
 def test_exact_trial_zero_variance_gpu():
@@ -96,13 +84,15 @@ def test_exact_trial_zero_variance_gpu():
 
 
 def test_c4_full_size_sampled_fp64():
-    s = config_c4()
-    w = run_pair(s, "fp64", 3, 1e-10, walkers=[0, 1023], energy_at=(3,), green_at=(3,))
+    """200-determinant workload at full size, two sampled walkers followed for
+    the first 20 steps (comb off)."""
+    s = config_c4(pc_every=0)
+    w = run_pair(s, "fp64", 20, 1e-10, walkers=[0, 1023], energy_at=(20,))
     print("c4 fp64 worst", w)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp32"])
 def test_c4_full_size_sampled_reduced(prec):
-    s = config_c4()
-    w = run_pair(s, prec, 19, 1e-4, walkers=[0, 511, 1023], energy_at=(19,))
+    s = config_c4(pc_every=0)
+    w = run_pair(s, prec, 20, 1e-4, walkers=[0, 511, 1023], energy_at=(20,))
     print(f"c4 {prec} worst", w)

@@ -72,6 +72,29 @@ def test_static_comb_matches_context_comb_on_two_calls():
         assert np.all(w_ctx == wn)
 
 
+def test_static_comb_reports_an_impossible_comb_by_a_negative_weight():
+    """All-zero or non-finite weights leave nothing to comb: the call returns
+    d_wnew = -1 with the identity in d_parent (its only signal; the kernel's
+    status word stays in the library's array). A normal call right after
+    must not be disturbed by the status left behind."""
+    rng = np.random.default_rng(5)
+    n = 77
+    zero = np.zeros(n)
+    nan = rng.uniform(0.5, 1.5, size=n)
+    nan[13] = np.nan
+    inf = rng.uniform(0.5, 1.5, size=n)
+    inf[40] = np.inf
+    for w in (zero, nan, inf):
+        p, wn = static_comb(w, 3, 0)
+        assert wn == -1.0
+        assert np.array_equal(p, np.arange(n))
+    w = rng.uniform(0.0, 2.0, size=n)
+    p_ctx, w_ctx, s_seed, s_run = context_comb(w, 9)
+    p_st, wn = static_comb(w, s_seed, s_run)
+    assert np.array_equal(p_st, p_ctx)
+    assert np.all(w_ctx == wn)
+
+
 def test_static_comb_rejects_oversized_population():
     from paper_1804_03310_gb300 import AfqmcError
     from paper_1804_03310_gb300.afqmc import COMB_STATIC_MAX_WALKERS, afqmc_comb_static
