@@ -400,7 +400,8 @@ def fp64_compare(args, s, hist):
 def energy_check_shapes(precision):
     """Paired energy deviation at the full-size shapes: the H-chain shape
     (200 steps), the TM-atom shape (100 steps) and the multi-determinant
-    shape (200 steps), each in `precision` and in FP64 on the GPU with the
+    shape (60 steps: without the comb its walkers die off from about step
+    50), each in `precision` and in FP64 on the GPU with the
     same seed, comb off, one measurement every 20 steps. Walker i of one run
     is walker i of the other, so the difference of the mixed estimates is
     the precision error alone, whether or not the energy still drifts."""
@@ -408,7 +409,7 @@ def energy_check_shapes(precision):
     from synth import CONFIGS
     from paper_1804_03310_gb300 import Afqmc
     out = {}
-    for name, n_steps in (("c2", 200), ("c3", 100), ("c4", 200)):
+    for name, n_steps in (("c2", 200), ("c3", 100), ("c4", 60)):
         s = CONFIGS[name]().replace(pc_every=0, measure_every=20)
         e = {}
         for p in ("fp64", precision):
@@ -627,6 +628,50 @@ def ndet_leg(precision, ndets=(1, 10, 50, 200, 500)):
             "points": out}
 
 
+def cs_leg(precision, W=2048, n_steps=800):
+    """Correlated sampling (Sec. V): the ionisation energy E(cation) -
+    E(neutral) of the 10-orbital system (5+5 and 5+4 electrons, same
+    Hamiltonian and orbitals, comb off, energy every 10 steps) with shared
+    field paths (equal seed and Philox tag) against independent paths. The
+    reblocked standard error of the difference series is the figure of
+    merit: the variance ratio is the factor of sampling time correlated
+    sampling saves at equal error bar."""
+    import numpy as np
+    from synth import make_system
+    from paper_1804_03310_gb300 import Afqmc
+    kw = dict(M=10, n_chol=40, ham_seed=0, l_kind="dense", l_sigma=0.05, trial="eig",
+              dtau=0.01, n_walkers=W, seed=17, ortho_every=5, measure_every=10, pc_every=0)
+    out = {}
+    t0 = time.perf_counter()
+    for label, ids in (("correlated", (3, 3)), ("independent", (3, 4))):
+        e = []
+        for nd, rid in ((5, ids[0]), (4, ids[1])):
+            sy = make_system("cs", n_up=5, n_dn=nd, run_id=rid, **kw)
+            with Afqmc.from_system(sy, precision=precision) as ctx:
+                ctx.afqmc_propagate(n_steps)
+                e.append(ctx.afqmc_energy_history()[:, 1])
+        d = (e[1] - e[0])[10:]
+        out[label] = {"ip_ha": round(float(np.mean(d)), 6),
+                      "stderr_ha": round(reblocked_error(d), 7)}
+    r = (out["independent"]["stderr_ha"] / max(out["correlated"]["stderr_ha"], 1e-300)) ** 2
+    return {"workload": (f"M=10 N=5+5 / 5+4 n_chol=40 W={W} dtau=0.01, {n_steps} steps, "
+                         f"comb off, {precision}"),
+            **out, "variance_ratio": round(r, 2),
+            "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def reblocked_error(x):
+    """Standard error of a serially correlated series (blocking analysis)."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    best = 0.0
+    while len(x) >= 4:
+        best = max(best, float(np.std(x, ddof=1) / np.sqrt(len(x))))
+        n = len(x) // 2 * 2
+        x = 0.5 * (x[0:n:2] + x[1:n:2])
+    return best
+
+
 def shapes_leg(precision):
     """The other workload shapes of the scope, each in the measured mode and
     in FP64 on the GPU (same walkers and seed): the TM-atom shape (M = 150,
@@ -700,6 +745,7 @@ def main():
         line["fp64_islands"] = islands_leg(s, args.precision, value)
         line["batch"] = batch_leg(args.precision)
         line["ndet_sweep"] = ndet_leg(args.precision)
+        line["correlated_sampling"] = cs_leg(args.precision)
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,

@@ -103,7 +103,19 @@ typedef struct {
                             a walker near a node of the trial taking a runaway
                             weight, at the price of a bias that vanishes as k
                             grows. */
-  int32_t reserved[4];   /* must be zero */
+  int32_t cs_group;      /* correlated sampling (Sec. V): 0 = none. Runs
+                            that share seed and run_id draw the same fields
+                            walker by walker (the Philox counter depends on
+                            nothing else), so a neutral/cation pair given the
+                            same seed, run_id, n_chol and n_walkers samples
+                            the same auxiliary-field paths and their energy
+                            difference loses most of its variance. A server
+                            admits the runs submitted with the same nonzero
+                            cs_group together, once all cs_size of them have
+                            arrived; outside a server the field is only
+                            validated. */
+  int32_t cs_size;       /* runs in the group, 2..16 (0 when cs_group is 0) */
+  int32_t reserved[2];   /* must be zero */
 } afqmc_params;
 
 /* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,
@@ -167,6 +179,11 @@ afqmc_status afqmc_weights(afqmc_ctx* ctx, double* w, double* log_ovlp);
  * (re, im interleaved, row-major); either pointer may be NULL. */
 afqmc_status afqmc_green(afqmc_ctx* ctx, int32_t walker, double* G_up,
                          double* G_dn);
+
+/* The energy shift E_T in use (Sec. II): params.e_shift, or when that is NaN
+ * the energy of the reference determinant <D_0|H|D_0>, evaluated in FP64 at
+ * creation whatever the step precision. */
+afqmc_status afqmc_energy_shift(afqmc_ctx* ctx, double* e_shift);
 
 /* Force bias xbar of the last step, [n_walkers * n_chol * 2] (re, im). */
 afqmc_status afqmc_force_bias(afqmc_ctx* ctx, double* xbar);
@@ -341,7 +358,12 @@ typedef struct {
 afqmc_status afqmc_server_create(const afqmc_server_config* cfg, afqmc_server** out);
 /* Queue a run. All inputs as for afqmc_create (copied during the call);
  * n_blocks >= 1 blocks of steps_per_block >= 1 steps. *run_id receives the
- * run's handle (not the Philox run_id, which stays params->run_id). */
+ * run's handle (not the Philox run_id, which stays params->run_id).
+ * Correlated-sampling groups (params->cs_group != 0): every member must
+ * match the group's first member in seed, run_id, n_chol, n_walkers, dtau,
+ * the cadences, the Taylor order, cs_size, n_blocks and steps_per_block
+ * (else AFQMC_E_INVALID), a group takes at most cs_size runs, and a group
+ * id cannot be reused once its runs were admitted. */
 afqmc_status afqmc_server_submit(afqmc_server* s, const afqmc_params* params,
                                  const double* h1, const double* L,
                                  const double* C_up, const double* C_dn,

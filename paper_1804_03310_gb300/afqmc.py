@@ -34,7 +34,8 @@ class afqmc_params(C.Structure):
                 ("taylor_order", C.c_int32), ("fb_cap", C.c_double),
                 ("e_shift", C.c_double), ("fp64_islands", C.c_int32),
                 ("graphs", C.c_int32), ("autotune", C.c_int32),
-                ("weight_cap", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("weight_cap", C.c_int32), ("cs_group", C.c_int32),
+                ("cs_size", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class afqmc_tuning(C.Structure):
@@ -107,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "afqmc_weights": (C.c_int, [vp, d, d]),
         "afqmc_green": (C.c_int, [vp, C.c_int32, d, d]),
         "afqmc_force_bias": (C.c_int, [vp, d]),
+        "afqmc_energy_shift": (C.c_int, [vp, d]),
         "afqmc_energy_history": (C.c_int, [vp, d, C.c_int32, i32]),
         "afqmc_get_state": (C.c_int, [vp, vp, P(C.c_size_t)]),
         "afqmc_set_state": (C.c_int, [vp, vp, C.c_size_t]),
@@ -167,7 +169,7 @@ class Inputs:
                  n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
                  measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
                  e_shift=None, fp64_islands=False, graphs=True, autotune=True,
-                 weight_cap=0):
+                 weight_cap=0, cs_group=0, cs_size=0):
         self.h1 = np.ascontiguousarray(h1, dtype=np.float64)
         self.L = np.ascontiguousarray(L, dtype=np.float64)
         self.C_up = np.ascontiguousarray(C_up, dtype=np.float64)
@@ -196,6 +198,8 @@ class Inputs:
         p.graphs = int(bool(graphs))
         p.autotune = int(bool(autotune))
         p.weight_cap = int(weight_cap)
+        p.cs_group = int(cs_group)
+        p.cs_size = int(cs_size)
         self.params = p
 
     @classmethod
@@ -299,6 +303,11 @@ class Afqmc:
         self._check(self._lib.afqmc_green(self._h, walker, _dptr(gu), _dptr(gd)))
         return (gu.view(np.complex128).reshape(self.M, self.M),
                 gd.view(np.complex128).reshape(self.M, self.M))
+
+    def afqmc_energy_shift(self) -> float:
+        e = np.zeros(1)
+        self._check(self._lib.afqmc_energy_shift(self._h, _dptr(e)))
+        return float(e[0])
 
     def afqmc_force_bias(self):
         x = np.zeros(2 * self.n_walkers * self.n_chol)

@@ -96,7 +96,6 @@ struct afqmc_ctx {
 
   // multi-determinant trial (Sherman-Morrison-Woodbury), unused for one determinant
   bool md;
-  bool ref_only;            // evaluate with the reference determinant alone (E_T)
   const double* ci_h;       // caller's CI coefficients (valid during create only)
   MdTables mdt;
   void *md_dets, *md_cc, *md_r0, *md_r1, *md_ct0, *md_ct1;
@@ -269,7 +268,7 @@ afqmc_status force_bias_contraction(afqmc_ctx* c) {
   const int W = c->W, G = c->G;
   KTimer t(c, 0);
   // single determinant: X = Theta . L~^T; multi-determinant: X = Gamma . L~act^T
-  const bool md = c->md && !c->ref_only;
+  const bool md = c->md;
   const void* A = md ? c->Gamma : c->Theta;
   const void* B = md ? c->LtilA : c->Ltil;
   const long ld = md ? c->ldg : c->ldt;
@@ -288,7 +287,7 @@ afqmc_status force_bias_contraction(afqmc_ctx* c) {
 template <typename T>
 afqmc_status measure_T(afqmc_ctx* c, bool record) {
   const int W = c->W, M = c->M, G = c->G;
-  if (c->md && !c->ref_only) {
+  if (c->md) {
     KTimer t(c, 7);
     LK(launch_md_energy<T>(c->st, c->mdt, W, M, c->nu, c->nd, G, (const T*)c->Theta, c->ldt,
                            c->dn_off, c->logdet, (const T*)c->LtilA, c->ldg, c->gdn_off,
@@ -509,8 +508,11 @@ afqmc_status step_T(afqmc_ctx* c) {
 afqmc_status validate_sizes(const afqmc_params* p) {
   afqmc_ctx* c = nullptr;
   if (!p) return fail(c, AFQMC_E_INVALID, "null argument");
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
     if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
+  if (p->cs_group < 0) return fail(c, AFQMC_E_INVALID, "cs_group must be >= 0");
+  if (p->cs_group == 0 ? p->cs_size != 0 : (p->cs_size < 2 || p->cs_size > 16))
+    return fail(c, AFQMC_E_INVALID, "cs_size must be 2..16 in a correlated-sampling group, else 0");
   if (p->weight_cap < 0) return fail(c, AFQMC_E_INVALID, "weight_cap must be >= 0");
   if ((p->graphs != 0 && p->graphs != 1) || (p->autotune != 0 && p->autotune != 1))
     return fail(c, AFQMC_E_INVALID, "graphs and autotune must be 0 or 1");
@@ -661,6 +663,18 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
                   (long)N * M, G));
   LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, h1, M, 0, 0.0,
                   Ltil + (size_t)G * N * M, M, 0, 1));
+  // E_T = E_L of the reference determinant (phi = D, so Theta = D and
+  // theta = vec(D^T)), in FP64 whatever the step precision: tr(h~ D) and
+  // X_g = tr(L~_g D) from one product with the half-rotated vectors, the
+  // exchange term 1/2 theta^T Yx theta per spin below
+  double *et_x, *et_z;
+  TM(et_x, G + 1);
+  TM(et_z, (size_t)std::max(c->nu, c->nd) * M + 1);
+  std::vector<double> et_xh(G + 1);
+  LK(gemm<double>(st, false, true, G + 1, 1, N * M, 1.0, Ltil, (long)N * M, 0, PsiT,
+                  (long)N * M, 0, 0.0, et_x, 1, 0, 1));
+  CK(cudaMemcpyAsync(et_xh.data(), et_x, (G + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double e_exch = 0.0;
   // exchange part of the Eq. 5 tensor, per spin
   for (int sig = 0; sig < 2; ++sig) {
     const int ns = sig ? c->nd : c->nu;
@@ -674,6 +688,16 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
                     (long)N * M, 0, Ltil + (size_t)j0 * M, (long)N * M, 0, 0.0, gram, J, 0, 1));
     CK(cudaMemsetAsync(yx, 0, (size_t)J * J * sizeof(double), st));
     LK(launch_yx_permute(st, ns, M, gram, yx, c->Jp[sig]));
+    {   // 1/2 theta^T Yx theta of the reference determinant, FP64
+      std::vector<double> zh((size_t)J);
+      LK(gemm<double>(st, false, false, 1, (int)J, (int)J, 1.0, PsiT + (size_t)j0 * M, J, 0, yx,
+                      c->Jp[sig], 0, 0.0, et_z, J, 0, 1));
+      CK(cudaMemcpyAsync(zh.data(), et_z, J * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      double q = 0.0;
+      for (long e = 0; e < J; ++e) q += psiT_h[(size_t)j0 * M + e] * zh[e];
+      e_exch += 0.5 * q;
+    }
     void* dst = sig ? c->Yx_dn : c->Yx_up;
     LK(launch_convert<T>(st, J * c->Jp[sig], yx, (T*)dst));
   }
@@ -743,16 +767,13 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   afqmc_status s = overlap_T<T>(c, c->logO);
   if (s != AFQMC_OK) return s;
   if (isnan(c->p.e_shift)) {
-    // E_T: energy of the reference determinant, <D_0|H|D_0>
-    c->ref_only = true;
-    s = measure_T<T>(c, false);
-    c->ref_only = false;
-    if (s != AFQMC_OK) return s;
-    double2 e0;
-    CK(cudaMemcpyAsync(&e0, c->eloc, sizeof(double2), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (!isfinite(e0.x)) return fail(c, AFQMC_E_NUMERIC, "trial energy is not finite");
-    c->e_shift = e0.x;
+    // E_T: energy of the reference determinant, <D_0|H|D_0>, from the FP64
+    // terms gathered above
+    double coul = 0.0;
+    for (int g = 0; g < G; ++g) coul += et_xh[g] * et_xh[g];
+    const double e0 = et_xh[G] + 0.5 * coul + e_exch;
+    if (!isfinite(e0)) return fail(c, AFQMC_E_NUMERIC, "trial energy is not finite");
+    c->e_shift = e0;
   } else {
     c->e_shift = c->p.e_shift;
   }
@@ -1207,6 +1228,8 @@ size_t setup_bytes(const Plan& P) {
   add(MM); add(G * MM); add(N * M); add(MM); add(MM);
   add((G + 1) * N * M); add(MM); add(MM); add(MM); add(MM);
   add((G + 1) * P.ldt);
+  add(G + 1);                                   // trial-energy terms
+  add((size_t)std::max(P.nu, P.nd) * M + 1);
   for (int sig = 0; sig < 2; ++sig) {
     const size_t ns = sig ? P.nd : P.nu;
     if (ns == 0) continue;
@@ -1241,7 +1264,6 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
                          const int32_t* od) {
   const int M = c->M;
   c->md = c->ndet > 1;
-  c->ref_only = false;
   std::vector<MdDet> dets_h;
   std::vector<double2> cconj_h;
   c->nact[0] = c->nu;
@@ -1548,6 +1570,13 @@ afqmc_status afqmc_green(afqmc_ctx* c, int32_t walker, double* G_up, double* G_d
         G[2 * ((size_t)i * M + j) + 1] = im;
       }
   }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_energy_shift(afqmc_ctx* c, double* e_shift) {
+  GUARD(c);
+  if (!e_shift) return fail(c, AFQMC_E_INVALID, "e_shift is NULL");
+  *e_shift = c->e_shift;
   return AFQMC_OK;
 }
 

@@ -69,6 +69,10 @@ struct afqmc_server {
   int64_t next_id = 0;
   std::map<int64_t, std::shared_ptr<Run>> runs;
   std::deque<std::shared_ptr<Run>> queue;
+  // correlated-sampling groups: members in submission order; a group is
+  // admitted whole once it has cs_size members, and is then closed
+  std::map<int32_t, std::vector<std::shared_ptr<Run>>> groups;
+  std::map<int32_t, bool> group_admitted;
   std::vector<std::shared_ptr<Run>> active;   // scheduler thread only
   std::vector<int> free_slots;
   std::vector<cudaStream_t> streams;
@@ -193,64 +197,91 @@ bool service(afqmc_server* S, Run& r) {
   return progress;
 }
 
-// Pick the next run to admit (under mu): the queue head if it fits, else the
-// first later run that fits while the head has been overtaken fewer than
-// kMaxBypass times.
-std::shared_ptr<Run> pick(afqmc_server* S) {
-  if (S->queue.empty() || S->free_slots.empty()) return nullptr;
-  auto fits = [&](const Run& r) { return S->in_use + r.resident + r.setup <= S->budget; };
+// The runs that admitting queued run r takes with it (under mu): r alone, or
+// its whole correlated-sampling group; empty while the group is incomplete.
+std::vector<std::shared_ptr<Run>> unit_of(afqmc_server* S, const std::shared_ptr<Run>& r) {
+  if (r->p.cs_group == 0) return {r};
+  const auto& m = S->groups[r->p.cs_group];
+  if ((int)m.size() < r->p.cs_size) return {};
+  return m;
+}
+
+bool unit_fits(afqmc_server* S, const std::vector<std::shared_ptr<Run>>& u) {
+  if (u.empty() || S->free_slots.size() < u.size()) return false;
+  size_t need = 0;
+  for (const auto& r : u) need += r->resident + r->setup;
+  return S->in_use + need <= S->budget;
+}
+
+// Pick the next runs to admit (under mu): the queue head's unit if it fits,
+// else the first later unit that fits while the head has been overtaken
+// fewer than kMaxBypass times. The picked runs leave the queue.
+std::vector<std::shared_ptr<Run>> pick(afqmc_server* S) {
+  if (S->queue.empty() || S->free_slots.empty()) return {};
+  auto take = [&](const std::vector<std::shared_ptr<Run>>& u) {
+    for (const auto& r : u) {
+      auto it = std::find(S->queue.begin(), S->queue.end(), r);
+      if (it != S->queue.end()) S->queue.erase(it);
+    }
+    if (u.front()->p.cs_group) S->group_admitted[u.front()->p.cs_group] = true;
+    return u;
+  };
   std::shared_ptr<Run> head = S->queue.front();
-  if (fits(*head)) {
-    S->queue.pop_front();
-    return head;
-  }
-  if (head->bypassed >= kMaxBypass) return nullptr;
+  std::vector<std::shared_ptr<Run>> u = unit_of(S, head);
+  if (unit_fits(S, u)) return take(u);
+  if (head->bypassed >= kMaxBypass) return {};
   for (auto it = S->queue.begin() + 1; it != S->queue.end(); ++it) {
-    if (fits(**it)) {
-      std::shared_ptr<Run> r = *it;
-      S->queue.erase(it);
+    u = unit_of(S, *it);
+    if (unit_fits(S, u)) {
       head->bypassed += 1;
-      return r;
+      return take(u);
     }
   }
-  return nullptr;
+  return {};
 }
 
 bool admit_one(afqmc_server* S) {
-  std::shared_ptr<Run> r;
+  std::vector<std::shared_ptr<Run>> unit;
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    r = pick(S);
-    if (!r) return false;
-    r->slot = S->free_slots.back();
-    S->free_slots.pop_back();
-    S->in_use += r->resident;
-    S->peak = std::max(S->peak, S->in_use + r->setup);
-    S->admitted += 1;
-    r->info.state = AFQMC_RUN_ACTIVE;
-    r->info.t_admit = S->now();
+    unit = pick(S);
+    if (unit.empty()) return false;
+    for (auto& r : unit) {
+      r->slot = S->free_slots.back();
+      S->free_slots.pop_back();
+      S->in_use += r->resident;
+      S->admitted += 1;
+      r->info.state = AFQMC_RUN_ACTIVE;
+      r->info.t_admit = S->now();
+    }
+    size_t setup = 0;
+    for (auto& r : unit) setup = std::max(setup, r->setup);
+    S->peak = std::max(S->peak, S->in_use + setup);
   }
-  afqmc_ctx* ctx = nullptr;
-  afqmc_status s = afqmc_create(&r->p, r->h1.data(), r->L.data(), r->Cu.data(), r->Cd.data(),
-                                r->ou.data(), r->od.data(), r->ci.data(),
-                                (void*)S->streams[r->slot], &ctx);
-  // the host copies of the inputs are no longer needed
-  std::vector<double>().swap(r->h1);
-  std::vector<double>().swap(r->L);
-  std::vector<double>().swap(r->Cu);
-  std::vector<double>().swap(r->Cd);
-  std::vector<double>().swap(r->ci);
-  if (s != AFQMC_OK) {
-    finish(S, *r, AFQMC_RUN_FAILED, s, afqmc_last_error(nullptr));
-    return true;
+  for (auto& r : unit) {
+    afqmc_ctx* ctx = nullptr;
+    afqmc_status s = afqmc_create(&r->p, r->h1.data(), r->L.data(), r->Cu.data(),
+                                  r->Cd.data(), r->ou.data(), r->od.data(), r->ci.data(),
+                                  (void*)S->streams[r->slot], &ctx);
+    // the host copies of the inputs are no longer needed
+    std::vector<double>().swap(r->h1);
+    std::vector<double>().swap(r->L);
+    std::vector<double>().swap(r->Cu);
+    std::vector<double>().swap(r->Cd);
+    std::vector<double>().swap(r->ci);
+    if (s != AFQMC_OK) {
+      finish(S, *r, AFQMC_RUN_FAILED, s, afqmc_last_error(nullptr));
+      continue;
+    }
+    r->ctx = ctx;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->active.push_back(r);
+      S->max_active_seen = std::max(S->max_active_seen, (int)S->active.size());
+    }
   }
-  r->ctx = ctx;
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->active.push_back(r);
-    S->max_active_seen = std::max(S->max_active_seen, (int)S->active.size());
-  }
-  service(S, *r);
+  for (auto& r : unit)
+    if (r->ctx) service(S, *r);
   return true;
 }
 
@@ -373,6 +404,25 @@ afqmc_status afqmc_server_submit(afqmc_server* S, const afqmc_params* p, const d
   r->info.t_done = -1;
   r->info.footprint = resident + setup;
   std::lock_guard<std::mutex> lk(S->mu);
+  if (p->cs_group != 0) {
+    if (S->group_admitted.count(p->cs_group))
+      return fail(AFQMC_E_INVALID, "correlated-sampling group already admitted");
+    auto& m = S->groups[p->cs_group];
+    if ((int)m.size() >= p->cs_size)
+      return fail(AFQMC_E_INVALID, "correlated-sampling group is full");
+    if (!m.empty()) {
+      const Run& f = *m.front();
+      const afqmc_params& q = f.p;
+      if (q.seed != p->seed || q.run_id != p->run_id || q.n_chol != p->n_chol ||
+          q.n_walkers != p->n_walkers || q.dtau != p->dtau || q.cs_size != p->cs_size ||
+          q.ortho_every != p->ortho_every || q.measure_every != p->measure_every ||
+          q.pc_every != p->pc_every || q.taylor_order != p->taylor_order ||
+          f.n_blocks != n_blocks || f.spb != steps_per_block)
+        return fail(AFQMC_E_INVALID,
+                    "correlated-sampling group members must share seed, run_id, n_chol, "
+                    "n_walkers, dtau, cadences, taylor_order, cs_size and the block plan");
+    }
+  }
   r->id = S->next_id++;
   r->info.t_submit = S->now();
   S->runs[r->id] = r;
@@ -384,8 +434,22 @@ afqmc_status afqmc_server_submit(afqmc_server* S, const afqmc_params* p, const d
     strncpy(r->info.message, "footprint exceeds the server's HBM budget",
             sizeof(r->info.message) - 1);
     S->failed += 1;
+    if (p->cs_group != 0) {   // the group can never be admitted whole: fail it
+      S->group_admitted[p->cs_group] = true;
+      for (auto& m : S->groups[p->cs_group]) {
+        auto it = std::find(S->queue.begin(), S->queue.end(), m);
+        if (it != S->queue.end()) S->queue.erase(it);
+        m->info.state = AFQMC_RUN_FAILED;
+        m->info.status = AFQMC_E_OOM;
+        m->info.t_done = S->now();
+        strncpy(m->info.message, "a member of its correlated-sampling group exceeds the budget",
+                sizeof(m->info.message) - 1);
+        S->failed += 1;
+      }
+    }
   } else {
     S->queue.push_back(r);
+    if (p->cs_group != 0) S->groups[p->cs_group].push_back(r);
   }
   *run_id = r->id;
   S->cv.notify_all();

@@ -36,6 +36,9 @@ struct TcCtx {
 namespace {
 
 constexpr int BM = 128, BK = 32;
+// K tiles (of BK values) the tensor core accumulates before the epilogue
+// drains the accumulator into FP32 registers.
+constexpr int kGemmChunkTiles = 4;
 
 // x rounded to the nearest TF32 value (10 explicit mantissa bits, the 13
 // low bits of the FP32 pattern cleared), so that x - tf32_hi(x) is exact in
@@ -55,8 +58,14 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 // ------------------------------------------------------------------ GEMM
 // Persistent: each CTA walks work items (output tile, K range) i = blockIdx.x,
 // blockIdx.x + gridDim.x, ...; the TMA -> MMA ring of stages runs on across
-// items, and the accumulator lives in one of two TMEM buffers so that the
-// epilogue of item j overlaps the main loop of item j + 1.
+// items. Within an item the tensor core accumulates at most kc K tiles
+// (kc * 32 values) into one TMEM accumulator; the epilogue drains each such
+// chunk into FP32 registers (round-to-nearest adds) and stores the item
+// after its last chunk. The tensor core's own accumulation rounds with a
+// bias that grows with the number of accumulated products (measured: a
+// relative error growing linearly with K, 2.3e-5 at K = 3600), which the
+// chunking bounds. The accumulator alternates between two TMEM buffers, so
+// the draining of one chunk overlaps the products of the next.
 // Warps: 0 TMA producer, 1 MMA issuer, 2-5 epilogue (TMEM lane quadrant =
 // warp % 4), 6-9 operand split (TF32X3 only).
 template <int BN, bool SPLIT3>
@@ -70,7 +79,7 @@ struct GemmCfg {
 };
 
 struct GemmWork {
-  int mt, nt, ktiles_total, ktiles_per_split, items;
+  int mt, nt, ktiles_total, ktiles_per_split, items, kc;
   __device__ void item(int i, int& m0, int& n0, int& z, int& kt0, int& nkt) const {
     const int tn = i % nt;
     const int rest = i / nt;
@@ -162,81 +171,100 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t id = idesc_tf32(BM, BN);
-      int it = 0, j = 0;
+      int it = 0, j = 0;                     // j counts accumulation chunks
       uint32_t last_bar = 0, last_par = 0;   // the latest commit, for the drain
-      for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x, ++j) {
+      for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x) {
         int m0, tn, z, kt0, nkt;
         wk.item(i, m0, tn, z, kt0, nkt);
-        const int acc = j & 1;
-        const uint32_t aph = (uint32_t)(j >> 1) & 1u;
-        if (j >= 2 && !mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
-          flag_timeout(status);
-          *fail = 1;
-          break;
-        }
-        fence_after_sync();
-        const uint32_t td = tmem + (uint32_t)(acc * BN);
-        for (int k = 0; k < nkt; ++k, ++it) {
-          const int s = it % S;
-          const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!mbar_wait(smem_u32(SPLIT3 ? &conv[s] : &full[s]), ph)) {
+        const int nch = nkt > 0 ? (nkt + wk.kc - 1) / wk.kc : 1;
+        for (int ch = 0; ch < nch && !*fail; ++ch, ++j) {
+          const int acc = j & 1;
+          const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+          if (j >= 2 && !mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
             flag_timeout(status);
             *fail = 1;
             break;
           }
           fence_after_sync();
-#pragma unroll
-          for (int ks = 0; ks < BK / 8; ++ks) {
-            const uint64_t ad = desc_sw128(smem_u32(a_hi(s)) + ks * 32);
-            const uint64_t bd = desc_sw128(smem_u32(b_hi(s)) + ks * 32);
-            mma_tf32(td, ad, bd, id, (k > 0 || ks > 0) ? 1u : 0u);
-            if (SPLIT3) {
-              mma_tf32(td, ad, desc_sw128(smem_u32(b_lo(s)) + ks * 32), id, 1u);
-              mma_tf32(td, desc_sw128(smem_u32(a_lo(s)) + ks * 32), bd, id, 1u);
+          const uint32_t td = tmem + (uint32_t)(acc * BN);
+          const int k_lo = ch * wk.kc, k_hi = min(nkt, k_lo + wk.kc);
+          for (int k = k_lo; k < k_hi; ++k, ++it) {
+            const int s = it % S;
+            const uint32_t ph = (uint32_t)(it / S) & 1u;
+            if (!mbar_wait(smem_u32(SPLIT3 ? &conv[s] : &full[s]), ph)) {
+              flag_timeout(status);
+              *fail = 1;
+              break;
             }
+            fence_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < BK / 8; ++ks) {
+              const uint64_t ad = desc_sw128(smem_u32(a_hi(s)) + ks * 32);
+              const uint64_t bd = desc_sw128(smem_u32(b_hi(s)) + ks * 32);
+              mma_tf32(td, ad, bd, id, (k > k_lo || ks > 0) ? 1u : 0u);
+              if (SPLIT3) {
+                mma_tf32(td, ad, desc_sw128(smem_u32(b_lo(s)) + ks * 32), id, 1u);
+                mma_tf32(td, desc_sw128(smem_u32(a_lo(s)) + ks * 32), bd, id, 1u);
+              }
+            }
+            mma_commit(smem_u32(&empty[s]));
+            last_bar = smem_u32(&empty[s]);
+            last_par = ph;
           }
-          mma_commit(smem_u32(&empty[s]));
-          last_bar = smem_u32(&empty[s]);
-          last_par = ph;
+          if (*fail) break;
+          mma_commit(smem_u32(&tfull[acc]));
+          last_bar = smem_u32(&tfull[acc]);
+          last_par = aph;
         }
-        mma_commit(smem_u32(&tfull[acc]));
-        last_bar = smem_u32(&tfull[acc]);
-        last_par = aph;
       }
       // no MMA may outlive the TMEM allocation: a commit arrives once every
       // earlier MMA of this thread has completed
       if (last_bar && !mbar_wait(last_bar, last_par)) flag_timeout(status);
     }
   } else if (warp < 6) {
-    // epilogue: TMEM lane quadrant q = warp % 4 holds rows 32q .. 32q + 31
+    // epilogue: TMEM lane quadrant q = warp % 4 holds rows 32q .. 32q + 31;
+    // each chunk's accumulator is added into sum[] (FP32, round to nearest)
     const int q = warp & 3;
     int j = 0;
-    for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x, ++j) {
+    float sum[BN];
+    for (int i = blockIdx.x; i < wk.items && !*fail; i += gridDim.x) {
       int m0, tn, z, kt0, nkt;
       wk.item(i, m0, tn, z, kt0, nkt);
       const int n0 = tn * BN;
-      const int acc = j & 1;
-      const uint32_t aph = (uint32_t)(j >> 1) & 1u;
-      const bool ok = mbar_wait(smem_u32(&tfull[acc]), aph);
-      if (!ok) {
-        flag_timeout(status);
-        *fail = 1;
-        break;
+      const int nch = nkt > 0 ? (nkt + wk.kc - 1) / wk.kc : 1;
+      bool ok = true;
+      for (int ch = 0; ch < nch; ++ch, ++j) {
+        const int acc = j & 1;
+        const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+        if (!mbar_wait(smem_u32(&tfull[acc]), aph)) {
+          flag_timeout(status);
+          *fail = 1;
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c0), v);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const float x = nkt == 0 ? 0.f : v[jj];
+            sum[c0 + jj] = ch == 0 ? x : sum[c0 + jj] + x;
+          }
+        }
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
       }
-      fence_after_sync();
+      if (!ok) break;
       const int row = m0 + 32 * q + lane;
       float* crow = C + (long)z * split_stride + (long)row * ldc;
       float* lrow = Clo ? Clo + (long)row * ldc : nullptr;
       const float* rrow = R ? R + (long)row * ldr : nullptr;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c0), v);
-        if (nkt == 0) {
+      if (row < m) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) v[jj] = 0.f;
-        }
-        if (row < m) {
+        for (int c0 = 0; c0 < BN; c0 += 32) {
           const int cb = n0 + c0;
           if (cb + 32 <= n && (ldc & 3) == 0 && (!rrow || (ldr & 3) == 0) &&
               ((uintptr_t)(crow + cb) & 15) == 0 &&
@@ -245,8 +273,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
 #pragma unroll
             for (int jj = 0; jj < 32; jj += 4) {
               float4 o;
-              o.x = alpha * v[jj]; o.y = alpha * v[jj + 1];
-              o.z = alpha * v[jj + 2]; o.w = alpha * v[jj + 3];
+              o.x = alpha * sum[c0 + jj]; o.y = alpha * sum[c0 + jj + 1];
+              o.z = alpha * sum[c0 + jj + 2]; o.w = alpha * sum[c0 + jj + 3];
               if (rrow) {
                 float4 r = *(const float4*)(rrow + cb + jj);
                 o.x += beta * r.x; o.y += beta * r.y; o.z += beta * r.z; o.w += beta * r.w;
@@ -262,10 +290,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
               *(float4*)(crow + cb + jj) = o;
             }
           } else {
+#pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
               const int col = cb + jj;
               if (col < n) {
-                float o = alpha * v[jj];
+                float o = alpha * sum[c0 + jj];
                 if (rrow) o += beta * rrow[col];
                 if (lrow) {
                   const float h = tf32_hi(o);
@@ -278,9 +307,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
           }
         }
       }
-      fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
     }
   } else if (SPLIT3) {
     // operand split: hi = x rounded to TF32 in place, lo = x - hi
@@ -1004,6 +1030,7 @@ cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const fl
   GemmWork wk;
   wk.ktiles_total = (k + BK - 1) / BK;
   wk.ktiles_per_split = (wk.ktiles_total + ksplit - 1) / ksplit;
+  wk.kc = kGemmChunkTiles;
   wk.mt = (m + BM - 1) / BM;
   wk.nt = (n + BN - 1) / BN;
   const long items = (long)wk.mt * wk.nt * ksplit;

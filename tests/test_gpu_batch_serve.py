@@ -275,3 +275,70 @@ def test_oversized_run_fails_without_blocking_the_queue():
     srv.close()
     assert ib["state"] == "failed" and ib["status"] == 2 and "budget" in ib["message"]
     assert is_["state"] == "done"
+
+
+# ------------------------------------------------------- correlated sampling
+def cs_pair(run_ids=(0, 0), W=512, measure=10, pc=0):
+    """Neutral (5+5) and cation (5+4) of the 10-orbital system, same
+    Hamiltonian and orbitals; equal run_ids mean shared field draws. Without
+    the comb (pc = 0) walker i of the neutral run and walker i of the cation
+    run see the same fields at every step."""
+    from synth import make_system
+    kw = dict(M=10, n_chol=40, ham_seed=0, l_kind="dense", l_sigma=0.05, trial="eig",
+              dtau=0.01, n_walkers=W, seed=17, ortho_every=5, measure_every=measure,
+              pc_every=pc)
+    neu = make_system("neutral", n_up=5, n_dn=5, run_id=run_ids[0], **kw)
+    cat = make_system("cation", n_up=5, n_dn=4, run_id=run_ids[1], **kw)
+    return neu, cat
+
+
+def test_correlated_sampling_reduces_the_variance_of_the_difference():
+    """Sec. V: with shared auxiliary-field paths the cation - neutral energy
+    difference fluctuates far less than with independent paths."""
+    out = {}
+    for label, ids in (("cs", (3, 3)), ("independent", (3, 4))):
+        neu, cat = cs_pair(ids)
+        e = []
+        for s in (neu, cat):
+            with ctx(s, precision="fp64") as c:
+                c.afqmc_propagate(600)
+                e.append(c.afqmc_energy_history()[:, 1])
+        d = (e[1] - e[0])[10:]           # after 1 Ha^-1
+        out[label] = float(np.var(d))
+    print("variance of the energy difference per measurement:", out)
+    assert out["cs"] < 0.25 * out["independent"]
+
+
+def test_server_admits_a_correlated_sampling_group_together():
+    from paper_1804_03310_gb300 import AfqmcError, Inputs, Server
+    neu, cat = cs_pair((5, 5), W=128, measure=10, pc=10)
+    other = mixed_system(seed=3, W=64)
+    srv = Server(max_active=8)
+    a = srv.afqmc_server_submit(Inputs.from_system(neu, precision="fp64", cs_group=9,
+                                                   cs_size=2), 2, 20)
+    b = srv.afqmc_server_submit(Inputs.from_system(other, precision="fp64"), 2, 20)
+    srv.afqmc_server_wait(b, 120)
+    assert srv.afqmc_server_poll(a)["state"] == "queued"   # waits for its partner
+    # a member that does not match the group is refused
+    bad = cat.replace(seed=99)
+    with pytest.raises(AfqmcError):
+        srv.afqmc_server_submit(Inputs.from_system(bad, precision="fp64", cs_group=9,
+                                                   cs_size=2), 2, 20)
+    c = srv.afqmc_server_submit(Inputs.from_system(cat, precision="fp64", cs_group=9,
+                                                   cs_size=2), 2, 20)
+    srv.afqmc_server_wait(-1, 120)
+    ia, ic = srv.afqmc_server_poll(a), srv.afqmc_server_poll(c)
+    assert ia["state"] == ic["state"] == "done"
+    assert ia["t_admit"] >= ic["t_submit"] and ic["t_admit"] >= ic["t_submit"]
+    with pytest.raises(AfqmcError):           # the group is closed once admitted
+        srv.afqmc_server_submit(Inputs.from_system(cat, precision="fp64", cs_group=9,
+                                                   cs_size=2), 2, 20)
+    # each member's blocks equal the same run alone
+    for info, s in ((ia, neu), (ic, cat)):
+        with ctx(s, precision="fp64") as alone:
+            alone.afqmc_propagate(40)
+            h = alone.afqmc_energy_history()
+        got = [blk["e_mixed"] for blk in info["blocks"]]
+        want = [h[h[:, 0] == blk["step"], 1][0] for blk in info["blocks"]]
+        assert got == want
+    srv.close()

@@ -36,6 +36,8 @@ def side_by_side(system, precision, n_steps, rtol, walkers=None, energy_at=(), *
     orc = O.OracleRun(system, walker_ids=walkers)
     e0, _ = gpu.afqmc_local_energy()
     assert abs(e0[0].real - orc.e_shift) <= rtol * max(1.0, abs(orc.e_shift))
+    # the shift itself is an FP64 setup quantity in every precision
+    assert abs(gpu.afqmc_energy_shift() - orc.e_shift) <= 1e-10 * max(1.0, abs(orc.e_shift))
     worst = run_side_by_side(gpu, orc, n_steps, rtol, walkers=walkers,
                              energy_at=energy_at, label=precision)
     gpu.close()
