@@ -734,18 +734,28 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+
+    def leg(key, fn):
+        # an optional leg that fails reports its error instead of ending the run
+        try:
+            line[key] = fn()
+        except Exception as e:  # noqa: BLE001
+            line[key] = {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+
     if not args.no_fp64_compare and world == 1 and args.precision != "fp64":
-        f64 = fp64_compare(args, s, hist)
-        f64["speedup"] = round(value / f64["value"], 2)
-        line["fp64_gpu"] = f64
+        def f64_leg():
+            f64 = fp64_compare(args, s, hist)
+            f64["speedup"] = round(value / f64["value"], 2)
+            return f64
+        leg("fp64_gpu", f64_leg)
     if not args.no_serving and world == 1:
-        line["serving"] = serving_leg(args.precision)
+        leg("serving", lambda: serving_leg(args.precision))
     if not args.no_shapes and world == 1 and args.precision != "fp64":
-        line["shapes"] = shapes_leg(args.precision)
-        line["fp64_islands"] = islands_leg(s, args.precision, value)
-        line["batch"] = batch_leg(args.precision)
-        line["ndet_sweep"] = ndet_leg(args.precision)
-        line["correlated_sampling"] = cs_leg(args.precision)
+        leg("shapes", lambda: shapes_leg(args.precision))
+        leg("fp64_islands", lambda: islands_leg(s, args.precision, value))
+        leg("batch", lambda: batch_leg(args.precision))
+        leg("ndet_sweep", lambda: ndet_leg(args.precision))
+        leg("correlated_sampling", lambda: cs_leg(args.precision))
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,

@@ -671,8 +671,7 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   TM(et_x, G + 1);
   TM(et_z, (size_t)std::max(c->nu, c->nd) * M + 1);
   std::vector<double> et_xh(G + 1);
-  LK(gemm<double>(st, false, true, G + 1, 1, N * M, 1.0, Ltil, (long)N * M, 0, PsiT,
-                  (long)N * M, 0, 0.0, et_x, 1, 0, 1));
+  LK(launch_gemv_rows(st, G + 1, (long)N * M, Ltil, (long)N * M, PsiT, et_x));
   CK(cudaMemcpyAsync(et_xh.data(), et_x, (G + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
   double e_exch = 0.0;
   // exchange part of the Eq. 5 tensor, per spin
@@ -690,8 +689,7 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     LK(launch_yx_permute(st, ns, M, gram, yx, c->Jp[sig]));
     {   // 1/2 theta^T Yx theta of the reference determinant, FP64
       std::vector<double> zh((size_t)J);
-      LK(gemm<double>(st, false, false, 1, (int)J, (int)J, 1.0, PsiT + (size_t)j0 * M, J, 0, yx,
-                      c->Jp[sig], 0, 0.0, et_z, J, 0, 1));
+      LK(launch_gemv_cols(st, J, J, yx, c->Jp[sig], PsiT + (size_t)j0 * M, et_z));
       CK(cudaMemcpyAsync(zh.data(), et_z, J * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       double q = 0.0;

@@ -132,6 +132,11 @@ cudaError_t launch_pad_rows(cudaStream_t st, long rows, long Jup, long Jdn,
                             const double* in, double* out, long ld, long dn_off);
 cudaError_t launch_transpose(cudaStream_t st, long rows, long cols, const double* in,
                              double* out, long ldo);
+// FP64 matrix-vector products: y = A x (rows of A) and y = x^T A (columns).
+cudaError_t launch_gemv_rows(cudaStream_t st, long rows, long cols, const double* A, long lda,
+                             const double* x, double* y);
+cudaError_t launch_gemv_cols(cudaStream_t st, long rows, long cols, const double* A, long lda,
+                             const double* x, double* y);
 // L [G][M*M] -> out [M*ldv][ldo], out[i ldv + k][g] = L[g][i M + k] (other
 // rows untouched).
 cudaError_t launch_transpose_pad(cudaStream_t st, long G, int M, long ldv, const double* in,

@@ -982,6 +982,32 @@ __global__ void transpose_pad_kernel(long G, int M, long ldv, const double* __re
   out[(i * ldv + k) * ldo + g] = in[e];
 }
 
+// y[r] = sum_c A[r][c] x[c] (FP64, one block per row).
+__global__ void gemv_rows_kernel(long cols, const double* __restrict__ A, long lda,
+                                 const double* __restrict__ x, double* __restrict__ y) {
+  __shared__ double red[256];
+  const long r = blockIdx.x;
+  double acc = 0.0;
+  for (long c = threadIdx.x; c < cols; c += blockDim.x) acc += A[r * lda + c] * x[c];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) y[r] = red[0];
+}
+
+// y[c] = sum_r x[r] A[r][c] (FP64, one thread per column).
+__global__ void gemv_cols_kernel(long rows, long cols, const double* __restrict__ A, long lda,
+                                 const double* __restrict__ x, double* __restrict__ y) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double acc = 0.0;
+  for (long r = 0; r < rows; ++r) acc += x[r] * A[r * lda + c];
+  y[c] = acc;
+}
+
 // out[i][j] = in[j][i] for an rows x cols matrix, into leading dimension ldo.
 __global__ void transpose_kernel(long rows, long cols, const double* __restrict__ in,
                                  double* __restrict__ out, long ldo) {
@@ -1219,6 +1245,20 @@ cudaError_t launch_pad_rows(cudaStream_t st, long rows, long Jup, long Jdn,
                             const double* in, double* out, long ld, long dn_off) {
   pad_rows_kernel<<<blocks_for(rows * (Jup + Jdn), 256), 256, 0, st>>>(rows, Jup, Jdn, in,
                                                                      out, ld, dn_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_rows(cudaStream_t st, long rows, long cols, const double* A, long lda,
+                             const double* x, double* y) {
+  if (rows <= 0) return cudaSuccess;
+  gemv_rows_kernel<<<(unsigned)rows, 256, 0, st>>>(cols, A, lda, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_cols(cudaStream_t st, long rows, long cols, const double* A, long lda,
+                             const double* x, double* y) {
+  if (cols <= 0) return cudaSuccess;
+  gemv_cols_kernel<<<blocks_for(cols, 256), 256, 0, st>>>(rows, cols, A, lda, x, y);
   return cudaGetLastError();
 }
 
