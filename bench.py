@@ -79,20 +79,24 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
-def roofline_for(kernel_stats, precision, peaks, src, s, workload_name):
-    """Dominant kernel of the timed region against its bound. For M > 64 the
-    Taylor series runs on the CUDA cores (between two half-step GEMMs), so
-    the propagate group is rated against the FP32 CUDA-core peak there."""
+def roofline_for(kernel_stats, precision, peaks, src, s, workload_name, taylor_fused=None):
+    """Dominant kernel of the timed region against its bound. The propagate
+    group runs on the tensor cores unless the propagation path is the
+    CUDA-core series (taylor_fused = 0; when the path is not given, the
+    CUDA-core series is assumed above M = 64), where it is rated against the
+    FP32 CUDA-core peak. BF16X3 propagates with BF16 products (BF16 peak);
+    its other contractions are TF32X3 (TF32 peak)."""
     best = max(kernel_stats.items(), key=lambda kv: kv[1]["total_ms"])
     name, st = best
     avg_s = st["total_ms"] / max(1, st["launches"]) / 1e3
-    tensor_groups = ("force_bias", "one_body", "energy") + (("propagate",) if s.M <= 64 else ())
+    prop_tc = (taylor_fused != 0) if taylor_fused is not None else s.M <= 64
+    tensor_groups = ("force_bias", "one_body", "energy") + (("propagate",) if prop_tc else ())
     if st["is_bytes"]:
         bound, unit = "hbm", "GB/s"
         achieved = st["work"] / avg_s / 1e9
         peak = peaks["hbm_gbs"]
         peak_src = f"hbm_gbs ({src})"
-    elif precision in ("tf32", "tf32x3") and name not in tensor_groups:
+    elif precision in ("tf32", "tf32x3", "bf16x3") and name not in tensor_groups:
         # the small inverses, QR and field draws run on the CUDA cores in FP32
         bound, unit = "alu", "TFLOP/s"
         achieved = st["work"] / avg_s / 1e12
@@ -108,6 +112,11 @@ def roofline_for(kernel_stats, precision, peaks, src, s, workload_name):
         achieved = st["work"] / avg_s / 1e12
         peak = FP32_SIMT_TFLOPS
         peak_src = "FP32 SIMT: 152 SM x 128 lanes x 2 x 2070 MHz"
+    elif precision == "bf16x3" and name == "propagate":
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = st["work"] / avg_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        peak_src = f"bf16 sustained ({src})"
     else:
         bound, unit = "tensor", "TFLOP/s"
         achieved = st["work"] / avg_s / 1e12
@@ -317,6 +326,8 @@ def _timed(args, s, stream, rank, world):
     from paper_1804_03310_gb300 import KERNEL_IDS
     kstats = {k: ctx.afqmc_kernel_stats(k) for k in KERNEL_IDS}
     kstats = {k: v for k, v in kstats.items() if v["launches"] > 0}
+    kstats["_taylor_fused"] = ctx.afqmc_get_tuning().get("taylor_fused") if args.precision in (
+        "tf32", "tf32x3", "bf16x3") else 0
     ctx.afqmc_synchronize()
     hist = ctx.afqmc_energy_history()
     ctx.close()
@@ -693,7 +704,8 @@ def shapes_leg(precision):
 
 
 def dtype_of(precision):
-    return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[precision]
+    return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3",
+            "bf16x3": "bf16x3"}[precision]
 
 
 def main():
@@ -711,6 +723,7 @@ def main():
     if rank != 0:
         return 0
     peaks, src = load_peaks()
+    fused = kstats.pop("_taylor_fused", None)
     value = whole_job_value(s.n_walkers * BLOCK * args.steps, world, total_ms)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
@@ -727,7 +740,7 @@ def main():
                    "l2": "flushed (256 MB write) between timed iterations",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gpu_launches": int(launches),
-        "roofline": roofline_for(kstats, args.precision, peaks, src, s, args.workload),
+        "roofline": roofline_for(kstats, args.precision, peaks, src, s, args.workload, fused),
         "kernels_ms": {k: round(v["total_ms"], 3) for k, v in kstats.items()},
         "clocks": clocks,
         "energy_last": float(hist[-1][1]) if len(hist) else None,

@@ -55,16 +55,24 @@ typedef enum {
  * FP32:    complex64 walkers, FP32 SIMT contractions.
  * TF32:    complex64 walkers, dense contractions on tcgen05 tensor cores with
  *          TF32 operands and FP32 accumulation.
- * TF32X3:  as TF32 with split (hi + lo) operands, three products per term.
+ * TF32X3:  as TF32 with split (hi + lo) operands, three products per term;
+ *          the tensor core accumulates at most 128 K values before the sum
+ *          continues in FP32 registers.
+ * BF16X3:  the propagation (Taylor series and both half steps) with BF16
+ *          hi + lo operands, three BF16 products per term, FP32
+ *          accumulation; the force-bias, one-body-operator and energy
+ *          contractions, which feed the weights and the energy directly,
+ *          as in TF32X3.
  * The reduced modes keep FP64 for walker weights, the accumulation of
- * log-determinants and ln det R, and the population-control prefix sums;
- * params.fp64_islands moves the small inverse and Gram-Schmidt arithmetic
- * to FP64 as well. */
+ * log-determinants and ln det R, the population-control prefix sums and the
+ * energy shift E_T; params.fp64_islands moves the small inverse and
+ * Gram-Schmidt arithmetic to FP64 as well. */
 typedef enum {
   AFQMC_FP64 = 0,
   AFQMC_FP32 = 1,
   AFQMC_TF32 = 2,
-  AFQMC_TF32X3 = 3
+  AFQMC_TF32X3 = 3,
+  AFQMC_BF16X3 = 4
 } afqmc_precision;
 
 typedef struct {
@@ -227,7 +235,7 @@ afqmc_status afqmc_kernel_stats(afqmc_ctx* ctx, int32_t kernel_id,
  * counting each kernel of a replayed graph. */
 int64_t afqmc_launch_count(const afqmc_ctx* ctx);
 
-/* Launch shapes of the tensor-core modes (TF32, TF32X3). Shapes change the
+/* Launch shapes of the tensor-core modes (TF32, TF32X3, BF16X3). Shapes change the
  * numerics only through the order of FP32 sums (split K) and through the
  * propagation path (taylor_fused below);
  * every choice meets the same tolerance against the FP64 path. In the FP64

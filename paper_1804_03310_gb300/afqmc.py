@@ -15,9 +15,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libafqmc.so")
 
-AFQMC_FP64, AFQMC_FP32, AFQMC_TF32, AFQMC_TF32X3 = 0, 1, 2, 3
+AFQMC_FP64, AFQMC_FP32, AFQMC_TF32, AFQMC_TF32X3, AFQMC_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": AFQMC_FP64, "fp32": AFQMC_FP32, "tf32": AFQMC_TF32,
-              "tf32x3": AFQMC_TF32X3}
+              "tf32x3": AFQMC_TF32X3, "bf16x3": AFQMC_BF16X3}
 STATUS = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_POPULATION",
           5: "E_TIMEOUT", 6: "E_NUMERIC", 7: "E_STATE"}
 KERNEL_IDS = ["force_bias", "fields", "one_body", "propagate", "overlap",

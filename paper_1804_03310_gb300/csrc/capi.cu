@@ -111,6 +111,7 @@ struct afqmc_ctx {
   bool tc_bhalf_ok;   // M % 4 == 0: B_half on the tensor cores
   bool tc_wide_ok;    // M > 64: the wide tensor-core Taylor kernel (operator streamed by TMA)
   bool split3;
+  bool bf16;          // BF16X3: propagation (series and half steps) in BF16 hi + lo
   int taylor_fused;   // 0: CUDA-core series; 1: fused tensor-core kernel with the
                       // half steps; 2: tensor-core series, half steps as GEMMs;
                       // 3: wide tensor-core kernel with the half steps (M > 64)
@@ -391,15 +392,14 @@ afqmc_status propagate_T(afqmc_ctx* c, T* out) {
   const int W = c->W, N = c->N, M = c->M;
   const int rows = W * N * 2;
   if (c->tc && c->taylor_fused == 3) {   // operator streamed by TMA, half steps fused
-    LK(tc_taylor_wide(c->tc, c->st, W, M, N, c->p.taylor_order, c->ldV, (const float*)c->V,
-                      (const float*)c->Vlo, (const float*)c->dBp, (const float*)c->dBp_lo,
-                      (const float*)c->Phi, (float*)out, c->split3, c->status));
+    LK(tc_taylor_wide(c->tc, c->st, W, M, N, c->p.taylor_order, c->ldV, c->V, c->Vlo, c->dBp,
+                      c->dBp_lo, (const float*)c->Phi, (float*)out, c->split3, c->bf16,
+                      c->status));
     return AFQMC_OK;
   }
   if (c->tc && c->taylor_fused == 1) {   // B_half exp(V) B_half in one tensor-core kernel, in place
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
-                 (const float*)c->Phi, (float*)out, (const float*)c->bimg, c->split3,
-                 c->status));
+                 (const float*)c->Phi, (float*)out, c->bimg, c->split3, c->bf16, c->status));
     return AFQMC_OK;
   }
   // Phi2 = B_half Phi
@@ -419,7 +419,8 @@ afqmc_status propagate_T(afqmc_ctx* c, T* out) {
   // Phi3 = exp_T(V) Phi2
   if (c->tc && c->taylor_fused == 2) {
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
-                 (const float*)c->Phi2, (float*)c->Phi3, nullptr, c->split3, c->status));
+                 (const float*)c->Phi2, (float*)c->Phi3, nullptr, c->split3, c->bf16,
+                 c->status));
   } else {
     LK(launch_taylor<T>(c->st, W, M, N, c->p.taylor_order, (const T*)c->V, c->ldV,
                         (const T*)c->Phi2, (T*)c->Phi3));
@@ -460,7 +461,8 @@ afqmc_status step_T(afqmc_ctx* c) {
       LK(tc_gemm(c->tc, c->st, 2 * W, (int)nv, G, (const float*)c->S, c->ldS,
                  (const float*)c->LT, c->ldS, (float*)c->V, nv, 1.0f, 0.0f, nullptr, 0,
                  c->split3, 1, 0, c->status, c->bn_v, (const float*)c->LT_lo,
-                 c->taylor_fused == 3 && c->split3 ? (float*)c->Vlo : nullptr));
+                 c->taylor_fused == 3 && c->split3 ? (float*)c->Vlo : nullptr,
+                 c->taylor_fused == 3 && c->bf16));
     } else {
       LK(gemm<T>(c->st, false, false, 2 * W, M * M, G, T(1), (const T*)c->S, c->ldS, 0,
                  (const T*)c->L, (long)M * M, 0, T(0), (T*)c->V, (long)M * M, 0, 1));
@@ -528,7 +530,7 @@ afqmc_status validate_sizes(const afqmc_params* p) {
   if (!(p->dtau > 0.0)) return fail(c, AFQMC_E_INVALID, "dtau must be > 0");
   if (p->taylor_order < 1 || p->taylor_order > 12)
     return fail(c, AFQMC_E_INVALID, "taylor_order must be in 1..12");
-  if (p->precision < AFQMC_FP64 || p->precision > AFQMC_TF32X3)
+  if (p->precision < AFQMC_FP64 || p->precision > AFQMC_BF16X3)
     return fail(c, AFQMC_E_INVALID, "unknown precision");
   if (p->run_id < 0 || p->run_id >= (1 << 29)) return fail(c, AFQMC_E_INVALID, "run_id out of range");
   if (p->ortho_every < 0 || p->measure_every < 0 || p->pc_every < 0)
@@ -717,15 +719,19 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     LK(launch_add_diag(st, M, tb, -1.0));
     LK(launch_convert<T>(st, MM, tb, (T*)c->dB));
     if (c->bimg)
-      LK(tc_bhalf_image(st, M, (const float*)c->dB, (float*)c->bimg, c->split3));
-    if (c->dBp) {   // rows padded to ldV (TMA), then split for TF32X3
+      LK(tc_bhalf_image(st, M, (const float*)c->dB, c->bimg, c->split3, c->bf16));
+    if (c->dBp) {   // rows padded to ldV (TMA), then split for TF32X3 / BF16X3
       double* pad;
       TM(pad, (size_t)M * c->ldV);
       CK(cudaMemsetAsync(pad, 0, (size_t)M * c->ldV * sizeof(double), st));
       LK(launch_pad_rows(st, M, M, 0, tb, pad, c->ldV, c->ldV));
-      LK(launch_convert<T>(st, (long)M * c->ldV, pad, (T*)c->dBp));
-      if (c->dBp_lo)
-        LK(tc_split(st, (long)M * c->ldV, (float*)c->dBp, (float*)c->dBp_lo));
+      if (c->bf16) {
+        LK(tc_split_bf16(st, (long)M * c->ldV, pad, c->dBp, c->dBp_lo));
+      } else {
+        LK(launch_convert<T>(st, (long)M * c->ldV, pad, (T*)c->dBp));
+        if (c->dBp_lo)
+          LK(tc_split(st, (long)M * c->ldV, (float*)c->dBp, (float*)c->dBp_lo));
+      }
     }
   }
   if (c->split3) {   // the constant operands of the TF32X3 contractions, split once
@@ -952,7 +958,8 @@ afqmc_status autotune(afqmc_ctx* c) {
         LK(tc_gemm(c->tc, c->st, 2 * W, (int)nv, G, (const float*)c->S, c->ldS,
                    (const float*)c->LT, c->ldS, (float*)c->V, nv, 1.0f, 0.0f, nullptr, 0,
                    c->split3, 1, 0, c->status, bn, (const float*)c->LT_lo,
-                   c->tc_wide_ok && c->split3 ? (float*)c->Vlo : nullptr));
+                   c->tc_wide_ok && c->split3 ? (float*)c->Vlo : nullptr,
+                   c->tc_wide_ok && c->bf16));
         return AFQMC_OK;
       });
       if (ms < best) { best = ms; v.bn_v = bn; }
@@ -1094,7 +1101,7 @@ void advance_host(afqmc_ctx* c, long len, const GraphEntry* ge) {
 // active-orbital counts of a multi-determinant trial).
 struct Plan {
   int M, nu, nd, N, G, W, ndet, nact[2];
-  bool fp64, tcmode, split3, md, tc_taylor_ok, tc_bhalf_ok, tc_wide_ok;
+  bool fp64, tcmode, split3, bf16, md, tc_taylor_ok, tc_bhalf_ok, tc_wide_ok;
   size_t es;
   long ldS, ldx, dn_off, ldt, Jp[2], gdn_off, ldg, ldV;
   int xsplit, xsplit_max;
@@ -1108,12 +1115,15 @@ Plan make_plan(const afqmc_params* p, int nact_up, int nact_dn) {
   P.nact[0] = P.md ? nact_up : P.nu;
   P.nact[1] = P.md ? nact_dn : P.nd;
   P.fp64 = p->precision == AFQMC_FP64;
-  P.tcmode = p->precision == AFQMC_TF32 || p->precision == AFQMC_TF32X3;
-  P.split3 = p->precision == AFQMC_TF32X3;
+  P.tcmode = p->precision == AFQMC_TF32 || p->precision == AFQMC_TF32X3 ||
+             p->precision == AFQMC_BF16X3;
+  P.bf16 = p->precision == AFQMC_BF16X3;
+  P.split3 = p->precision == AFQMC_TF32X3 || P.bf16;
   P.tc_taylor_ok = P.tcmode && P.M <= 64;
   P.tc_bhalf_ok = P.tcmode && P.M % 4 == 0;
   P.tc_wide_ok = P.tcmode && P.M > 64;
-  P.ldV = P.tc_wide_ok ? round4(P.M) : P.M;
+  // rows of V 16-byte aligned for the TMA: 4 FP32 or 8 BF16 values
+  P.ldV = P.tc_wide_ok ? (P.bf16 ? (P.M + 7) / 8 * 8 : round4(P.M)) : P.M;
   P.es = P.fp64 ? sizeof(double) : sizeof(float);
   const int M = P.M, G = P.G, W = P.W;
   P.ldS = round4(G);
@@ -1191,7 +1201,7 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
     add(&c->Yx_dn_lo, (size_t)P.nd * M * P.Jp[1] * es);
   }
   if (!P.fp64) add(&c->dB, MM * es);
-  if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_floats(P.split3) * sizeof(float));
+  if (P.tc_taylor_ok) add(&c->bimg, tc_bhalf_image_bytes(P.split3, P.bf16));
   if (P.tc_wide_ok) {
     add(&c->dBp, M * P.ldV * es);
     if (P.split3) {
@@ -1282,6 +1292,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   c->xsplit = P.xsplit;
   c->xsplit_max = P.xsplit_max;
   c->split3 = P.split3;
+  c->bf16 = P.bf16;
   c->tc_taylor_ok = P.tc_taylor_ok;
   c->tc_bhalf_ok = P.tc_bhalf_ok;
   c->tc_wide_ok = P.tc_wide_ok;

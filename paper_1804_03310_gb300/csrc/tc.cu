@@ -99,7 +99,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                const __grid_constant__ CUtensorMap mapBlo, int m, int n, GemmWork wk,
                float* __restrict__ C, long ldc, float alpha,
                float beta, const float* __restrict__ R, long ldr, long split_stride,
-               int* status, float* __restrict__ Clo) {
+               int* status, float* __restrict__ Clo, int out_bf16) {
   using Cfg = GemmCfg<BN, SPLIT3>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -262,7 +262,43 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       float* crow = C + (long)z * split_stride + (long)row * ldc;
       float* lrow = Clo ? Clo + (long)row * ldc : nullptr;
       const float* rrow = R ? R + (long)row * ldr : nullptr;
-      if (row < m) {
+      if (row < m && out_bf16) {
+        // split output in BF16: C and Clo are BF16 arrays (hi, lo parts)
+        uint16_t* bh = (uint16_t*)C + (long)row * ldc;
+        uint16_t* bl = (uint16_t*)Clo + (long)row * ldc;
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          const int cb = n0 + c0;
+          if (cb + 32 <= n && (ldc & 7) == 0 && ((uintptr_t)(bh + cb) & 15) == 0 &&
+              ((uintptr_t)(bl + cb) & 15) == 0) {
+#pragma unroll
+            for (int jj = 0; jj < 32; jj += 8) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                uint16_t h0, l0, h1, l1;
+                bf16_split(alpha * sum[c0 + jj + 2 * u], h0, l0);
+                bf16_split(alpha * sum[c0 + jj + 2 * u + 1], h1, l1);
+                hw[u] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                lw[u] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+              }
+              *(uint4*)(bh + cb + jj) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *(uint4*)(bl + cb + jj) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int col = cb + jj;
+              if (col < n) {
+                uint16_t h, l;
+                bf16_split(alpha * sum[c0 + jj], h, l);
+                bh[col] = h;
+                bl[col] = l;
+              }
+            }
+          }
+        }
+      } else if (row < m) {
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 32) {
           const int cb = n0 + c0;
@@ -682,6 +718,248 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
+// ------------------------------------------------------ Taylor, BF16X3
+// The on-chip series of tc_taylor_kernel (M <= 64, real 2M-row operator in
+// tensor memory, one walker chunk of 64 columns per work item, half steps
+// fused) with BF16 hi + lo operands and three kind::f16 products per term.
+// BF16 halves every operand: the operator's hi and lo parts take 64 TMEM
+// columns each (two K values per 32-bit column), the term 16 KB per part in
+// shared memory, the half-step image 32 KB per part. With 192 TMEM columns
+// and 97 KB of shared memory per CTA, two CTAs share an SM, so one walker's
+// products overlap the other's epilogue.
+constexpr int TB_A_BYTES = 128 * 128 * 2;     // half-step image part, 2 K-blocks of 64
+constexpr int TB_B_BYTES = 64 * 128 * 2;      // term part, 64 columns x 128 K
+constexpr int TB_SMEM = 2 * TB_A_BYTES + 2 * TB_B_BYTES + 1024 + 128;
+constexpr uint32_t TB_TMEM_AHI = 64, TB_TMEM_ALO = 128, TB_TMEM_COLS = 256;
+
+// (B_half - I) image in BF16: hi part then lo part, 128 x 128 each, K-major
+// SW128 with 64 K values per row block.
+__global__ void bhalf_image_bf16_kernel(int M, const float* __restrict__ dB,
+                                        uint16_t* __restrict__ img) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 128 * 128) return;
+  const int r = e / 128, k = e % 128;
+  const int rc = r >> 6, rr = r & 63, kc = k >> 6, kk = k & 63;
+  float x = 0.f;
+  if (rc == kc && rr < M && kk < M) x = dB[rr * M + kk];
+  const uint32_t off = sw128_offset_bf16(r, k, 128) / 2;
+  uint16_t h, l;
+  bf16_split(x, h, l);
+  img[off] = h;
+  img[128 * 128 + off] = l;
+}
+
+__device__ __forceinline__ void put_operand_bf16(uint32_t shi, uint32_t slo, uint32_t off,
+                                                 float x) {
+  uint16_t h, l;
+  bf16_split(x, h, l);
+  st_shared_b16(shi + off, h);
+  st_shared_b16(slo + off, l);
+}
+
+__global__ void __launch_bounds__(128, 2)
+tc_taylor_bf16_kernel(int W, int M, int N, int order, const float* __restrict__ V,
+                      const float* Pin, float* Pout, const uint16_t* __restrict__ dB_img,
+                      int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* Ihi = base;                      // image hi, lo adjacent (one bulk copy)
+  unsigned char* Bhi = base + 2 * TB_A_BYTES;
+  unsigned char* Blo = Bhi + TB_B_BYTES;
+  uint64_t* bar = (uint64_t*)(Blo + TB_B_BYTES);
+  uint64_t* lbar = bar + 1;
+  uint32_t* tslot = (uint32_t*)(bar + 2);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int nchunk = (N + 63) / 64;
+  const int items = W * nchunk;
+  const bool fuse_b = dB_img != nullptr;
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(smem_u32(bar), 1);
+    mbar_init(smem_u32(lbar), 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tslot), TB_TMEM_COLS);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t tAhi = tmem + TB_TMEM_AHI, tAlo = tmem + TB_TMEM_ALO;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const uint32_t id = idesc_bf16(128, 64);
+  uint32_t phase = 0;
+  const int r = tid;                       // embedded row / K index owned
+  const int rc = r >> 6, rr = r & 63;      // component (0 re, 1 im), orbital row
+  const uint32_t sIhi = smem_u32(Ihi), sIlo = sIhi + TB_A_BYTES;
+  const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+  const int MM = M * M;
+
+  auto wait_mma = [&]() {
+    const bool ok = mbar_wait(smem_u32(bar), phase);
+    phase ^= 1u;
+    if (!ok) {
+      flag_timeout(status);
+      s_fail = 1;
+    }
+    fence_after_sync();
+  };
+  auto sync_for_mma = [&]() {
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  };
+  // D (+)= image x term (both in shared memory), three products per K step
+  auto half_products = [&]() {
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {
+      const int kb = ks >> 2, koff = (ks & 3) * 32;
+      const uint64_t ad = desc_sw128(sIhi + kb * 16384 + koff);
+      const uint64_t bd = desc_sw128(sBhi + kb * 8192 + koff);
+      mma_bf16(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
+      mma_bf16(tmem, ad, desc_sw128(sBlo + kb * 8192 + koff), id, 1u);
+      mma_bf16(tmem, desc_sw128(sIlo + kb * 16384 + koff), bd, id, 1u);
+    }
+  };
+  // D = operator (tensor memory) x term (shared memory)
+  auto series_products = [&]() {
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {
+      const int kb = ks >> 2, koff = (ks & 3) * 32;
+      const uint64_t bd = desc_sw128(sBhi + kb * 8192 + koff);
+      mma_bf16_ts(tmem, tAhi + 8 * ks, bd, id, ks > 0 ? 1u : 0u);
+      mma_bf16_ts(tmem, tAhi + 8 * ks, desc_sw128(sBlo + kb * 8192 + koff), id, 1u);
+      mma_bf16_ts(tmem, tAlo + 8 * ks, bd, id, 1u);
+    }
+  };
+  bool img_pending = false;
+  if (fuse_b) {                            // the half-step image, once per CTA
+    if (tid == 0) {
+      mbar_arrive_expect_tx(smem_u32(lbar), 2u * TB_A_BYTES);
+      bulk_load(sIhi, dB_img, 2u * TB_A_BYTES, smem_u32(lbar));
+    }
+    img_pending = true;
+  }
+
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int w = item / nchunk;
+    const int j0 = (item - w * nchunk) * 64;
+    const int nc = min(64, N - j0);
+    const float* Vw = V + (long)w * 2 * MM;
+    float acc[64];
+    const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
+#pragma unroll
+    for (int j = 0; j < 64; ++j)
+      acc[j] = (j < nc && rr < M) ? Pw[((long)j * 2 + rc) * M + rr] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 64; ++j)
+      put_operand_bf16(sBhi, sBlo, sw128_offset_bf16(j, r, 64), acc[j]);
+    if (fuse_b) {                          // t0 = Phi + dB Phi
+      if (img_pending) {
+        if (!mbar_wait(smem_u32(lbar), 0)) {
+          flag_timeout(status);
+          s_fail = 1;
+        }
+        img_pending = false;
+      }
+      sync_for_mma();
+      if (tid == 0) {
+        half_products();
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          acc[c0 + j] += v[j];
+          put_operand_bf16(sBhi, sBlo, sw128_offset_bf16(c0 + j, r, 64), acc[c0 + j]);
+        }
+      }
+    }
+    // the operator into tensor memory: row r of [[Vr, -Vi], [Vi, Vr]] as BF16
+    // hi and lo parts, two K values per 32-bit column (lower K in the low half)
+#pragma unroll 1
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      const int half = c0 >> 6, k0 = c0 & 63;
+      const int plane = half == 0 ? rc : 1 - rc;
+      const float sgn = (rc == 0 && half == 1) ? -1.f : 1.f;
+      const float* src = Vw + (long)plane * MM + (long)rr * M;
+      float hw[16], lw[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int ka = k0 + 2 * u, kb2 = ka + 1;
+        const float xa = (rr < M && ka < M) ? sgn * src[ka] : 0.f;
+        const float xb = (rr < M && kb2 < M) ? sgn * src[kb2] : 0.f;
+        uint16_t ha, la, hb, lb;
+        bf16_split(xa, ha, la);
+        bf16_split(xb, hb, lb);
+        hw[u] = __uint_as_float((uint32_t)ha | ((uint32_t)hb << 16));
+        lw[u] = __uint_as_float((uint32_t)la | ((uint32_t)lb << 16));
+      }
+      tmem_st16(tAhi + lane_base + (uint32_t)(c0 >> 1), hw);
+      tmem_st16(tAlo + lane_base + (uint32_t)(c0 >> 1), lw);
+    }
+    tmem_wait_st();
+    for (int term = 1; term <= order; ++term) {
+      sync_for_mma();
+      if (tid == 0) {
+        series_products();
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
+      const float inv = 1.0f / (float)term;
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float x = v[j] * inv;
+          acc[c0 + j] += x;
+          if (term < order || fuse_b)
+            put_operand_bf16(sBhi, sBlo, sw128_offset_bf16(c0 + j, r, 64),
+                             term < order ? x : acc[c0 + j]);
+        }
+      }
+    }
+    if (fuse_b) {                          // out = s + dB s
+      sync_for_mma();
+      if (tid == 0) {
+        half_products();
+        mma_commit(smem_u32(bar));
+      }
+      wait_mma();
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[c0 + j] += v[j];
+      }
+    }
+    float* Ow = Pout + ((long)w * N + j0) * 2 * M;
+    if (rr < M) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j)
+        if (j < nc) Ow[((long)j * 2 + rc) * M + rr] = acc[j];
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (s_fail) break;
+  }
+  if (img_pending && !mbar_wait(smem_u32(lbar), 0)) flag_timeout(status);
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TB_TMEM_COLS);
+}
+
 // ------------------------------------------------------------ wide Taylor
 // B_half exp_T(V) B_half Phi for 64 < M <= 256 (Sec. II, Thouless propagation
 // by matrix products), where the operator no longer fits on chip: each CTA
@@ -698,13 +976,16 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
 // Di = Pi + Qr. Rows and K indices past M are zero-filled by the TMA.
 // TF32X3: A arrives pre-split (hi and lo planes in global memory); the
 // epilogue writes t as hi and lo planes; three products per MMA step.
+// BF16X3 (BF): the same with BF16 hi and lo parts (kind::f16 MMAs, 64 K
+// values per 128-byte row, so a stage covers twice the K range and the
+// streamed operand half the bytes).
 // Warps: 0 TMA producer, 1 MMA issuer, 2..9 epilogue (TMEM lane quadrant =
 // warp % 4; group (warp - 2) / 4 takes the second row tile, or the second
 // half of the columns when there is one row tile).
 constexpr int TW_THREADS = 320;
 constexpr int TW_TILE_BYTES = 128 * 32 * 4;   // one 128 x 32 fp32 operand tile
 
-template <bool SPLIT3>
+template <bool SPLIT3, bool BF>
 __global__ void __launch_bounds__(TW_THREADS, 1)
 tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
                       const __grid_constant__ CUtensorMap mapVlo,
@@ -713,7 +994,8 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
                       int order, int n16, int S, const float* Pin, float* Pout, int* status) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int MT = (M + 127) / 128, KB = (M + 31) / 32;
+  constexpr int KBLK = BF ? 64 : 32;                   // K values per 128-byte row
+  const int MT = (M + 127) / 128, KB = (M + KBLK - 1) / KBLK;
   const int P = SPLIT3 ? 2 : 1;
   const int kb_bytes = 2 * n16 * 128;                 // one K block of B
   const int b_bytes = KB * kb_bytes;
@@ -776,10 +1058,10 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
                 mbar_arrive_expect_tx(smem_u32(&full[s]), (uint32_t)stage_bytes);
                 const int z = half ? 0 : 2 * w + pl;
                 tma_load_3d(smem_u32(st), half ? (const void*)&mapB : (const void*)&mapV,
-                            kb * 32, mt * 128, z, smem_u32(&full[s]));
+                            kb * KBLK, mt * 128, z, smem_u32(&full[s]));
                 if (SPLIT3)
                   tma_load_3d(smem_u32(st + TW_TILE_BYTES),
-                              half ? (const void*)&mapBlo : (const void*)&mapVlo, kb * 32,
+                              half ? (const void*)&mapBlo : (const void*)&mapVlo, kb * KBLK,
                               mt * 128, z, smem_u32(&full[s]));
               }
         }
@@ -790,8 +1072,12 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t id = idesc_tf32(128, 2 * n16);
+      const uint32_t id = BF ? idesc_bf16(128, 2 * n16) : idesc_tf32(128, 2 * n16);
       const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+      auto mma = [&](uint32_t td, uint64_t a, uint64_t b, uint32_t acc) {
+        if (BF) mma_bf16(td, a, b, id, acc);
+        else mma_tf32(td, a, b, id, acc);
+      };
       int it = 0;
       uint32_t pb = 0, pa = 0;
       uint32_t last_bar = 0, last_par = 0;
@@ -823,10 +1109,10 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
                 for (int ks = 0; ks < 4; ++ks) {
                   const uint64_t ad = desc_sw128(sa + ks * 32);
                   const uint64_t bd = desc_sw128(sBhi + kb * kb_bytes + ks * 32);
-                  mma_tf32(td, ad, bd, id, (kb > 0 || ks > 0) ? 1u : 0u);
+                  mma(td, ad, bd, (kb > 0 || ks > 0) ? 1u : 0u);
                   if (SPLIT3) {
-                    mma_tf32(td, ad, desc_sw128(sBlo + kb * kb_bytes + ks * 32), id, 1u);
-                    mma_tf32(td, desc_sw128(sa + TW_TILE_BYTES + ks * 32), bd, id, 1u);
+                    mma(td, ad, desc_sw128(sBlo + kb * kb_bytes + ks * 32), 1u);
+                    mma(td, desc_sw128(sa + TW_TILE_BYTES + ks * 32), bd, 1u);
                   }
                 }
                 mma_commit(smem_u32(&empty[s]));
@@ -849,7 +1135,7 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
     const int cp = MT == 2 ? n16 : n16 / 2;
     const int c0 = MT == 2 ? 0 : g * cp;
     const int i = mt * 128 + 32 * q + lane;             // orbital row (= K index of B)
-    const bool in_b = i < KB * 32;
+    const bool in_b = i < KB * KBLK;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
     uint32_t pa = 0;
     float sr[32], si[32];
@@ -859,11 +1145,13 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
     // bytes apart, and K block i / 32 sits at kb * 2 n16 * 128.
     uint32_t offu[8];
     {
-      const int kk = i & 31;
-      const uint32_t base_i = (uint32_t)((i >> 5) * 2 * n16 * 128 + (kk & 3) * 4);
+      const int kk = i & (KBLK - 1);
+      const int elem = BF ? (kk & 7) * 2 : (kk & 3) * 4;   // byte within the 16-byte chunk
+      const int chunk = BF ? kk >> 3 : kk >> 2;
+      const uint32_t base_i = (uint32_t)((i / KBLK) * 2 * n16 * 128 + elem);
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        offu[u] = base_i + (uint32_t)(u * 128) + (uint32_t)((((kk >> 2) ^ u) & 7) << 4);
+        offu[u] = base_i + (uint32_t)(u * 128) + (uint32_t)(((chunk ^ u) & 7) << 4);
     }
     const uint32_t im_off = (uint32_t)(n16 >> 3) * 1024u;
     const uint32_t sBh = smem_u32(Bhi), sBl = smem_u32(Blo);
@@ -871,7 +1159,15 @@ tc_taylor_wide_kernel(const __grid_constant__ CUtensorMap mapV,
     auto put_b = [&](int gi, int u, float xr, float xi) {
       if (!in_b) return;
       const uint32_t o_r = (uint32_t)gi * 1024u + offu[u], o_i = o_r + im_off;
-      if (SPLIT3) {
+      if (BF) {
+        uint16_t hr, lr, hi_, li;
+        bf16_split(xr, hr, lr);
+        bf16_split(xi, hi_, li);
+        st_shared_b16(sBh + o_r, hr);
+        st_shared_b16(sBl + o_r, lr);
+        st_shared_b16(sBh + o_i, hi_);
+        st_shared_b16(sBl + o_i, li);
+      } else if (SPLIT3) {
         const float hr = tf32_hi(xr), hi_ = tf32_hi(xi);
         st_shared_f32(sBh + o_r, hr);
         st_shared_f32(sBl + o_r, tf32_lo(xr, hr));
@@ -991,17 +1287,20 @@ cudaError_t make_map(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, lo
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// 3-D map of `planes` row-major matrices (rows x k, row stride ld floats,
-// plane stride rows * ld floats) with 128-row x 32-K boxes.
-cudaError_t make_map3(TcCtx* t, CUtensorMap* map, const float* ptr, long rows, long k, long ld,
-                      long planes) {
-  if (((uintptr_t)ptr & 15) != 0 || (ld & 3) != 0 || k < 1 || rows < 1 || planes < 1)
+// 3-D map of `planes` row-major matrices (rows x k, row stride ld elements,
+// plane stride rows * ld elements) with 128-row boxes of 128 bytes along K
+// (32 FP32 or 64 BF16 values).
+cudaError_t make_map3(TcCtx* t, CUtensorMap* map, const void* ptr, long rows, long k, long ld,
+                      long planes, bool bf16 = false) {
+  const long es_b = bf16 ? 2 : 4;
+  if (((uintptr_t)ptr & 15) != 0 || (ld * es_b) % 16 != 0 || k < 1 || rows < 1 || planes < 1)
     return cudaErrorInvalidValue;
   cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)(rows * ld) * 4};
-  cuuint32_t box[3] = {32u, 128u, 1u};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * es_b), (cuuint64_t)(rows * ld * es_b)};
+  cuuint32_t box[3] = {bf16 ? 64u : 32u, 128u, 1u};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = t->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims, strides,
+  CUresult r = t->encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         3, (void*)ptr, dims, strides,
                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1012,7 +1311,8 @@ template <int BN, bool SPLIT3, bool BLO>
 cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A,
                         long lda, const float* B, const float* Blo, long ldb, float* C,
                         long ldc, float alpha, float beta, const float* R, long ldr,
-                        int ksplit, long split_stride, int* status, float* Clo) {
+                        int ksplit, long split_stride, int* status, float* Clo,
+                        bool out_bf16) {
   using Cfg = GemmCfg<BN, SPLIT3>;
   const cudaError_t attr = set_smem(tc_gemm_kernel<BN, SPLIT3, BLO>, Cfg::SMEM);
   if (attr != cudaSuccess) return attr;
@@ -1038,7 +1338,8 @@ cudaError_t launch_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const fl
   wk.items = (int)items;
   const int grid = wk.items < t->num_sms ? wk.items : t->num_sms;
   tc_gemm_kernel<BN, SPLIT3, BLO><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(
-      ma, mb, mbl, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status, Clo);
+      ma, mb, mbl, m, n, wk, C, ldc, alpha, beta, R, ldr, split_stride, status, Clo,
+      out_bf16 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1068,16 +1369,17 @@ void tc_destroy(TcCtx* t) { delete t; }
 cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float* A, long lda,
                     const float* B, long ldb, float* C, long ldc, float alpha, float beta,
                     const float* R, long ldr, bool split3, int ksplit, long split_stride,
-                    int* status, int bn, const float* Blo, float* Clo) {
+                    int* status, int bn, const float* Blo, float* Clo, bool out_bf16) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ksplit < 1 || (ksplit > 1 && (R || beta != 0.f))) return cudaErrorInvalidValue;
   if (Clo && ksplit != 1) return cudaErrorInvalidValue;
+  if (out_bf16 && (!Clo || R)) return cudaErrorInvalidValue;
   if (bn != 0 && bn != 64 && bn != 128) return cudaErrorInvalidValue;
   if (Blo && !split3) return cudaErrorInvalidValue;
   if (bn == 0) bn = n <= 64 ? 64 : 128;
 #define AFQMC_GEMM(BNV, S3, BL)                                                            \
   return launch_gemm<BNV, S3, BL>(t, st, m, n, k, A, lda, B, Blo, ldb, C, ldc, alpha, beta, \
-                                  R, ldr, ksplit, split_stride, status, Clo)
+                                  R, ldr, ksplit, split_stride, status, Clo, out_bf16)
   if (bn == 64) {
     if (!split3) AFQMC_GEMM(64, false, false);
     if (Blo) AFQMC_GEMM(64, true, true);
@@ -1098,6 +1400,24 @@ __global__ void tf32_split_kernel(long n, float* __restrict__ x, float* __restri
   lo[e] = tf32_lo(v, h);
 }
 
+// BF16 hi and lo parts of n FP64 values (setup).
+__global__ void bf16_split_f64_kernel(long n, const double* __restrict__ x,
+                                      uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  uint16_t h, l;
+  bf16_split((float)x[e], h, l);
+  hi[e] = h;
+  lo[e] = l;
+}
+
+cudaError_t tc_split_bf16(cudaStream_t st, long n, const double* x, void* hi, void* lo) {
+  if (n <= 0) return cudaSuccess;
+  bf16_split_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, (uint16_t*)hi,
+                                                                    (uint16_t*)lo);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo) {
   if (n <= 0) return cudaSuccess;
   tf32_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, lo);
@@ -1105,34 +1425,46 @@ cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo) {
 }
 
 cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
-                      const float* V, const float* Pin, float* Pout, const float* bhalf_img,
-                      bool split3, int* status) {
+                      const float* V, const float* Pin, float* Pout, const void* bhalf_img,
+                      bool split3, bool bf16, int* status) {
   if (M > 64 || M < 1 || N < 1) return cudaErrorInvalidValue;
   if (bhalf_img && ((uintptr_t)bhalf_img & 15)) return cudaErrorInvalidValue;
   const int items = W * ((N + 63) / 64);
+  if (bf16) {
+    const cudaError_t attr = set_smem(tc_taylor_bf16_kernel, TB_SMEM);
+    if (attr != cudaSuccess) return attr;
+    int grid = items < 2 * t->num_sms ? items : 2 * t->num_sms;
+    tc_taylor_bf16_kernel<<<grid, 128, TB_SMEM, st>>>(W, M, N, order, V, Pin, Pout,
+                                                      (const uint16_t*)bhalf_img, status);
+    return cudaGetLastError();
+  }
   if (split3) {
     const cudaError_t attr = set_smem(tc_taylor_kernel<true>, taylor_smem<true>());
     if (attr != cudaSuccess) return attr;
     int grid = items < t->num_sms ? items : t->num_sms;
     tc_taylor_kernel<true><<<grid, 128, taylor_smem<true>(), st>>>(W, M, N, order, V, Pin,
-                                                                  Pout, bhalf_img, status);
+                                                                  Pout, (const float*)bhalf_img,
+                                                                  status);
   } else {
     const cudaError_t attr = set_smem(tc_taylor_kernel<false>, taylor_smem<false>());
     if (attr != cudaSuccess) return attr;
     int grid = items < 2 * t->num_sms ? items : 2 * t->num_sms;
     tc_taylor_kernel<false><<<grid, 128, taylor_smem<false>(), st>>>(W, M, N, order, V, Pin,
-                                                                    Pout, bhalf_img, status);
+                                                                    Pout, (const float*)bhalf_img,
+                                                                    status);
   }
   return cudaGetLastError();
 }
 
 cudaError_t tc_taylor_wide(TcCtx* t, cudaStream_t st, int W, int M, int N, int order, long ldV,
-                           const float* V, const float* Vlo, const float* dB, const float* dBlo,
-                           const float* Pin, float* Pout, bool split3, int* status) {
-  if (M < 1 || M > 256 || N < 1 || W < 1 || order < 1 || ldV < M || (ldV & 3))
+                           const void* V, const void* Vlo, const void* dB, const void* dBlo,
+                           const float* Pin, float* Pout, bool split3, bool bf16, int* status) {
+  if (M < 1 || M > 256 || N < 1 || W < 1 || order < 1 || ldV < M || (ldV & (bf16 ? 7 : 3)))
     return cudaErrorInvalidValue;
+  if (bf16) split3 = true;
   if (split3 && (!Vlo || !dBlo)) return cudaErrorInvalidValue;
-  const int MT = (M + 127) / 128, KB = (M + 31) / 32, P = split3 ? 2 : 1;
+  const int kblk = bf16 ? 64 : 32;
+  const int MT = (M + 127) / 128, KB = (M + kblk - 1) / kblk, P = split3 ? 2 : 1;
   const int stage = TW_TILE_BYTES * P;
   const int budget = 227 * 1024 - 1024 - 256;
   int n16 = ((N + 15) / 16) * 16;
@@ -1145,10 +1477,10 @@ cudaError_t tc_taylor_wide(TcCtx* t, cudaStream_t st, int W, int M, int N, int o
   if (S < 2) return cudaErrorInvalidValue;
   const int smem = 1024 + b + S * stage + 256;
   CUtensorMap mv, mvl, mb, mbl;
-  cudaError_t e = make_map3(t, &mv, V, M, M, ldV, 2L * W);
-  if (e == cudaSuccess) e = make_map3(t, &mb, dB, M, M, ldV, 1);
-  if (e == cudaSuccess && split3) e = make_map3(t, &mvl, Vlo, M, M, ldV, 2L * W);
-  if (e == cudaSuccess && split3) e = make_map3(t, &mbl, dBlo, M, M, ldV, 1);
+  cudaError_t e = make_map3(t, &mv, V, M, M, ldV, 2L * W, bf16);
+  if (e == cudaSuccess) e = make_map3(t, &mb, dB, M, M, ldV, 1, bf16);
+  if (e == cudaSuccess && split3) e = make_map3(t, &mvl, Vlo, M, M, ldV, 2L * W, bf16);
+  if (e == cudaSuccess && split3) e = make_map3(t, &mbl, dBlo, M, M, ldV, 1, bf16);
   if (e != cudaSuccess) return e;
   if (!split3) {
     mvl = mv;
@@ -1156,25 +1488,32 @@ cudaError_t tc_taylor_wide(TcCtx* t, cudaStream_t st, int W, int M, int N, int o
   }
   const long items = (long)W * ((N + n16 - 1) / n16);
   const int grid = items < t->num_sms ? (int)items : t->num_sms;
-  if (split3) {
-    e = set_smem(tc_taylor_wide_kernel<true>, smem);
-    if (e != cudaSuccess) return e;
-    tc_taylor_wide_kernel<true><<<grid, TW_THREADS, smem, st>>>(mv, mvl, mb, mbl, W, M, N, order,
-                                                               n16, S, Pin, Pout, status);
-  } else {
-    e = set_smem(tc_taylor_wide_kernel<false>, smem);
-    if (e != cudaSuccess) return e;
-    tc_taylor_wide_kernel<false><<<grid, TW_THREADS, smem, st>>>(mv, mvl, mb, mbl, W, M, N,
-                                                                order, n16, S, Pin, Pout, status);
-  }
+#define AFQMC_WIDE(S3, BF)                                                                 \
+  do {                                                                                     \
+    e = set_smem(tc_taylor_wide_kernel<S3, BF>, smem);                                     \
+    if (e != cudaSuccess) return e;                                                        \
+    tc_taylor_wide_kernel<S3, BF><<<grid, TW_THREADS, smem, st>>>(                         \
+        mv, mvl, mb, mbl, W, M, N, order, n16, S, Pin, Pout, status);                      \
+  } while (0)
+  if (bf16) AFQMC_WIDE(true, true);
+  else if (split3) AFQMC_WIDE(true, false);
+  else AFQMC_WIDE(false, false);
+#undef AFQMC_WIDE
   return cudaGetLastError();
 }
 
-size_t tc_bhalf_image_floats(bool split3) { return (size_t)128 * 128 * (split3 ? 2 : 1); }
+size_t tc_bhalf_image_bytes(bool split3, bool bf16) {
+  return bf16 ? (size_t)2 * TB_A_BYTES : (size_t)128 * 128 * 4 * (split3 ? 2 : 1);
+}
 
-cudaError_t tc_bhalf_image(cudaStream_t st, int M, const float* dB, float* img, bool split3) {
+cudaError_t tc_bhalf_image(cudaStream_t st, int M, const float* dB, void* img, bool split3,
+                           bool bf16) {
   if (M > 64) return cudaErrorInvalidValue;
-  bhalf_image_kernel<<<(128 * 128 + 255) / 256, 256, 0, st>>>(M, dB, img, split3 ? 1 : 0);
+  if (bf16)
+    bhalf_image_bf16_kernel<<<(128 * 128 + 255) / 256, 256, 0, st>>>(M, dB, (uint16_t*)img);
+  else
+    bhalf_image_kernel<<<(128 * 128 + 255) / 256, 256, 0, st>>>(M, dB, (float*)img,
+                                                                split3 ? 1 : 0);
   return cudaGetLastError();
 }
 

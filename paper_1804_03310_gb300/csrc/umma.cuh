@@ -53,6 +53,64 @@ __host__ __device__ __forceinline__ uint32_t idesc_tf32(int M, int N, bool neg_a
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor for kind::f16 with BF16 operands, FP32 accumulate,
+// both operands K-major: D format F32 (bits 4-5 = 1), A and B format BF16
+// (bits 7-9 and 10-12 = 1), N >> 3 in bits 17-22, M >> 4 in bits 24-28. One
+// MMA consumes K = 16 values (32 bytes of a 128-byte swizzled row).
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// As mma_bf16 with the A operand in tensor memory: lane i holds row i, the
+// 16 K values of the slice packed two to a 32-bit column (the lower K index
+// in the low half), in 8 consecutive columns.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// BF16 bits of x rounded to nearest (ties to even), and the value they stand for.
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  uint16_t h;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  return h;
+}
+__device__ __forceinline__ float bf16_value(uint16_t h) {
+  return __uint_as_float((uint32_t)h << 16);
+}
+// x split as hi + lo, both BF16: hi = x rounded, lo = (x - hi) rounded.
+__device__ __forceinline__ void bf16_split(float x, uint16_t& hi, uint16_t& lo) {
+  hi = bf16_bits(x);
+  lo = bf16_bits(x - bf16_value(hi));
+}
+__device__ __forceinline__ void st_shared_b16(uint32_t addr, uint16_t v) {
+  asm volatile("st.shared.b16 [%0], %1;\n" ::"r"(addr), "h"(v) : "memory");
+}
+
+// Byte offset of element (row, k) of a K-major SW128 BF16 tile with `rows`
+// rows (a multiple of 8): K in blocks of 64 values, a block holding rows / 8
+// atoms of 8 rows x 128 bytes, row r's 16-byte chunks at chunk ^ (r % 8).
+__host__ __device__ __forceinline__ uint32_t sw128_offset_bf16(int row, int k, int rows) {
+  const int kb = k >> 6, kk = k & 63;
+  const int chunk = (kk >> 3) ^ (row & 7);
+  return (uint32_t)(kb * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 +
+                    (kk & 7) * 2);
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(

@@ -19,12 +19,27 @@ def test_tensor_core_taylor_is_rated_against_tf32():
     assert r["traffic"] is not None       # the committed C2 capture
 
 
-def test_cuda_core_taylor_above_m64_is_rated_against_fp32():
-    r = bench.roofline_for(stats("propagate"), "tf32x3", PEAKS, "measured", config_c3(), "c3")
-    assert config_c3().M > 64
+def test_cuda_core_taylor_is_rated_against_fp32():
+    r = bench.roofline_for(stats("propagate"), "tf32x3", PEAKS, "measured", config_c3(), "c3",
+                           taylor_fused=0)
     assert r["bound"] == "alu"
     assert r["peak"] == round(bench.FP32_SIMT_TFLOPS, 3)
-    assert r["traffic"] is None           # no capture of this group at this workload
+
+
+def test_streamed_tensor_core_taylor_above_m64_is_rated_against_tf32():
+    r = bench.roofline_for(stats("propagate"), "tf32x3", PEAKS, "measured", config_c3(), "c3",
+                           taylor_fused=3)
+    assert config_c3().M > 64
+    assert r["bound"] == "tensor" and r["peak"] == 850.0
+
+
+def test_bf16x3_propagation_is_rated_against_bf16():
+    r = bench.roofline_for(stats("propagate"), "bf16x3", PEAKS, "measured", config_c2(), "c2",
+                           taylor_fused=1)
+    assert r["bound"] == "tensor" and r["peak"] == 1700.0
+    r = bench.roofline_for(stats("one_body"), "bf16x3", PEAKS, "measured", config_c2(), "c2",
+                           taylor_fused=1)
+    assert r["peak"] == 850.0             # TF32X3 contractions
 
 
 def test_small_matrix_kernels_are_rated_against_fp32():

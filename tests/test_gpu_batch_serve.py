@@ -47,7 +47,7 @@ def mixed_system(seed=5, M=20, n_up=4, n_dn=3, n_chol=30, W=48):
                         measure_every=10, pc_every=10)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_graph_replay_is_bitwise_plain_launches(prec):
     s = mixed_system()
     g = ctx(s, precision=prec, graphs=True)

@@ -110,9 +110,9 @@ def fp64_shape(name):
     return _FP64_SHAPES[name]
 
 
-@pytest.mark.parametrize("name,prec", [("c2", "tf32x3"), ("c2", "fp32"),
-                                       ("c3", "tf32x3"), ("c4", "tf32x3"),
-                                       ("c4", "fp32")])
+@pytest.mark.parametrize("name,prec", [("c2", "tf32x3"), ("c2", "bf16x3"), ("c2", "fp32"),
+                                       ("c3", "tf32x3"), ("c3", "bf16x3"), ("c4", "tf32x3"),
+                                       ("c4", "bf16x3"), ("c4", "fp32")])
 def test_paired_energy_at_workload_shapes(name, prec):
     s, n = SHAPES[name]
     ref = fp64_shape(name)

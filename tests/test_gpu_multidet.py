@@ -91,7 +91,7 @@ def test_c4_full_size_sampled_fp64():
     print("c4 fp64 worst", w)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "fp32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp32"])
 def test_c4_full_size_sampled_reduced(prec):
     s = config_c4(pc_every=0)
     w = run_pair(s, prec, 20, 1e-4, walkers=[0, 511, 1023], energy_at=(20,))
