@@ -420,18 +420,20 @@ def energy_check_shapes(precision):
     from synth import CONFIGS
     from paper_1804_03310_gb300 import Afqmc
     out = {}
+    precs = [precision] + [p for p in ("tf32x3", "bf16x3") if p != precision]
     for name, n_steps in (("c2", 200), ("c3", 100), ("c4", 60)):
         s = CONFIGS[name]().replace(pc_every=0, measure_every=20)
         e = {}
-        for p in ("fp64", precision):
+        for p in ["fp64"] + precs:
             with Afqmc.from_system(s, precision=p) as ctx:
                 ctx.afqmc_propagate(n_steps)
                 e[p] = ctx.afqmc_energy_history()[:, 1]
-        d = (e[precision] - e["fp64"]) * 1e3
-        out[name] = {"steps": n_steps, "measurements": int(len(d)),
-                     "max_abs_mHa": round(float(np.max(np.abs(d))), 6),
-                     "mean_mHa": round(float(np.mean(d)), 6),
+        out[name] = {"steps": n_steps, "measurements": int(len(e["fp64"])),
                      "e_fp64_last": round(float(e["fp64"][-1]), 6)}
+        for p in precs:
+            d = (e[p] - e["fp64"]) * 1e3
+            out[name][p] = {"max_abs_mHa": round(float(np.max(np.abs(d))), 6),
+                            "mean_mHa": round(float(np.mean(d)), 6)}
     return out
 
 
@@ -683,20 +685,32 @@ def reblocked_error(x):
     return best
 
 
+def precisions_leg(s, n_blocks=3):
+    """The bench workload in each reduced precision (same seed): walker-steps/s
+    per mode; the energy deviation of each mode is in fp64_gpu."""
+    out = {}
+    for prec in ("fp32", "tf32x3", "bf16x3"):
+        ms, _ = _blocks(s, prec, n_blocks)
+        out[prec] = {"value": round(s.n_walkers * BLOCK / (ms / 1e3), 1),
+                     "ms_per_block": round(ms, 3)}
+    return out
+
+
 def shapes_leg(precision):
-    """The other workload shapes of the scope, each in the measured mode and
-    in FP64 on the GPU (same walkers and seed): the TM-atom shape (M = 150,
-    where the Taylor series runs on the CUDA cores) and the
-    multi-determinant shape (200 determinants, batched SMW ratios)."""
+    """The other workload shapes of the scope, each in its stated arithmetic
+    and in FP64 on the GPU (same walkers and seed): the TM-atom shape
+    (M = 150, BF16 hi + lo propagation, operator streamed by TMA) and the
+    multi-determinant shape (200 determinants, batched SMW ratios) in the
+    bench's precision."""
     from synth import CONFIGS
     out = {}
-    for name in ("c3", "c4"):
+    for name, prec in (("c3", "bf16x3"), ("c4", precision)):
         s = CONFIGS[name]().replace(measure_every=BLOCK, pc_every=BLOCK, ortho_every=2)
-        ms, kms = _blocks(s, precision, 2)
+        ms, kms = _blocks(s, prec, 2)
         ms64, _ = _blocks(s, "fp64", 1)
         v = s.n_walkers * BLOCK / (ms / 1e3)
         v64 = s.n_walkers * BLOCK / (ms64 / 1e3)
-        out[name] = {"workload": describe(s), "precision": precision,
+        out[name] = {"workload": describe(s), "precision": prec,
                      "value": round(v, 1), "unit": METRIC, "ms_per_block": round(ms, 3),
                      "fp64_value": round(v64, 1), "speedup": round(v / v64, 2),
                      "kernels_ms_2_blocks": kms}
@@ -765,6 +779,7 @@ def main():
         leg("serving", lambda: serving_leg(args.precision))
     if not args.no_shapes and world == 1 and args.precision != "fp64":
         leg("shapes", lambda: shapes_leg(args.precision))
+        leg("precisions", lambda: precisions_leg(s))
         leg("fp64_islands", lambda: islands_leg(s, args.precision, value))
         leg("batch", lambda: batch_leg(args.precision))
         leg("ndet_sweep", lambda: ndet_leg(args.precision))

@@ -188,6 +188,14 @@ afqmc_status afqmc_weights(afqmc_ctx* ctx, double* w, double* log_ovlp);
 afqmc_status afqmc_green(afqmc_ctx* ctx, int32_t walker, double* G_up,
                          double* G_dn);
 
+/* Self-test of failure detection (no counterpart in the paper): runs on the
+ * context's stream one kernel whose single thread waits, with the bounded
+ * wait every tensor-core pipeline uses, on an mbarrier that nothing ever
+ * completes, giving up after about limit_cycles SM clock cycles (0..4e9);
+ * no copy or MMA is in flight. Returns AFQMC_E_TIMEOUT, the status a
+ * timed-out pipeline wait reports, and leaves the context usable. */
+afqmc_status afqmc_selftest_wait_timeout(afqmc_ctx* ctx, int64_t limit_cycles);
+
 /* The energy shift E_T in use (Sec. II): params.e_shift, or when that is NaN
  * the energy of the reference determinant <D_0|H|D_0>, evaluated in FP64 at
  * creation whatever the step precision. */

@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "afqmc_green": (C.c_int, [vp, C.c_int32, d, d]),
         "afqmc_force_bias": (C.c_int, [vp, d]),
         "afqmc_energy_shift": (C.c_int, [vp, d]),
+        "afqmc_selftest_wait_timeout": (C.c_int, [vp, C.c_int64]),
         "afqmc_energy_history": (C.c_int, [vp, d, C.c_int32, i32]),
         "afqmc_get_state": (C.c_int, [vp, vp, P(C.c_size_t)]),
         "afqmc_set_state": (C.c_int, [vp, vp, C.c_size_t]),
@@ -303,6 +304,9 @@ class Afqmc:
         self._check(self._lib.afqmc_green(self._h, walker, _dptr(gu), _dptr(gd)))
         return (gu.view(np.complex128).reshape(self.M, self.M),
                 gd.view(np.complex128).reshape(self.M, self.M))
+
+    def afqmc_selftest_wait_timeout(self, limit_cycles: int):
+        self._check(self._lib.afqmc_selftest_wait_timeout(self._h, int(limit_cycles)))
 
     def afqmc_energy_shift(self) -> float:
         e = np.zeros(1)

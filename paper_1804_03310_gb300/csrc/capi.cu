@@ -1582,6 +1582,15 @@ afqmc_status afqmc_green(afqmc_ctx* c, int32_t walker, double* G_up, double* G_d
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_selftest_wait_timeout(afqmc_ctx* c, int64_t limit_cycles) {
+  GUARD(c);
+  if (limit_cycles < 0 || limit_cycles > 4000000000LL)
+    return fail(c, AFQMC_E_INVALID, "limit_cycles must be in 0..4e9");
+  CK(cudaStreamSynchronize(c->st));
+  LK(tc_wait_timeout_probe(c->st, (long long)limit_cycles, c->status));
+  return check_status(c);
+}
+
 afqmc_status afqmc_energy_shift(afqmc_ctx* c, double* e_shift) {
   GUARD(c);
   if (!e_shift) return fail(c, AFQMC_E_INVALID, "e_shift is NULL");

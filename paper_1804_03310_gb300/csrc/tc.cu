@@ -1418,6 +1418,23 @@ cudaError_t tc_split_bf16(cudaStream_t st, long n, const double* x, void* hi, vo
   return cudaGetLastError();
 }
 
+// Self-test of the bounded pipeline wait: one thread initialises an mbarrier
+// that nothing ever arrives at and waits on it with the limit given; the
+// wait gives up and bit 4 of *status is set, as a timed-out pipeline wait in
+// the GEMM and Taylor kernels does. No copy or MMA is issued.
+__global__ void wait_timeout_probe_kernel(long long limit_cycles, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  mbar_fence_init();
+  if (!mbar_wait(smem_u32(&bar), 0, limit_cycles)) flag_timeout(status);
+}
+
+cudaError_t tc_wait_timeout_probe(cudaStream_t st, long long limit_cycles, int* status) {
+  wait_timeout_probe_kernel<<<1, 32, 0, st>>>(limit_cycles, status);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_split(cudaStream_t st, long n, float* x, float* lo) {
   if (n <= 0) return cudaSuccess;
   tf32_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, lo);

@@ -30,6 +30,10 @@ cudaError_t tc_gemm(TcCtx* t, cudaStream_t st, int m, int n, int k, const float*
                     long split_stride, int* status, int bn = 0, const float* Blo = nullptr,
                     float* Clo = nullptr, bool out_bf16 = false);
 
+// Self-test of the bounded wait: a kernel waits on an mbarrier nothing
+// completes, gives up after limit_cycles and sets bit 4 of *status.
+cudaError_t tc_wait_timeout_probe(cudaStream_t st, long long limit_cycles, int* status);
+
 // BF16 hi and lo parts (hi = x rounded, lo = x - hi rounded) of n FP64 values.
 cudaError_t tc_split_bf16(cudaStream_t st, long n, const double* x, void* hi, void* lo);
 

@@ -206,6 +206,24 @@ def test_comb_matches_oracle_on_given_weights():
         gpu.close()
 
 
+def test_bounded_wait_times_out_and_context_stays_usable():
+    """Failure detection without a fault: a pipeline wait that nothing
+    completes gives up after its limit (about 2e6 cycles, a millisecond),
+    the host reads AFQMC_E_TIMEOUT, and the context keeps working."""
+    from paper_1804_03310_gb300 import AfqmcError
+    s = config_c1()
+    gpu = gpu_ctx(s, precision="tf32x3")
+    with pytest.raises(AfqmcError) as e:
+        gpu.afqmc_selftest_wait_timeout(2_000_000)
+    assert e.value.status == 5
+    orc = O.OracleRun(s)
+    gpu.afqmc_propagate(3)
+    orc.run(3)
+    w, _ = gpu.afqmc_weights()
+    assert np.max(np.abs(w - orc.weight) / orc.weight) < 1e-4
+    gpu.close()
+
+
 def test_kernel_timing_and_launch_counter():
     s = config_c1()
     gpu = gpu_ctx(s)
