@@ -56,6 +56,19 @@ def test_small_multidet_fp64(n_det):
     print(f"multidet n_det={n_det} fp64 worst", w)
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("M", [12, 14])
+def test_small_multidet_tensor_cores(prec, M):
+    """Multi-determinant trials in the tensor-core modes: M % 4 == 0 puts the
+    half steps on the tensor cores as well, M = 14 keeps them on the CUDA
+    cores."""
+    s = small_system(M=M, n_up=3, n_dn=2, n_chol=15, seed=4, n_det=20, n_walkers=16,
+                     dtau=0.01, l_sigma=0.05, ortho_every=2, measure_every=4, pc_every=0)
+    s = scrambled(s, np.random.default_rng(7))
+    w = run_pair(s, prec, 8, 1e-4, energy_at=(1, 4, 8))
+    print(f"multidet M={M} {prec} worst", w)
+
+
 def test_unequal_spins_multidet_fp64():
     s = small_system(M=9, n_up=4, n_dn=2, n_chol=11, seed=9, n_det=12, n_walkers=8,
                      dtau=0.01, l_sigma=0.08, ortho_every=2, measure_every=3,
