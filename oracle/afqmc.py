@@ -26,7 +26,16 @@ every function follows one step of the method as the paper states it:
 * Weight (Sec. II, hybrid form of Sec. IV.A): with
   ``R = <Psi_T|phi'> / <Psi_T|phi>`` the walker weight is multiplied by
   ``|R exp(sum_g x_g xbar_g - xbar_g^2/2) exp(dt E_T)|`` and by
-  ``max(0, cos(Im ln R))``, the phaseless constraint.
+  ``max(0, cos(Im ln R))``, the phaseless constraint. The local-energy form
+  (Sec. II) multiplies it instead by ``exp(-dt (Re E_L - E_T))``, ``E_L`` the
+  local energy of the walker before the move, and by the same cut.
+* Mean-field subtraction (an option; Sec. II's propagator is unchanged by
+  it): with ``lbar_g = <L_g>`` of the reference determinant,
+  ``1/2 L_g^2 = 1/2 (L_g - lbar_g)^2 + lbar_g L_g - 1/2 lbar_g^2``, so the
+  one-body remainder gains ``sum_g lbar_g L_g``, the force bias becomes
+  ``-i sqrt(dt) (X_g - lbar_g)``, each walker's overlap ratio carries the
+  scalar ``exp(-i sqrt(dt) sum_g (x_g - xbar_g) lbar_g)`` (inside the cut's
+  phase), and the constant ``-1/2 sum_g lbar_g^2`` enters the weight's shift.
 * Orthonormalisation every few steps (Sec. IV.A) by modified Gram-Schmidt;
   the log-overlap drops by ``ln det R``.
 * Local energy ``<Psi_T|H|phi>/<Psi_T|phi>`` (Sec. II) from the mixed Green's
@@ -56,10 +65,32 @@ from .philox import gaussian_fields, comb_uniform
 # ---------------------------------------------------------------------------
 
 
-def one_body_remainder(h1, L):
+def one_body_remainder(h1, L, lbar=None):
     """H1' = T - 1/2 sum_g L_g L_g: the one-body part left after writing the
-    two-body term of Eq. 1 as -1/2 sum_g v_g^2 (Sec. II)."""
-    return h1 - 0.5 * np.einsum("gik,gkj->ij", L, L)
+    two-body term of Eq. 1 as -1/2 sum_g v_g^2 (Sec. II). With the mean
+    field lbar subtracted, H1' + sum_g lbar_g L_g."""
+    h = h1 - 0.5 * np.einsum("gik,gkj->ij", L, L)
+    if lbar is not None:
+        h = h + np.einsum("g,gij->ij", lbar, L)
+    return h
+
+
+def mean_field(L, D_up, D_dn):
+    """lbar_g = <D|L_g|D> / <D|D> for the determinant D (its spins' column
+    blocks D_up, D_dn): sum_sigma tr((D^H D)^-1 D^H L_g D)."""
+    lbar = np.zeros(L.shape[0])
+    for D in (D_up, D_dn):
+        if D.shape[1] == 0:
+            continue
+        Sinv = np.linalg.inv(D.conj().T @ D)
+        for g in range(L.shape[0]):
+            lbar[g] += np.trace(Sinv @ (D.conj().T @ L[g] @ D)).real
+    return lbar
+
+
+def mean_field_constant(lbar):
+    """E_0 = -1/2 sum_g lbar_g^2, the constant of the rewritten two-body term."""
+    return -0.5 * float(np.sum(np.asarray(lbar) ** 2))
 
 
 def half_step_propagator(h1p, dtau):
@@ -148,11 +179,12 @@ def mixed_green(trial, Phi_up, Phi_dn):
 # ---------------------------------------------------------------------------
 
 
-def force_bias(L, Gu, Gd, dtau, cap):
-    """X_g = sum_sigma sum_ik L_g,ik G^sigma_ik and xbar_g = -i sqrt(dt) X_g,
-    each xbar_g scaled down to modulus ``cap`` when larger (cap <= 0: none)."""
+def force_bias(L, Gu, Gd, dtau, cap, lbar=None):
+    """X_g = sum_sigma sum_ik L_g,ik G^sigma_ik and xbar_g = -i sqrt(dt) X_g
+    (-i sqrt(dt) (X_g - lbar_g) with the mean field subtracted), each xbar_g
+    scaled down to modulus ``cap`` when larger (cap <= 0: none)."""
     X = np.einsum("gik,wik->wg", L, Gu + Gd)
-    xbar = -1j * np.sqrt(dtau) * X
+    xbar = -1j * np.sqrt(dtau) * (X if lbar is None else X - lbar[None, :])
     xbar = np.where(np.isfinite(xbar), xbar, 0.0)   # a walker with no defined bias
     if cap > 0:
         a = np.abs(xbar)
@@ -186,22 +218,52 @@ def importance_log(x, xbar):
     return np.sum(x * xbar - 0.5 * xbar * xbar, axis=1)
 
 
-def update_weights(weight, logO_old, logO_new, x, xbar, dtau, e_shift, cap=0,
-                   w_ref=1.0):
-    """Hybrid weight with the phaseless cut (Sec. II):
-    W <- W |I| max(0, cos(Im ln R)), ln I = ln R + sum(x xbar - xbar^2/2)
-    + dt E_T. A walker at weight 0 stays there; non-finite results give 0.
-    With cap > 0 (an option, not part of the paper's step) the result is
-    capped at cap * w_ref, w_ref the common weight of the last comb."""
-    lnR = logO_new - logO_old
-    lnI = lnR + importance_log(x, xbar) + dtau * e_shift
-    with np.errstate(over="ignore", invalid="ignore"):
-        w = weight * np.exp(lnI.real) * np.maximum(0.0, np.cos(lnR.imag))
+def mean_field_log(x, xbar, lbar, dtau):
+    """-i sqrt(dt) sum_g (x_g - xbar_g) lbar_g: the log of the scalar factor
+    that the subtracted mean field puts on each propagated walker."""
+    return -1j * np.sqrt(dtau) * ((x - xbar) @ lbar)
+
+
+def log_importance(lnR, x, xbar, dtau, e_shift, e0=0.0):
+    """ln I = ln R + sum(x xbar - xbar^2/2) + dt (E_T - E_0): the complex
+    importance factor of the hybrid form before the phaseless cut (E_0 the
+    mean-field constant, 0 without the subtraction)."""
+    return lnR + importance_log(x, xbar) + dtau * (e_shift - e0)
+
+
+def _finish_weights(weight, w, cap, w_ref):
     w = np.where(weight == 0.0, 0.0, w)
     w = np.where(np.isfinite(w), w, 0.0)
     if cap > 0 and w_ref > 0:
         w = np.minimum(w, cap * w_ref)
     return w
+
+
+def update_weights(weight, logO_old, logO_new, x, xbar, dtau, e_shift, cap=0,
+                   w_ref=1.0, lmf=0.0, e0=0.0):
+    """Hybrid weight with the phaseless cut (Sec. II):
+    W <- W |I| max(0, cos(Im ln R)), ln I as in log_importance, ln R the
+    overlap ratio's log plus the mean-field scalar lmf (0 without the
+    subtraction). A walker at weight 0 stays there; non-finite results
+    give 0. With cap > 0 (an option, not part of the paper's step) the
+    result is capped at cap * w_ref, w_ref the common weight of the last
+    comb."""
+    lnR = logO_new - logO_old + lmf
+    lnI = log_importance(lnR, x, xbar, dtau, e_shift, e0)
+    with np.errstate(over="ignore", invalid="ignore"):
+        w = weight * np.exp(lnI.real) * np.maximum(0.0, np.cos(lnR.imag))
+    return _finish_weights(weight, w, cap, w_ref)
+
+
+def update_weights_local(weight, eloc, lnR, dtau, e_shift, cap=0, w_ref=1.0):
+    """Local-energy weight form with the phaseless cut (Sec. II):
+    W <- W exp(-dt (Re E_L - E_T)) max(0, cos(Im ln R)), E_L the local
+    energy before the move, ln R as for update_weights. Same handling of
+    zero and non-finite weights and of the cap."""
+    with np.errstate(over="ignore", invalid="ignore"):
+        w = (weight * np.exp(-dtau * (eloc.real - e_shift))
+             * np.maximum(0.0, np.cos(lnR.imag)))
+    return _finish_weights(weight, w, cap, w_ref)
 
 
 def modified_gram_schmidt(Phi):
@@ -381,7 +443,8 @@ class OracleRun:
     """W walkers of one system, propagated step by step in FP64.
 
     Step s (0-based counter, as drawn by Philox) does: mixed G and force bias
-    at the current walkers, field draw, propagation, new overlap, weight.
+    at the current walkers (and, in the local-energy weight form, their local
+    energies), field draw, propagation, new overlap, weight.
     After it, with n = s + 1 steps done: orthonormalise if n % ortho_every
     == 0, measure if n % measure_every == 0, comb if n % pc_every == 0.
     """
@@ -397,7 +460,12 @@ class OracleRun:
         self.trial = Trial.from_system(s)
         self.h1 = np.asarray(s.h1, dtype=np.float64)
         self.L = np.asarray(s.L, dtype=np.float64)
-        self.h1p = one_body_remainder(self.h1, self.L)
+        self.weight_mode = getattr(s, "weight_mode", 0)
+        # mean field of the reference determinant (zero: no subtraction)
+        self.lbar = (mean_field(self.L, self.trial.D_up[0], self.trial.D_dn[0])
+                     if getattr(s, "mf_subtract", 0) else None)
+        self.e0 = 0.0 if self.lbar is None else mean_field_constant(self.lbar)
+        self.h1p = one_body_remainder(self.h1, self.L, self.lbar)
         self.Bhalf = half_step_propagator(self.h1p, s.dtau)
         W = self.walker_ids.size
         self.Phi_up = np.repeat(self.trial.D_up[0][None], W, axis=0).copy()
@@ -421,17 +489,25 @@ class OracleRun:
     def step(self):
         s = self.s
         logO_old, Gu, Gd, _ = mixed_green(self.trial, self.Phi_up, self.Phi_dn)
-        X, xbar = force_bias(self.L, Gu, Gd, s.dtau, s.fb_cap)
+        X, xbar = force_bias(self.L, Gu, Gd, s.dtau, s.fb_cap, self.lbar)
+        eloc = self.local_energies() if self.weight_mode == 1 else None
         x = self.fields()
         V = one_body_operator(self.L, x, xbar, s.dtau)
         self.Phi_up = propagate(self.Bhalf, V, self.Phi_up, s.taylor_order)
         self.Phi_dn = propagate(self.Bhalf, V, self.Phi_dn, s.taylor_order)
         logO_new, _ = trial_overlap(self.trial, self.Phi_up, self.Phi_dn)
-        self.weight = update_weights(self.weight, self.logO, logO_new, x,
-                                     xbar, s.dtau, self.e_shift,
-                                     getattr(s, "weight_cap", 0), self.w_ref)
+        lmf = 0.0 if self.lbar is None else mean_field_log(x, xbar, self.lbar, s.dtau)
+        cap = getattr(s, "weight_cap", 0)
+        lnR = logO_new - self.logO + lmf
+        if self.weight_mode == 1:
+            self.weight = update_weights_local(self.weight, eloc, lnR, s.dtau,
+                                               self.e_shift, cap, self.w_ref)
+        else:
+            self.weight = update_weights(self.weight, self.logO, logO_new, x,
+                                         xbar, s.dtau, self.e_shift, cap,
+                                         self.w_ref, lmf=lmf, e0=self.e0)
         self.logO = logO_new
-        self.last = dict(X=X, xbar=xbar, x=x, V=V)
+        self.last = dict(X=X, xbar=xbar, x=x, V=V, lnR=lnR, eloc=eloc)
         self.step_count += 1
         n = self.step_count
         if s.ortho_every > 0 and n % s.ortho_every == 0:

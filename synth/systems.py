@@ -58,6 +58,8 @@ class System:
     fb_cap: float = 1.0
     run_id: int = 0
     weight_cap: int = 0
+    weight_mode: int = 0      # 0: hybrid weights, 1: local-energy form
+    mf_subtract: int = 0      # 1: subtract the reference determinant's mean field
 
     @property
     def M(self) -> int:

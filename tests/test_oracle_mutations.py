@@ -43,6 +43,13 @@ FAST_PINS = [
     ("comb", lambda: pins.test_blocked_prefix_sum_and_comb()),
     ("comb_intervals", lambda: pins.test_comb_brute_force_intervals()),
     ("zero_variance", lambda: pins.test_zero_variance_exact_trial(_FOCK)),
+    ("mean_field", lambda: pins.test_mean_field_is_the_reference_expectation(_FOCK, _SYS4)),
+    ("mf_hs_quadrature", lambda: pins.test_mean_field_hs_quadrature(_FOCK, _SYS4)),
+    ("step_average", lambda: pins.test_step_importance_factor_is_the_projected_overlap(_FOCK, 0)),
+    ("step_average_mf", lambda: pins.test_step_importance_factor_is_the_projected_overlap(_FOCK, 1)),
+    ("local_weight", lambda: pins.test_local_energy_weight_is_the_mean_importance_factor(0)),
+    ("local_weight_mf", lambda: pins.test_local_energy_weight_is_the_mean_importance_factor(1)),
+    ("mf_phase", lambda: pins.test_mean_field_subtraction_shrinks_the_phase()),
 ]
 SLOW_PINS = {
     "hs_quadrature": lambda: pins.test_hs_importance_factor_quadrature(_FOCK, _SYS4),
@@ -75,8 +82,9 @@ def plus_force_bias_in_v(L, x, xbar, dtau):
     return 1j * np.sqrt(dtau) * np.einsum("wg,gij->wij", x + xbar, L)   # slip: x + xbar
 
 
-def remainder_sign(h1, L):
-    return h1 + 0.5 * np.einsum("gik,gkj->ij", L, L)            # slip: + remainder
+def remainder_sign(h1, L, lbar=None):
+    h = h1 + 0.5 * np.einsum("gik,gkj->ij", L, L)               # slip: + remainder
+    return h if lbar is None else h + np.einsum("g,gij->ij", lbar, L)
 
 
 def transposed_green(D, Phi):
@@ -87,9 +95,9 @@ def transposed_green(D, Phi):
     return logdet, Theta, GT                                    # slip: G^T for G
 
 
-def force_bias_sign(L, Gu, Gd, dtau, cap):
+def force_bias_sign(L, Gu, Gd, dtau, cap, lbar=None):
     X = np.einsum("gik,wik->wg", L, Gu + Gd)
-    xbar = 1j * np.sqrt(dtau) * X                               # slip: + i sqrt(dt) X
+    xbar = 1j * np.sqrt(dtau) * (X if lbar is None else X - lbar)   # slip: + i sqrt(dt)
     xbar = np.where(np.isfinite(xbar), xbar, 0.0)
     if cap > 0:
         a = np.abs(xbar)
@@ -98,9 +106,9 @@ def force_bias_sign(L, Gu, Gd, dtau, cap):
 
 
 def cut_on_importance_phase(weight, logO_old, logO_new, x, xbar, dtau, e_shift, cap=0,
-                            w_ref=1.0):
-    lnR = logO_new - logO_old
-    lnI = lnR + O.importance_log(x, xbar) + dtau * e_shift
+                            w_ref=1.0, lmf=0.0, e0=0.0):
+    lnR = logO_new - logO_old + lmf
+    lnI = lnR + O.importance_log(x, xbar) + dtau * (e_shift - e0)
     with np.errstate(over="ignore", invalid="ignore"):
         w = weight * np.exp(lnI.real) * np.maximum(0.0, np.cos(lnI.imag))   # slip
     w = np.where(weight == 0.0, 0.0, w)
@@ -186,6 +194,74 @@ def mgs_no_projection_update(Phi):
     return Q, R
 
 
+def mf_remainder_sign(h1, L, lbar=None):
+    h = h1 - 0.5 * np.einsum("gik,gkj->ij", L, L)
+    if lbar is not None:
+        h = h - np.einsum("g,gij->ij", lbar, L)                 # slip: - lbar L
+    return h
+
+
+def mf_scalar_sign(x, xbar, lbar, dtau):
+    return 1j * np.sqrt(dtau) * ((x - xbar) @ lbar)             # slip: + i
+
+
+def mf_constant_sign(lbar):
+    return 0.5 * float(np.sum(np.asarray(lbar) ** 2))           # slip: + 1/2
+
+
+def mf_bias_sign(L, Gu, Gd, dtau, cap, lbar=None):
+    X = np.einsum("gik,wik->wg", L, Gu + Gd)
+    xbar = -1j * np.sqrt(dtau) * (X if lbar is None else X + lbar[None, :])   # slip: + lbar
+    xbar = np.where(np.isfinite(xbar), xbar, 0.0)
+    if cap > 0:
+        a = np.abs(xbar)
+        xbar = np.where(a > cap, xbar * (cap / np.where(a > 0, a, 1.0)), xbar)
+    return X, xbar
+
+
+def mean_field_up_only(L, D_up, D_dn):
+    lbar = np.zeros(L.shape[0])
+    Sinv = np.linalg.inv(D_up.conj().T @ D_up)
+    for g in range(L.shape[0]):                                 # slip: one spin only
+        lbar[g] += np.trace(Sinv @ (D_up.conj().T @ L[g] @ D_up)).real
+    return lbar
+
+
+def mf_constant_dropped(lnR, x, xbar, dtau, e_shift, e0=0.0):
+    return lnR + O.importance_log(x, xbar) + dtau * e_shift    # slip: no E_0
+
+
+def local_weight_sign(weight, eloc, lnR, dtau, e_shift, cap=0, w_ref=1.0):
+    with np.errstate(over="ignore", invalid="ignore"):
+        w = (weight * np.exp(dtau * (eloc.real - e_shift))       # slip: + dt
+             * np.maximum(0.0, np.cos(lnR.imag)))
+    return O._finish_weights(weight, w, cap, w_ref)
+
+
+_STEP = O.OracleRun.step
+
+
+def energy_after_move(self):
+    """The step with the local-energy form reading E_L after the move."""
+    if self.weight_mode != 1:
+        return _STEP(self)
+    s = self.s
+    _, Gu, Gd, _ = O.mixed_green(self.trial, self.Phi_up, self.Phi_dn)
+    X, xbar = O.force_bias(self.L, Gu, Gd, s.dtau, s.fb_cap, self.lbar)
+    x = self.fields()
+    V = O.one_body_operator(self.L, x, xbar, s.dtau)
+    self.Phi_up = O.propagate(self.Bhalf, V, self.Phi_up, s.taylor_order)
+    self.Phi_dn = O.propagate(self.Bhalf, V, self.Phi_dn, s.taylor_order)
+    eloc = self.local_energies()                                 # slip: after the move
+    logO_new, _ = O.trial_overlap(self.trial, self.Phi_up, self.Phi_dn)
+    lmf = 0.0 if self.lbar is None else O.mean_field_log(x, xbar, self.lbar, s.dtau)
+    lnR = logO_new - self.logO + lmf
+    self.weight = O.update_weights_local(self.weight, eloc, lnR, s.dtau, self.e_shift)
+    self.logO = logO_new
+    self.last = dict(X=X, xbar=xbar, x=x, V=V, lnR=lnR, eloc=eloc)
+    self.step_count += 1
+
+
 SLIPS = {
     "exchange_sign": [(O, "local_energy_rotated", exchange_sign)],
     "importance_exponent": [(O, "importance_log", importance_exponent)],
@@ -202,6 +278,14 @@ SLIPS = {
     "philox_constants": [(P, "_M0", P._M1), (P, "_M1", P._M0)],
     "box_muller": [(P, "box_muller", box_muller_radius)],
     "mgs_conjugate": [(O, "modified_gram_schmidt", mgs_no_projection_update)],
+    "mf_remainder_sign": [(O, "one_body_remainder", mf_remainder_sign)],
+    "mf_scalar_sign": [(O, "mean_field_log", mf_scalar_sign)],
+    "mf_constant_sign": [(O, "mean_field_constant", mf_constant_sign)],
+    "mf_bias_sign": [(O, "force_bias", mf_bias_sign)],
+    "mean_field_one_spin": [(O, "mean_field", mean_field_up_only)],
+    "mf_constant_dropped": [(O, "log_importance", mf_constant_dropped)],
+    "local_weight_sign": [(O, "update_weights_local", local_weight_sign)],
+    "local_energy_after_move": [(O.OracleRun, "step", energy_after_move)],
 }
 # slips whose natural pin is one of the slow ones
 NEEDS = {"importance_exponent": ["hs_quadrature"], "x_plus_xbar": ["hs_quadrature"]}

@@ -207,6 +207,157 @@ def test_propagation_is_thouless(fock4, sys4):
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
 
 
+def test_mean_field_is_the_reference_expectation(fock4, sys4):
+    """lbar_g = <D_0|L_g|D_0> / <D_0|D_0> for the reference determinant,
+    by brute force in Fock space; at phi = D_0 the subtracted force bias
+    vanishes, and the remainder with the mean field reproduces Eq. 1 with
+    the constant E_0 (an operator identity on the whole Fock space)."""
+    s = sys4
+    trial = O.Trial.from_system(s)
+    lbar = O.mean_field(s.L, trial.D_up[0], trial.D_dn[0])
+    d0 = fock4.slater(trial.D_up[0], trial.D_dn[0])
+    for g in range(s.n_chol):
+        Lg = fock4.one_body(s.L[g].astype(complex))
+        ref = np.vdot(d0, Lg @ d0) / np.vdot(d0, d0)
+        assert abs(lbar[g] - ref) < 1e-12
+    # a non-orthonormal determinant with the same span gives the same mean field
+    T = np.array([[1.0, 0.3], [0.2, 2.0]])
+    assert np.abs(O.mean_field(s.L, trial.D_up[0] @ T, 0.5 * trial.D_dn[0]) - lbar).max() < 1e-12
+    _, Gu, Gd, _ = O.mixed_green(trial, trial.D_up[:1], trial.D_dn[:1])
+    X, xbar = O.force_bias(s.L, Gu, Gd, 0.01, 0.0, lbar)
+    assert np.abs(xbar).max() < 1e-13 and np.abs(X).max() > 0.1
+    H = fock4.hamiltonian(s.h1, eri_from_chol(s.L)).toarray()
+    H2 = fock4.one_body(O.one_body_remainder(s.h1, s.L, lbar).astype(complex)).toarray()
+    eye = np.eye(fock4.dim)
+    for g in range(s.n_chol):
+        Lg = fock4.one_body(s.L[g].astype(complex)).toarray() - lbar[g] * eye
+        H2 = H2 + 0.5 * (Lg @ Lg)
+    assert np.abs(H - H2 - O.mean_field_constant(lbar) * eye).max() < 1e-12
+
+
+def test_mean_field_hs_quadrature(fock4, sys4):
+    """Eq. 2 for the subtracted operator: for one field, the Gaussian
+    average of exp(x xbar - xbar^2/2) times the mean-field scalar times
+    <Psi_T| exp(V(x - xbar)) |phi> equals <Psi_T| exp(-dt/2 (L - lbar)^2) |phi>
+    for any shift xbar."""
+    s = sys4
+    rng = np.random.default_rng(14)
+    dt = 0.05
+    Pu, Pd = rand_walker(rng, 4, 2), rand_walker(rng, 4, 1)
+    trial = O.Trial.from_system(s)
+    lbar = O.mean_field(s.L[:1], trial.D_up[0], trial.D_dn[0])
+    idx = fock4.sector(2, 1)          # the operators conserve both spins' counts
+    psi_t = fock4.slater(trial.D_up[0], trial.D_dn[0])[idx]
+    phi = fock4.slater(Pu, Pd)[idx]
+    Lh = fock4.one_body(s.L[0].astype(complex)).toarray()[np.ix_(idx, idx)]
+    Lh = Lh - lbar[0] * np.eye(len(idx))
+    target = np.vdot(psi_t, expm(-0.5 * dt * Lh @ Lh) @ phi)
+    nodes, wts = np.polynomial.hermite_e.hermegauss(80)
+    wts = wts / math.sqrt(2 * math.pi)
+    for xbar in (0.0 + 0.0j, -0.3j, 0.2 - 0.1j):
+        acc = 0.0
+        for xq, wq in zip(nodes, wts):
+            x, xb = np.array([[xq]]), np.array([[xbar]])
+            V = O.one_body_operator(s.L[:1], x, xb, dt)[0]
+            Vhat = fock4.one_body(V).toarray()[np.ix_(idx, idx)]
+            lnf = O.importance_log(x, xb)[0] + O.mean_field_log(x, xb, lbar, dt)[0]
+            acc += wq * np.exp(lnf) * np.vdot(psi_t, expm(Vhat) @ phi)
+        assert abs(acc - target) < 1e-10 * abs(target)
+
+
+def _step_average(s, Pu, Pd, dt, mf, nodes, wts):
+    """Gauss-Hermite average over the one field of the hybrid importance
+    factor I(x) of one step from the walker (Pu, Pd), with the oracle's own
+    force bias, propagation, overlaps and mean-field terms."""
+    trial = O.Trial.from_system(s)
+    lbar = O.mean_field(s.L, trial.D_up[0], trial.D_dn[0]) if mf else None
+    e0 = 0.0 if lbar is None else O.mean_field_constant(lbar)
+    B = O.half_step_propagator(O.one_body_remainder(s.h1, s.L, lbar), dt)
+    lo, Gu, Gd, _ = O.mixed_green(trial, Pu[None], Pd[None])
+    _, xb = O.force_bias(s.L, Gu, Gd, dt, 0.0, lbar)
+    et = O.reference_energy(s.h1, s.L, trial)
+    acc = 0.0
+    for xq, wq in zip(nodes, wts):
+        x = np.array([[xq]])
+        V = O.one_body_operator(s.L, x, xb, dt)
+        ln, _ = O.trial_overlap(trial, O.propagate(B, V, Pu[None], 30),
+                                O.propagate(B, V, Pd[None], 30))
+        lmf = 0.0 if lbar is None else O.mean_field_log(x, xb, lbar, dt)
+        acc += wq * np.exp(O.log_importance(ln - lo + lmf, x, xb, dt, et, e0))[0]
+    return acc, et, lbar
+
+
+@pytest.mark.parametrize("mf", [0, 1])
+def test_step_importance_factor_is_the_projected_overlap(fock4, mf):
+    """One field, so the field integral is exact: the Gaussian average of the
+    hybrid factor I(x) (overlap ratio, shift factor, mean-field scalar and
+    both constants) equals <Psi_T| B_half exp(-dt/2 (L - lbar)^2) B_half
+    |phi> / <Psi_T|phi> exp(dt (E_T - E_0)), with E_0 read off the Fock-space
+    identity H = H1' + 1/2 (L - lbar)^2 + E_0 rather than from the oracle."""
+    s = small_system(M=4, n_up=2, n_dn=1, n_chol=1, seed=5, l_sigma=0.3)
+    rng = np.random.default_rng(4)
+    Pu, Pd = rand_walker(rng, 4, 2), rand_walker(rng, 4, 1)
+    dt = 0.05
+    nodes, wts = np.polynomial.hermite_e.hermegauss(60)
+    wts = wts / math.sqrt(2 * math.pi)
+    got, et, lbar = _step_average(s, Pu, Pd, dt, mf, nodes, wts)
+    lb = np.zeros(1) if lbar is None else lbar
+    eye = np.eye(fock4.dim)
+    H = fock4.hamiltonian(s.h1, eri_from_chol(s.L)).toarray()
+    H1 = fock4.one_body(O.one_body_remainder(s.h1, s.L, lbar).astype(complex)).toarray()
+    Lh = fock4.one_body(s.L[0].astype(complex)).toarray() - lb[0] * eye
+    e0 = (H - H1 - 0.5 * Lh @ Lh)[0, 0]
+    Bh = expm(-0.5 * dt * H1)
+    trial = O.Trial.from_system(s)
+    psi_t = fock4.slater(trial.D_up[0], trial.D_dn[0])
+    phi = fock4.slater(Pu, Pd)
+    target = (np.vdot(psi_t, Bh @ expm(-0.5 * dt * Lh @ Lh) @ Bh @ phi)
+              / np.vdot(psi_t, phi) * np.exp(dt * (et - e0)))
+    assert abs(got - target) < 1e-10 * abs(target)
+
+
+@pytest.mark.parametrize("mf", [0, 1])
+def test_local_energy_weight_is_the_mean_importance_factor(mf):
+    """Sec. II's local-energy form: the factor exp(-dt (Re E_L - E_T)) that a
+    step in that form gives a walker (its cut divided out) is the modulus of
+    the Gaussian average of the hybrid factor up to O(dt^2): the gap falls
+    by four when dt halves (one field, so the average is exact)."""
+    s = small_system(M=4, n_up=2, n_dn=1, n_chol=1, seed=5, l_sigma=0.3)
+    rng = np.random.default_rng(4)
+    Pu, Pd = rand_walker(rng, 4, 2), rand_walker(rng, 4, 1)
+    nodes, wts = np.polynomial.hermite_e.hermegauss(60)
+    wts = wts / math.sqrt(2 * math.pi)
+    gaps = []
+    for dt in (0.02, 0.01):
+        avg, _, _ = _step_average(s, Pu, Pd, dt, mf, nodes, wts)
+        run = O.OracleRun(s.replace(dtau=dt, n_walkers=1, weight_mode=1, mf_subtract=mf,
+                                    fb_cap=0.0, ortho_every=0, measure_every=0,
+                                    pc_every=0))
+        run.Phi_up, run.Phi_dn = Pu[None].copy(), Pd[None].copy()
+        run.logO, _ = O.trial_overlap(run.trial, run.Phi_up, run.Phi_dn)
+        run.step()
+        cut = max(0.0, math.cos(run.last["lnR"][0].imag))
+        assert cut > 0.5
+        gaps.append(abs(run.weight[0] / cut - abs(avg)))
+    assert gaps[1] < 3e-4 and 3.5 < gaps[0] / gaps[1] < 4.5
+
+
+def test_mean_field_subtraction_shrinks_the_phase():
+    """What the subtraction is for: with the mean field taken out, the
+    overlap ratios' phases (the phaseless cut's argument) are smaller."""
+    s = small_system(M=6, n_up=2, n_dn=2, n_chol=8, seed=3, n_walkers=64, dtau=0.02,
+                     l_sigma=0.3, ortho_every=2, measure_every=0, pc_every=0, fb_cap=0.0)
+    spread = []
+    for mf in (0, 1):
+        run = O.OracleRun(s.replace(mf_subtract=mf))
+        ph = []
+        for _ in range(4):
+            run.step()
+            ph.append(np.abs(run.last["lnR"].imag))
+        spread.append(np.mean(ph))
+    assert spread[1] < 0.5 * spread[0]
+
+
 def test_taylor_truncation_bound():
     rng = np.random.default_rng(9)
     for scale in (0.05, 0.3, 0.8):
