@@ -75,6 +75,24 @@ typedef enum {
   AFQMC_BF16X3 = 4
 } afqmc_precision;
 
+/* Weight update after each step (Sec. II), both with the phaseless cut
+ * max(0, cos(dtheta)), dtheta the phase of the walker's overlap ratio
+ * <Psi_T|phi'>/<Psi_T|phi> (times the mean-field scalar factor when
+ * mf_subtract is set):
+ * HYBRID:        W <- W |I| cut, I = ratio * exp(sum_g x_g xbar_g -
+ *                xbar_g^2/2) * exp(dtau (E_T - E_0)); E_0 = -1/2 sum_g
+ *                lbar_g^2 with the mean field subtracted, else 0.
+ * LOCAL_ENERGY:  W <- W exp(-dtau (Re E_L - E_T)) cut, E_L the local energy
+ *                of the walker before the move (one energy evaluation per
+ *                step). One-determinant trials only (AFQMC_E_INVALID
+ *                otherwise): the walkers start at the reference
+ *                determinant, where a multi-determinant trial's
+ *                per-determinant energies are 0/0 limits. */
+typedef enum {
+  AFQMC_WEIGHT_HYBRID = 0,
+  AFQMC_WEIGHT_LOCAL_ENERGY = 1
+} afqmc_weight_mode;
+
 typedef struct {
   int32_t M;             /* orbitals (one-particle basis size), 1..256 */
   int32_t n_up, n_dn;    /* electrons per spin, 0..M each, n_up + n_dn >= 1 */
@@ -123,7 +141,13 @@ typedef struct {
                             arrived; outside a server the field is only
                             validated. */
   int32_t cs_size;       /* runs in the group, 2..16 (0 when cs_group is 0) */
-  int32_t reserved[2];   /* must be zero */
+  int32_t weight_mode;   /* afqmc_weight_mode (Sec. II): 0 = hybrid
+                            importance factor, 1 = local-energy form */
+  int32_t mf_subtract;   /* 1: subtract the mean field lbar_g = <L_g> of the
+                            reference determinant from the Cholesky
+                            operators (the propagator's exact form is
+                            unchanged; the phaseless cut sees smaller
+                            phases); 0: none */
 } afqmc_params;
 
 /* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,

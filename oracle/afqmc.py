@@ -461,6 +461,10 @@ class OracleRun:
         self.h1 = np.asarray(s.h1, dtype=np.float64)
         self.L = np.asarray(s.L, dtype=np.float64)
         self.weight_mode = getattr(s, "weight_mode", 0)
+        if self.weight_mode == 1 and s.n_det > 1:
+            # the walkers start at the reference determinant, where the
+            # other determinants' overlaps vanish and their energies are 0/0
+            raise ValueError("the local-energy weight form needs a one-determinant trial")
         # mean field of the reference determinant (zero: no subtraction)
         self.lbar = (mean_field(self.L, self.trial.D_up[0], self.trial.D_dn[0])
                      if getattr(s, "mf_subtract", 0) else None)

@@ -35,7 +35,8 @@ class afqmc_params(C.Structure):
                 ("e_shift", C.c_double), ("fp64_islands", C.c_int32),
                 ("graphs", C.c_int32), ("autotune", C.c_int32),
                 ("weight_cap", C.c_int32), ("cs_group", C.c_int32),
-                ("cs_size", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("cs_size", C.c_int32), ("weight_mode", C.c_int32),
+                ("mf_subtract", C.c_int32)]
 
 
 class afqmc_tuning(C.Structure):
@@ -170,7 +171,7 @@ class Inputs:
                  n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
                  measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
                  e_shift=None, fp64_islands=False, graphs=True, autotune=True,
-                 weight_cap=0, cs_group=0, cs_size=0):
+                 weight_cap=0, cs_group=0, cs_size=0, weight_mode=0, mf_subtract=0):
         self.h1 = np.ascontiguousarray(h1, dtype=np.float64)
         self.L = np.ascontiguousarray(L, dtype=np.float64)
         self.C_up = np.ascontiguousarray(C_up, dtype=np.float64)
@@ -201,6 +202,8 @@ class Inputs:
         p.weight_cap = int(weight_cap)
         p.cs_group = int(cs_group)
         p.cs_size = int(cs_size)
+        p.weight_mode = int(weight_mode)
+        p.mf_subtract = int(mf_subtract)
         self.params = p
 
     @classmethod
@@ -210,7 +213,8 @@ class Inputs:
                     ortho_every=system.ortho_every,
                     measure_every=system.measure_every,
                     pc_every=system.pc_every, taylor_order=system.taylor_order,
-                    fb_cap=system.fb_cap, weight_cap=system.weight_cap)
+                    fb_cap=system.fb_cap, weight_cap=system.weight_cap,
+                    weight_mode=system.weight_mode, mf_subtract=system.mf_subtract)
         args.update(kw)
         return cls(system.h1, system.L, system.C_up, system.C_dn,
                    system.occ_up, system.occ_dn, system.ci, **args)

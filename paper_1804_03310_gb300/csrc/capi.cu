@@ -72,6 +72,12 @@ struct afqmc_ctx {
   double* PsiT64;
   double *weight, *scan, *wnew, *escalar, *lr;
   double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
+  // mean-field subtraction: lbar_g of the reference determinant [G], the
+  // per-walker log of the scalar factor it puts on a propagated walker [W],
+  // and -E_0 = 1/2 sum_g lbar_g^2
+  double* lbar;
+  double2* lmf;
+  double e_mf;
   int *parent, *status;
   double wref_host;   // staging of a restored reference weight
   long long* ctr;   // device step counters: [0] completed steps, [1] measurements
@@ -285,23 +291,19 @@ afqmc_status force_bias_contraction(afqmc_ctx* c) {
   return AFQMC_OK;
 }
 
+// Local energies of the current walkers into c->eloc. A single-determinant
+// trial needs X from force_bias_contraction at these walkers.
 template <typename T>
-afqmc_status measure_T(afqmc_ctx* c, bool record) {
+afqmc_status local_energy_T(afqmc_ctx* c) {
   const int W = c->W, M = c->M, G = c->G;
+  KTimer t(c, 7);
   if (c->md) {
-    KTimer t(c, 7);
     LK(launch_md_energy<T>(c->st, c->mdt, W, M, c->nu, c->nd, G, (const T*)c->Theta, c->ldt,
                            c->dn_off, c->logdet, (const T*)c->LtilA, c->ldg, c->gdn_off,
                            c->eloc, c->fp64_islands));
-    LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, c->ctr, record ? c->hist : nullptr,
-                           kHist, c->escalar));
-    if (record) c->n_meas += 1;
     return AFQMC_OK;
   }
-  afqmc_status s = force_bias_contraction<T>(c);
-  if (s != AFQMC_OK) return s;
   {
-    KTimer t(c, 7);
     long zoff = 0;
     for (int sig = 0; sig < 2; ++sig) {
       const int ns = sig ? c->nd : c->nu;
@@ -326,7 +328,19 @@ afqmc_status measure_T(afqmc_ctx* c, bool record) {
                                c->xsplit, 2L * W * c->ldx, (const T*)c->Theta, c->ldt,
                                c->dn_off, (const T*)c->Z, c->Jp[0], c->Jp[1], c->eloc));
   }
-  LK(launch_mixed_energy(c->st, W, c->weight, c->eloc, c->ctr, record ? c->hist : nullptr,
+  return AFQMC_OK;
+}
+
+template <typename T>
+afqmc_status measure_T(afqmc_ctx* c, bool record) {
+  afqmc_status s = AFQMC_OK;
+  if (!c->md) {
+    s = force_bias_contraction<T>(c);
+    if (s != AFQMC_OK) return s;
+  }
+  s = local_energy_T<T>(c);
+  if (s != AFQMC_OK) return s;
+  LK(launch_mixed_energy(c->st, c->W, c->weight, c->eloc, c->ctr, record ? c->hist : nullptr,
                          kHist, c->escalar));
   if (record) c->n_meas += 1;
   return AFQMC_OK;
@@ -448,11 +462,16 @@ afqmc_status step_T(afqmc_ctx* c) {
   const double dt = c->p.dtau;
   afqmc_status s = force_bias_contraction<T>(c);
   if (s != AFQMC_OK) return s;
+  const bool local = c->p.weight_mode == AFQMC_WEIGHT_LOCAL_ENERGY;
+  if (local) {   // the local-energy weight form needs E_L before the move
+    s = local_energy_T<T>(c);
+    if (s != AFQMC_OK) return s;
+  }
   {
     KTimer t(c, 1);
     LK(launch_fields<T>(c->st, W, G, (const T*)c->X, c->ldx, c->xsplit, 2L * W * c->ldx,
                         sqrt(dt), c->p.fb_cap, c->p.seed, c->p.run_id, c->ctr, (T*)c->S,
-                        c->ldS, (T*)c->xbar, c->lw));
+                        c->ldS, (T*)c->xbar, c->lw, c->lbar, c->lmf));
   }
   {
     KTimer t(c, 2);
@@ -481,9 +500,9 @@ afqmc_status step_T(afqmc_ctx* c) {
   {
     KTimer t(c, 5);
     LK(launch_weights(c->st, W, c->md ? c->logO_new : nullptr, c->md ? nullptr : c->logdet,
-                      c->lw, dt, c->e_shift, (double)c->p.weight_cap,
-                      c->wnew, c->weight, c->logO,
-                      c->ctr));
+                      c->lw, c->lmf, local ? c->eloc : nullptr, dt,
+                      local ? c->e_shift : c->e_shift + c->e_mf, (double)c->p.weight_cap,
+                      c->wnew, c->weight, c->logO, c->ctr));
   }
   c->step += 1;
   const long n = c->step;
@@ -510,8 +529,13 @@ afqmc_status step_T(afqmc_ctx* c) {
 afqmc_status validate_sizes(const afqmc_params* p) {
   afqmc_ctx* c = nullptr;
   if (!p) return fail(c, AFQMC_E_INVALID, "null argument");
-  for (int i = 0; i < 2; ++i)
-    if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
+  if (p->weight_mode != AFQMC_WEIGHT_HYBRID && p->weight_mode != AFQMC_WEIGHT_LOCAL_ENERGY)
+    return fail(c, AFQMC_E_INVALID, "weight_mode must be 0 (hybrid) or 1 (local energy)");
+  if (p->mf_subtract != 0 && p->mf_subtract != 1)
+    return fail(c, AFQMC_E_INVALID, "mf_subtract must be 0 or 1");
+  if (p->weight_mode == AFQMC_WEIGHT_LOCAL_ENERGY && p->n_det > 1)
+    return fail(c, AFQMC_E_INVALID,
+                "the local-energy weight form needs a one-determinant trial");
   if (p->cs_group < 0) return fail(c, AFQMC_E_INVALID, "cs_group must be >= 0");
   if (p->cs_group == 0 ? p->cs_size != 0 : (p->cs_size < 2 || p->cs_size > 16))
     return fail(c, AFQMC_E_INVALID, "cs_size must be 2..16 in a correlated-sampling group, else 0");
@@ -636,12 +660,31 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(c->PsiT64, psiT_h.data(), psiT_h.size() * sizeof(double),
                      cudaMemcpyHostToDevice, st));
-  // H1' = h1 - 1/2 sum_g L_g L_g
-  LK(launch_h1_remainder(st, M, G, h1, L, h1p));
+  // half-rotated L~_g = D^T L_g (rows: up orbitals, then down), plus D^T h1
+  LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, L, M, MM, 0.0, Ltil, M,
+                  (long)N * M, G));
+  LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, h1, M, 0, 0.0,
+                  Ltil + (size_t)G * N * M, M, 0, 1));
+  // X_g = tr(L~_g D) and tr(h~ D) of the reference determinant (phi = D, so
+  // Theta = D and theta = vec(D^T)), FP64: the trial energy's Coulomb and
+  // one-body terms and, with mean-field subtraction, lbar_g
+  double *et_x, *et_z;
+  TM(et_x, G + 1);
+  TM(et_z, (size_t)std::max(c->nu, c->nd) * M + 1);
+  std::vector<double> et_xh(G + 1);
+  LK(launch_gemv_rows(st, G + 1, (long)N * M, Ltil, (long)N * M, PsiT, et_x));
+  CK(cudaMemcpyAsync(et_xh.data(), et_x, (G + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (c->lbar)
+    CK(cudaMemcpyAsync(c->lbar, et_x, G * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // H1' = h1 - 1/2 sum_g L_g L_g (+ sum_g lbar_g L_g)
+  LK(launch_h1_remainder(st, M, G, h1, L, c->lbar, h1p));
   // B_half = exp(-dt/2 H1'): scaling and squaring of a Taylor series
   std::vector<double> hp(MM);
   CK(cudaMemcpyAsync(hp.data(), h1p, MM * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  c->e_mf = 0.0;
+  if (c->lbar)
+    for (int g = 0; g < G; ++g) c->e_mf += 0.5 * et_xh[g] * et_xh[g];
   double fro = 0.0;
   for (double v : hp) fro += v * v;
   fro = sqrt(fro) * 0.5 * c->p.dtau;
@@ -660,21 +703,9 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     LK(gemm<double>(st, false, false, M, M, M, 1.0, Bh, M, 0, Bh, M, 0, 0.0, tb, M, 0, 1));
     std::swap(Bh, tb);
   }
-  // half-rotated L~_g = D^T L_g (rows: up orbitals, then down), plus D^T h1
-  LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, L, M, MM, 0.0, Ltil, M,
-                  (long)N * M, G));
-  LK(gemm<double>(st, false, false, N, M, M, 1.0, PsiT, M, 0, h1, M, 0, 0.0,
-                  Ltil + (size_t)G * N * M, M, 0, 1));
-  // E_T = E_L of the reference determinant (phi = D, so Theta = D and
-  // theta = vec(D^T)), in FP64 whatever the step precision: tr(h~ D) and
-  // X_g = tr(L~_g D) from one product with the half-rotated vectors, the
-  // exchange term 1/2 theta^T Yx theta per spin below
-  double *et_x, *et_z;
-  TM(et_x, G + 1);
-  TM(et_z, (size_t)std::max(c->nu, c->nd) * M + 1);
-  std::vector<double> et_xh(G + 1);
-  LK(launch_gemv_rows(st, G + 1, (long)N * M, Ltil, (long)N * M, PsiT, et_x));
-  CK(cudaMemcpyAsync(et_xh.data(), et_x, (G + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // E_T = E_L of the reference determinant in FP64 whatever the step
+  // precision: the terms gathered above plus the exchange term
+  // 1/2 theta^T Yx theta per spin
   double e_exch = 0.0;
   // exchange part of the Eq. 5 tensor, per spin
   for (int sig = 0; sig < 2; ++sig) {
@@ -1101,7 +1132,7 @@ void advance_host(afqmc_ctx* c, long len, const GraphEntry* ge) {
 // active-orbital counts of a multi-determinant trial).
 struct Plan {
   int M, nu, nd, N, G, W, ndet, nact[2];
-  bool fp64, tcmode, split3, bf16, md, tc_taylor_ok, tc_bhalf_ok, tc_wide_ok;
+  bool fp64, tcmode, split3, bf16, md, mf, tc_taylor_ok, tc_bhalf_ok, tc_wide_ok;
   size_t es;
   long ldS, ldx, dn_off, ldt, Jp[2], gdn_off, ldg, ldV;
   int xsplit, xsplit_max;
@@ -1112,6 +1143,7 @@ Plan make_plan(const afqmc_params* p, int nact_up, int nact_dn) {
   P.M = p->M; P.nu = p->n_up; P.nd = p->n_dn; P.N = P.nu + P.nd; P.G = p->n_chol;
   P.W = p->n_walkers; P.ndet = p->n_det;
   P.md = P.ndet > 1;
+  P.mf = p->mf_subtract != 0;
   P.nact[0] = P.md ? nact_up : P.nu;
   P.nact[1] = P.md ? nact_dn : P.nd;
   P.fp64 = p->precision == AFQMC_FP64;
@@ -1222,6 +1254,10 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->lw, W * sizeof(double2));
   add(&c->eloc, W * sizeof(double2));
   add(&c->hist, kHist * sizeof(double2));
+  if (P.mf) {
+    add(&c->lbar, G * sizeof(double));
+    add(&c->lmf, W * sizeof(double2));
+  }
   add(&c->parent, W * sizeof(int));
   add(&c->status, sizeof(int));
   add(&c->ctr, 2 * sizeof(long long));

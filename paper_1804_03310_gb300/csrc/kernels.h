@@ -40,12 +40,14 @@ cudaError_t gemm(cudaStream_t st, bool ta, bool tb, int m, int n, int k, T alpha
 // K1 + K3: Philox fields, capped force bias, shifted fields and the log of
 // the importance factor sum_g (x xbar - xbar^2/2) per walker, at step
 // ctr[0]. X holds `nsplit` partial sums (split_stride elements apart) that
-// are added in order.
+// are added in order. With lbar [n_chol] (FP64, else NULL) the mean field is
+// subtracted from X before the bias is formed, and lmf[w] receives
+// -i sqrt(dt) sum_g (x_g - xbar_g) lbar_g.
 template <typename T>
 cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
                           int nsplit, long split_stride, double sqdt, double cap,
                           uint64_t seed, int run_id, const long long* ctr, T* S, long ldS,
-                          T* xbar, double2* lw);
+                          T* xbar, double2* lw, const double* lbar, double2* lmf);
 
 // K5 on the CUDA cores: Phi_out = sum_{n<=order} V^n Phi_in / n!, with V
 // [W][2][M][ldv].
@@ -63,13 +65,15 @@ cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
                            const T* Phi, const T* PsiT, T* Theta, long ldt, long dn_off,
                            double2* logdet, double2* Ainv, bool fp64_compute);
 
-// K7: hybrid weight and phaseless cut from the new log-overlap (logO_new, or
+// K7: weight and phaseless cut from the new log-overlap (logO_new, or
 // with logO_new NULL the sum of the two spins' log-determinants in
-// logdet [W][2]); ends the step (ctr[0] += 1). With cap > 0 a weight is
-// capped at cap * (*wref) when *wref > 0.
+// logdet [W][2]) plus the mean-field scalar lmf (NULL: none); hybrid form
+// from the importance log lw, or, with eloc non-NULL, the local-energy form
+// from the pre-move local energies. Ends the step (ctr[0] += 1). With
+// cap > 0 a weight is capped at cap * (*wref) when *wref > 0.
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
-                           const double2* logdet, const double2* lw, double dtau,
-                           double e_shift, double cap,
+                           const double2* logdet, const double2* lw, const double2* lmf,
+                           const double2* eloc, double dtau, double e_shift, double cap,
                            const double* wref, double* weight, double2* logO,
                            long long* ctr);
 
@@ -123,7 +127,7 @@ cudaError_t launch_gather_rows(cudaStream_t st, int W, long elems, const int* pa
 
 // Setup helpers (FP64).
 cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,
-                                const double* L, double* h1p);
+                                const double* L, const double* lbar, double* h1p);
 cudaError_t launch_scale_identity(cudaStream_t st, int M, const double* A, double s,
                                   double* out_I_plus, double* out_scaled);
 cudaError_t launch_yx_permute(cudaStream_t st, int n, int M, const double* gram,

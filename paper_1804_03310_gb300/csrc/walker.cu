@@ -67,7 +67,8 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
                               long split_stride, double sqdt_d, double cap_d, uint32_t k0,
                               uint32_t k1, int run_id, const long long* __restrict__ ctr,
                               T* __restrict__ S, long ldS, T* __restrict__ xbar,
-                              double2* __restrict__ lw) {
+                              double2* __restrict__ lw, const double* __restrict__ lbar,
+                              double2* __restrict__ lmf) {
   using C = typename FieldMath<T>::type;
   __shared__ double red[32];
   const int w = blockIdx.x;
@@ -80,6 +81,7 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
   T* Bi = Br + n_chol;
   const C sqdt = (C)sqdt_d, cap = (C)cap_d;
   C lre = 0, lim = 0;
+  double mre = 0.0, mim = 0.0;   // mean-field scalar, FP64
   const int nq = (n_chol + 3) >> 2;
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     // X summed over the K-split partials, in order; the loads are issued
@@ -113,9 +115,11 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
     for (int j = 0; j < 4; ++j) {
       const int g = 4 * q + j;
       if (g >= n_chol) break;
-      // xbar = -i sqrt(dt) X
+      // xbar = -i sqrt(dt) X, or -i sqrt(dt) (X - lbar) with the mean field
+      // subtracted (lbar real, so only the imaginary part moves)
+      const C xre = lbar ? (C)((double)xr[j] - lbar[g]) : xr[j];
       C br = sqdt * xi[j];
-      C bi = -sqdt * xr[j];
+      C bi = -sqdt * xre;
       if (!isfinite(br) || !isfinite(bi)) { br = 0; bi = 0; }
       if (cap > 0) {
         const C a = sqrt(br * br + bi * bi);
@@ -129,11 +133,20 @@ __global__ void fields_kernel(int n_chol, const T* __restrict__ X, long ldx, int
       Bi[g] = (T)bi;
       lre += x * br - C(0.5) * (br * br - bi * bi);
       lim += x * bi - br * bi;
+      if (lbar) {   // -i sqrt(dt) (x - xbar) lbar
+        mre += sqdt_d * (double)si * lbar[g];
+        mim -= sqdt_d * (double)sr * lbar[g];
+      }
     }
   }
   const double tre = block_sum((double)lre, red);
   const double tim = block_sum((double)lim, red);
   if (threadIdx.x == 0) lw[w] = make_double2(tre, tim);
+  if (lbar) {   // uniform over the block
+    const double mr = block_sum(mre, red);
+    const double mi = block_sum(mim, red);
+    if (threadIdx.x == 0) lmf[w] = make_double2(mr, mi);
+  }
 }
 
 // Complex value of the elimination's compute type R (double or float).
@@ -610,9 +623,14 @@ __global__ void logdet_sum_kernel(int W, const double2* __restrict__ ld,
 }
 
 // --------------------------------------------------------------- K7
+// Hybrid form: ln|I| = Re(ln R + lmf) + Re(lw) + dtau e_shift (e_shift
+// already holding E_T - E_0); local-energy form (eloc given): ln|I| =
+// -dtau (Re E_L - e_shift). Both cut by max(0, cos Im(ln R + lmf)).
 __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
                                const double2* __restrict__ logdet,
-                               const double2* __restrict__ lw, double dtau,
+                               const double2* __restrict__ lw,
+                               const double2* __restrict__ lmf,
+                               const double2* __restrict__ eloc, double dtau,
                                double e_shift, double cap, const double* __restrict__ wref,
                                double* __restrict__ weight,
                                double2* __restrict__ logO, long long* __restrict__ ctr) {
@@ -621,8 +639,9 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
   if (w >= W) return;
   const double2 ln = logO_new ? logO_new[w] : cadd(logdet[2 * w], logdet[2 * w + 1]);
   double2 lnR = csub(ln, logO[w]);
-  double2 l = lw[w];
-  double lnI_re = lnR.x + l.x + dtau * e_shift;
+  if (lmf) lnR = cadd(lnR, lmf[w]);
+  const double lnI_re =
+      eloc ? -dtau * (eloc[w].x - e_shift) : lnR.x + lw[w].x + dtau * e_shift;
   double wt = weight[w];
   double out = 0.0;
   if (wt != 0.0) {
@@ -924,18 +943,22 @@ __global__ void gather_rows_kernel(long elems, const int* __restrict__ parent,
     out[(long)j * elems + e] = in[(long)p * elems + e];
 }
 
+// H1' = h1 - 1/2 sum_g L_g L_g (+ sum_g lbar_g L_g with the mean field
+// subtracted, lbar non-null).
 __global__ void h1_remainder_kernel(int M, int n_chol, const double* __restrict__ h1,
                                     const double* __restrict__ L,
+                                    const double* __restrict__ lbar,
                                     double* __restrict__ h1p) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= M * M) return;
   int i = e / M, j = e - i * M;
-  double s = 0.0;
+  double s = 0.0, m = 0.0;
   for (int g = 0; g < n_chol; ++g) {
     const double* Lg = L + (long)g * M * M;
     for (int k = 0; k < M; ++k) s = fma(Lg[i * M + k], Lg[k * M + j], s);
+    if (lbar) m = fma(lbar[g], Lg[e], m);
   }
-  h1p[e] = h1[e] - 0.5 * s;
+  h1p[e] = h1[e] - 0.5 * s + m;
 }
 
 __global__ void scale_identity_kernel(int M, const double* __restrict__ A, double s,
@@ -1056,10 +1079,10 @@ template <typename T>
 cudaError_t launch_fields(cudaStream_t st, int W, int n_chol, const T* X, long ldx,
                           int nsplit, long split_stride, double sqdt, double cap,
                           uint64_t seed, int run_id, const long long* ctr, T* S, long ldS,
-                          T* xbar, double2* lw) {
+                          T* xbar, double2* lw, const double* lbar, double2* lmf) {
   fields_kernel<T><<<W, 128, 0, st>>>(n_chol, X, ldx, nsplit, split_stride, sqdt, cap,
                                       (uint32_t)seed, (uint32_t)(seed >> 32), run_id, ctr,
-                                      S, ldS, xbar, lw);
+                                      S, ldS, xbar, lw, lbar, lmf);
   return cudaGetLastError();
 }
 
@@ -1130,11 +1153,12 @@ cudaError_t launch_overlap(cudaStream_t st, int W, int M, int n_up, int n_dn,
 }
 
 cudaError_t launch_weights(cudaStream_t st, int W, const double2* logO_new,
-                           const double2* logdet, const double2* lw, double dtau,
-                           double e_shift, double cap, const double* wref, double* weight,
-                           double2* logO, long long* ctr) {
-  weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, logdet, lw, dtau, e_shift,
-                                                     cap, wref, weight, logO, ctr);
+                           const double2* logdet, const double2* lw, const double2* lmf,
+                           const double2* eloc, double dtau, double e_shift, double cap,
+                           const double* wref, double* weight, double2* logO,
+                           long long* ctr) {
+  weights_kernel<<<blocks_for(W, 256), 256, 0, st>>>(W, logO_new, logdet, lw, lmf, eloc, dtau,
+                                                     e_shift, cap, wref, weight, logO, ctr);
   return cudaGetLastError();
 }
 
@@ -1222,8 +1246,9 @@ template cudaError_t launch_gather_rows<double2>(cudaStream_t, int, long, const 
                                                  const double2*, double2*);
 
 cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,
-                                const double* L, double* h1p) {
-  h1_remainder_kernel<<<blocks_for((long)M * M, 128), 128, 0, st>>>(M, n_chol, h1, L, h1p);
+                                const double* L, const double* lbar, double* h1p) {
+  h1_remainder_kernel<<<blocks_for((long)M * M, 128), 128, 0, st>>>(M, n_chol, h1, L, lbar,
+                                                                     h1p);
   return cudaGetLastError();
 }
 
@@ -1301,7 +1326,8 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
 #define AFQMC_INST(T)                                                                    \
   template cudaError_t launch_fields<T>(cudaStream_t, int, int, const T*, long, int,    \
                                         long, double, double, uint64_t, int,            \
-                                        const long long*, T*, long, T*, double2*);      \
+                                        const long long*, T*, long, T*, double2*,       \
+                                        const double*, double2*);                       \
   template cudaError_t launch_taylor<T>(cudaStream_t, int, int, int, int, const T*, long,\
                                         const T*, T*);                                  \
   template cudaError_t launch_overlap<T>(cudaStream_t, int, int, int, int, const T*,    \

@@ -72,10 +72,14 @@ def test_invalid_inputs_rejected_before_device(lib, mutate, needle):
     (dict(dtau=-1.0), "dtau"),
     (dict(n_walkers=0), "n_walkers"),
     (dict(precision=9), "precision"),
+    (dict(weight_mode=2), "weight_mode"),
+    (dict(mf_subtract=-1), "mf_subtract"),
+    (dict(weight_mode=1, n_det=2), "one-determinant"),
 ])
 def test_invalid_params_rejected(lib, kw, needle):
     from paper_1804_03310_gb300 import AfqmcError
-    s = small_system(M=6, n_up=2, n_dn=2, n_chol=3)
+    kw = dict(kw)
+    s = small_system(M=6, n_up=2, n_dn=2, n_chol=3, n_det=kw.pop("n_det", 1))
     with pytest.raises(AfqmcError) as e:
         _create(s, **kw)
     assert e.value.status == 1 and needle in str(e.value)
