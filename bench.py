@@ -460,11 +460,13 @@ def energy_check(precision, n_steps=600):
             "mean_mHa": round(float(np.mean(d)), 6)}
 
 
-def serving_leg(precision, n_runs=20, rate=20.0, seed=5, blocks=10, steps=50):
+def serving_leg(precision, n_runs=20, rate=20.0, seed=5, blocks=10, steps=50, mf_subtract=1):
     """The serving loop under a Poisson stream of independent runs drawn from
     the serving mix at its stated ranges: M in 20..200, N per spin M/5..M/3,
     n_chol 4M..6M, 128..2048 walkers, dt = 0.005, `blocks` blocks of `steps`
-    steps each (energy once per block, comb every 10 steps). Inputs are
+    steps each (energy once per block, comb every 10 steps), with the
+    reference determinant's mean field subtracted (without it the phaseless
+    cut empties a third of these random-trial populations). Inputs are
     drawn before the clock starts; submissions follow the arrival times;
     runs use the fixed launch heuristics (no per-request tuning); p50/p99 are
     the server's own per-block latencies. Offered load = the submitted runs'
@@ -475,7 +477,8 @@ def serving_leg(precision, n_runs=20, rate=20.0, seed=5, blocks=10, steps=50):
     from paper_1804_03310_gb300 import Inputs, Server
     rng = np.random.default_rng(seed)
     systems = [serving_run(rng, k) for k in range(n_runs)]
-    runs = [Inputs.from_system(sy, precision=precision, autotune=False) for sy in systems]
+    runs = [Inputs.from_system(sy, precision=precision, autotune=False,
+                               mf_subtract=mf_subtract) for sy in systems]
     gaps = rng.exponential(1.0 / rate, size=n_runs)
     srv = Server()
     t0 = time.perf_counter()
@@ -499,7 +502,8 @@ def serving_leg(precision, n_runs=20, rate=20.0, seed=5, blocks=10, steps=50):
     offered = sum(sy.n_walkers for sy in systems) * blocks * steps
     return {"workload": (f"{n_runs} runs, Poisson arrivals {rate}/s, M 20..200, N/spin M/5..M/3, "
                          f"n_chol 4M..6M, W 128..2048, {blocks} blocks of {steps} steps "
-                         f"(comb every 10), {precision}"),
+                         f"(comb every 10), {precision}, mean field "
+                         f"{'subtracted' if mf_subtract else 'kept'}"),
             "m_drawn": [int(sy.M) for sy in systems],
             "completed": int(st["completed"]), "failed": int(st["failed"]),
             "p50_block_ms": round(st["p50_ms"], 3), "p99_block_ms": round(st["p99_ms"], 3),
@@ -717,6 +721,45 @@ def shapes_leg(precision):
     return out
 
 
+def weight_forms_leg(s, precision, n_steps=200):
+    """The weight forms and the mean-field subtraction (Sec. II) on the bench
+    workload: walker-steps/s of each (two timed blocks; the local-energy form
+    evaluates the energy every step), the paired energy deviation of each
+    against the FP64 GPU path with the same draws (comb off, n_steps steps,
+    one measurement every 20), and the walkers the phaseless cut leaves
+    alive after 60 steps at dt = 0.02 (comb off) with and without the
+    subtraction."""
+    import numpy as np
+    from paper_1804_03310_gb300 import Afqmc
+    out = {}
+    for mode, mf in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        key = f"{'local_energy' if mode else 'hybrid'}{'_mf' if mf else ''}"
+        v = s.replace(weight_mode=mode, mf_subtract=mf)
+        ms, _ = _blocks(v, precision, 2)
+        r = {"value": round(s.n_walkers * BLOCK / (ms / 1e3), 1), "ms_per_block": round(ms, 3)}
+        if mode or mf:
+            p = v.replace(pc_every=0, measure_every=20)
+            e = {}
+            for prec in ("fp64", precision):
+                with Afqmc.from_system(p, precision=prec) as ctx:
+                    ctx.afqmc_propagate(n_steps)
+                    e[prec] = ctx.afqmc_energy_history()[:, 1]
+            d = (e[precision] - e["fp64"]) * 1e3
+            r["paired_max_abs_mHa"] = round(float(np.max(np.abs(d))), 6)
+            r["e_fp64_last"] = round(float(e["fp64"][-1]), 6)
+        out[key] = r
+    alive = {}
+    for mf in (0, 1):
+        p = s.replace(pc_every=0, measure_every=0, dtau=0.02, mf_subtract=mf)
+        with Afqmc.from_system(p, precision=precision) as ctx:
+            ctx.afqmc_propagate(60)
+            w, _ = ctx.afqmc_weights()
+        alive["mean_field_subtracted" if mf else "plain"] = int(np.count_nonzero(w > 0))
+    out["alive_after_60_steps_dt0.02"] = alive
+    out["paired_steps"] = n_steps
+    return out
+
+
 def dtype_of(precision):
     return {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3",
             "bf16x3": "bf16x3"}[precision]
@@ -784,6 +827,7 @@ def main():
         leg("batch", lambda: batch_leg(args.precision))
         leg("ndet_sweep", lambda: ndet_leg(args.precision))
         leg("correlated_sampling", lambda: cs_leg(args.precision))
+        leg("weight_forms", lambda: weight_forms_leg(s, args.precision))
     if not args.no_cpu_baseline and world == 1:
         v, cores, sample = cpu_oracle(args.workload)
         line["cpu_baseline"] = {"value": round(v, 2), "unit": METRIC, "cores": cores,

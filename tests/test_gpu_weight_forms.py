@@ -53,9 +53,16 @@ def test_c1_twenty_steps_fp64(mode, mf):
     (70, 5, 9, 130, 40),
 ])
 def test_ragged_sizes_fp64(M, nu, nd, G, W, mode, mf):
-    s = small_system(M=M, n_up=nu, n_dn=nd, n_chol=G, seed=M + G, l_sigma=0.08,
-                     n_walkers=W, dtau=0.02, ortho_every=3, measure_every=4,
-                     pc_every=4, trial="random").replace(weight_mode=mode, mf_subtract=mf)
+    """The gentler of the two ragged-size recipes (eigenvector trial,
+    dt = 0.01): in the local-energy form a weight takes dt E_L each step,
+    and with a random trial at dt = 0.02 the M = 70 walkers reach the trial's
+    nodes within a few steps, where |E_L| grows to 1e3-1e4 Ha and its
+    conditioning, not the kernels, decides the last digits (the oracle's
+    own E_L moves by 1e-12 relative under a 1e-14 change of the walker)."""
+    s = small_system(M=M, n_up=nu, n_dn=nd, n_chol=G, seed=M + G,
+                     l_sigma=0.05 * (10.0 / M) ** 0.5, n_walkers=W, dtau=0.01,
+                     ortho_every=3, measure_every=4, pc_every=4,
+                     trial="eig").replace(weight_mode=mode, mf_subtract=mf)
     side_by_side(s, "fp64", 8, 1e-10, energy_at=(4, 8))
 
 
@@ -123,4 +130,4 @@ def test_mean_field_subtraction_keeps_more_walkers_alive():
         alive[mf] = int(np.count_nonzero(w > 0))
         gpu.close()
     print("walkers alive after 60 steps (no subtraction, subtraction):", alive)
-    assert alive[1] >= alive[0]
+    assert alive[1] > 4 * alive[0]
