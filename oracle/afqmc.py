@@ -46,7 +46,11 @@ every function follows one step of the method as the paper states it:
   weighted sums over determinants, each from a full inverse (no
   Sherman-Morrison-Woodbury shortcut here).
 * Population control by simple combing (Sec. V, final comments) with a
-  blocked FP64 prefix sum whose order is fixed below.
+  blocked FP64 prefix sum whose order is fixed below. After a comb every
+  walker has the common weight S/n; the run divides it out (weights 1) and
+  keeps ln(S/n) in a log scale, so that a population whose energy lies far
+  below E_T cannot overflow. Every estimator is a ratio of weights, so
+  nothing observable changes.
 
 Green's function convention: ``G^sigma_ij = <c+_i c_j>`` (mixed), so for a
 determinant trial D and walker Phi, ``G^T = Phi (D^H Phi)^-1 D^H``.
@@ -481,6 +485,7 @@ class OracleRun:
         self.e_shift = e_shift
         self.step_count = 0
         self.w_ref = 1.0            # common weight of the last comb (weight cap)
+        self.log_scale = 0.0        # sum of ln(S/n) divided out at the combs
         self.energies = []          # (step, mixed energy, E_L per walker)
         self.last = {}
 
@@ -540,11 +545,12 @@ class OracleRun:
     def population_control(self):
         u = comb_uniform(self.s.seed, self.s.run_id, self.step_count)
         parent, wnew = comb(self.weight, u)
-        self.w_ref = wnew
+        self.log_scale += float(np.log(wnew))
+        self.w_ref = 1.0
         self.Phi_up = self.Phi_up[parent].copy()
         self.Phi_dn = self.Phi_dn[parent].copy()
         self.logO = self.logO[parent].copy()
-        self.weight = np.full(self.walker_ids.size, wnew)
+        self.weight = np.ones(self.walker_ids.size)
         self.last["parent"] = parent
         return parent
 

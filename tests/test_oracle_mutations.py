@@ -50,6 +50,7 @@ FAST_PINS = [
     ("local_weight", lambda: pins.test_local_energy_weight_is_the_mean_importance_factor(0)),
     ("local_weight_mf", lambda: pins.test_local_energy_weight_is_the_mean_importance_factor(1)),
     ("mf_phase", lambda: pins.test_mean_field_subtraction_shrinks_the_phase()),
+    ("comb_renormalised", lambda: pins.test_renormalised_comb_changes_nothing_observable()),
 ]
 SLOW_PINS = {
     "hs_quadrature": lambda: pins.test_hs_importance_factor_quadrature(_FOCK, _SYS4),
@@ -262,6 +263,18 @@ def energy_after_move(self):
     self.step_count += 1
 
 
+def comb_scale_of_sum(self):
+    u = P.comb_uniform(self.s.seed, self.s.run_id, self.step_count)
+    parent, wnew = O.comb(self.weight, u)
+    self.log_scale += float(np.log(wnew * len(self.weight)))   # slip: ln S, not ln(S/n)
+    self.w_ref = 1.0
+    self.Phi_up = self.Phi_up[parent].copy()
+    self.Phi_dn = self.Phi_dn[parent].copy()
+    self.logO = self.logO[parent].copy()
+    self.weight = np.ones(self.walker_ids.size)
+    return parent
+
+
 SLIPS = {
     "exchange_sign": [(O, "local_energy_rotated", exchange_sign)],
     "importance_exponent": [(O, "importance_log", importance_exponent)],
@@ -286,6 +299,7 @@ SLIPS = {
     "mf_constant_dropped": [(O, "log_importance", mf_constant_dropped)],
     "local_weight_sign": [(O, "update_weights_local", local_weight_sign)],
     "local_energy_after_move": [(O.OracleRun, "step", energy_after_move)],
+    "comb_log_scale": [(O.OracleRun, "population_control", comb_scale_of_sum)],
 }
 # slips whose natural pin is one of the slow ones
 NEEDS = {"importance_exponent": ["hs_quadrature"], "x_plus_xbar": ["hs_quadrature"]}

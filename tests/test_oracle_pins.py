@@ -502,6 +502,39 @@ def test_weight_cap_option():
 # ---------------------------------------------------------------- comb
 
 
+class _KeepScaleRun(O.OracleRun):
+    """The run without the renormalisation: after a comb every walker keeps
+    the common weight S/n."""
+
+    def population_control(self):
+        u = P.comb_uniform(self.s.seed, self.s.run_id, self.step_count)
+        parent, wnew = O.comb(self.weight, u)
+        self.w_ref = wnew
+        self.Phi_up = self.Phi_up[parent].copy()
+        self.Phi_dn = self.Phi_dn[parent].copy()
+        self.logO = self.logO[parent].copy()
+        self.weight = np.full(self.walker_ids.size, wnew)
+        return parent
+
+
+def test_renormalised_comb_changes_nothing_observable():
+    """Dividing the common weight S/n out at each comb (and keeping its log)
+    leaves the walkers and the mixed energies as they are: the weights times
+    exp(log_scale) are the weights of the run that keeps S/n."""
+    s = small_system(M=6, n_up=2, n_dn=2, n_chol=8, seed=3, n_walkers=32, dtau=0.05,
+                     l_sigma=0.3, ortho_every=2, measure_every=3, pc_every=3)
+    a = O.OracleRun(s, e_shift=-40.0)
+    b = _KeepScaleRun(s, e_shift=-40.0)
+    for _ in range(12):
+        a.step()
+        b.step()
+    assert a.log_scale != 0.0
+    assert np.abs(a.Phi_up - b.Phi_up).max() < 1e-12
+    assert np.abs(a.weight * np.exp(a.log_scale) - b.weight).max() < 1e-11 * b.weight.max()
+    for (sa, ea, _), (sb, eb, _) in zip(a.energies, b.energies):
+        assert sa == sb and abs(ea - eb) < 1e-11 * abs(eb)
+
+
 def test_blocked_prefix_sum_and_comb():
     rng = np.random.default_rng(6)
     for n in (1, 7, 32, 33, 100, 2048):
