@@ -123,9 +123,10 @@ typedef struct {
   int32_t weight_cap;    /* 0 (default): no cap, the paper's hybrid weights.
                             k > 0: after each step a walker's weight is capped
                             at k times the reference weight, the common weight
-                            the last comb gave every walker (1 before the
-                            first comb; a restored checkpoint takes the mean
-                            of its positive weights). Guards long runs against
+                            of the last comb (1, since the comb divides it out,
+                            see afqmc_log_weight_scale; 1 before the first
+                            comb; a restored checkpoint takes the mean of its
+                            positive weights). Guards long runs against
                             a walker near a node of the trial taking a runaway
                             weight, at the price of a bias that vanishes as k
                             grows. */
@@ -195,7 +196,8 @@ afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t n_steps);
 afqmc_status afqmc_orthonormalize(afqmc_ctx* ctx);
 
 /* Comb population control now (Sec. V final comments); offset drawn from
- * Philox stream 1 at the current step counter. */
+ * Philox stream 1 at the current step counter. Every walker leaves with
+ * weight 1; the common weight S/n goes to afqmc_log_weight_scale. */
 afqmc_status afqmc_population_control(afqmc_ctx* ctx);
 
 /* Local energy E_L = <Psi_T|H|phi>/<Psi_T|phi> of every walker (Sec. II,
@@ -224,6 +226,16 @@ afqmc_status afqmc_selftest_wait_timeout(afqmc_ctx* ctx, int64_t limit_cycles);
  * the energy of the reference determinant <D_0|H|D_0>, evaluated in FP64 at
  * creation whatever the step precision. */
 afqmc_status afqmc_energy_shift(afqmc_ctx* ctx, double* e_shift);
+
+/* Log of the factor the weights have been divided by. Each comb (Sec. V)
+ * gives every walker the common weight S/n (S the total weight, n the
+ * walkers); the library divides it out, so every walker restarts at weight
+ * 1, and adds ln(S/n) here, so that a population far below E_T cannot
+ * overflow. The absolute weight of walker i is w_i * exp(*log_scale);
+ * estimators are ratios of weights and need no correction. Counts from
+ * creation or from the last afqmc_set_state (whose image carries absolute
+ * weights). Synchronises the context's stream. */
+afqmc_status afqmc_log_weight_scale(afqmc_ctx* ctx, double* log_scale);
 
 /* Force bias xbar of the last step, [n_walkers * n_chol * 2] (re, im). */
 afqmc_status afqmc_force_bias(afqmc_ctx* ctx, double* xbar);
@@ -382,7 +394,8 @@ typedef struct {
   double t_end;         /* host seconds: completion seen by the scheduler */
   double device_ms;     /* device time between the block's start and end */
   double e_mixed;       /* mixed energy of the latest measurement (NaN if none) */
-  double weight_sum;    /* sum of walker weights at that measurement */
+  double weight_sum;    /* sum of walker weights at that measurement (in
+                           units of the run's log weight scale) */
   int64_t step;         /* step count at the end of the block */
 } afqmc_block_result;
 

@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH):
         "afqmc_green": (C.c_int, [vp, C.c_int32, d, d]),
         "afqmc_force_bias": (C.c_int, [vp, d]),
         "afqmc_energy_shift": (C.c_int, [vp, d]),
+        "afqmc_log_weight_scale": (C.c_int, [vp, d]),
         "afqmc_selftest_wait_timeout": (C.c_int, [vp, C.c_int64]),
         "afqmc_energy_history": (C.c_int, [vp, d, C.c_int32, i32]),
         "afqmc_get_state": (C.c_int, [vp, vp, P(C.c_size_t)]),
@@ -315,6 +316,11 @@ class Afqmc:
     def afqmc_energy_shift(self) -> float:
         e = np.zeros(1)
         self._check(self._lib.afqmc_energy_shift(self._h, _dptr(e)))
+        return float(e[0])
+
+    def afqmc_log_weight_scale(self) -> float:
+        e = np.zeros(1)
+        self._check(self._lib.afqmc_log_weight_scale(self._h, _dptr(e)))
         return float(e[0])
 
     def afqmc_force_bias(self):

@@ -71,6 +71,8 @@ struct afqmc_ctx {
   void *Ltil_lo, *LT_lo, *Yx_up_lo, *Yx_dn_lo;
   double* PsiT64;
   double *weight, *scan, *wnew, *escalar, *lr;
+  double* wref;        // reference weight of the weight cap (1 after a comb)
+  double* log_scale;   // sum of ln(S/n) divided out of the weights at the combs
   double2 *logO, *logO2, *logO_new, *logdet, *logdet2, *lw, *eloc, *hist;
   // mean-field subtraction: lbar_g of the reference determinant [G], the
   // per-walker log of the scalar factor it puts on a propagated walker [W],
@@ -365,7 +367,7 @@ afqmc_status comb_T(afqmc_ctx* c) {
   const long pe = (long)c->N * 2 * c->M;
   LK(launch_gather<T>(c->st, W, pe, 2 * c->ldt, c->parent, (const T*)c->Phi, (T*)c->Phi2,
                       (const T*)c->Theta, (T*)c->Theta2, c->logO, c->logO2, c->wnew,
-                      c->weight));
+                      c->weight, c->wref, c->log_scale));
   const size_t es = sizeof(T);
   CK(cudaMemcpyAsync(c->Phi, c->Phi2, (size_t)W * pe * es, cudaMemcpyDeviceToDevice, c->st));
   CK(cudaMemcpyAsync(c->Theta, c->Theta2, (size_t)W * 2 * c->ldt * es,
@@ -502,7 +504,7 @@ afqmc_status step_T(afqmc_ctx* c) {
     LK(launch_weights(c->st, W, c->md ? c->logO_new : nullptr, c->md ? nullptr : c->logdet,
                       c->lw, c->lmf, local ? c->eloc : nullptr, dt,
                       local ? c->e_shift : c->e_shift + c->e_mf, (double)c->p.weight_cap,
-                      c->wnew, c->weight, c->logO, c->ctr));
+                      c->wref, c->weight, c->logO, c->ctr));
   }
   c->step += 1;
   const long n = c->step;
@@ -795,9 +797,10 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
 #undef TM
   // walkers start at the reference determinant, weight 1
   LK(launch_init_walkers<T>(st, W, M, N, (const T*)c->PsiT, (T*)c->Phi, c->weight));
-  {                                   // reference weight of the weight cap
+  {                                   // reference weight of the weight cap, log scale
     static const double one = 1.0;
-    CK(cudaMemcpyAsync(c->wnew, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->wref, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->log_scale, 0, sizeof(double), st));
   }
   afqmc_status s = overlap_T<T>(c, c->logO);
   if (s != AFQMC_OK) return s;
@@ -1245,6 +1248,8 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->scan, W * sizeof(double));
   add(&c->lr, 2 * W * sizeof(double));
   add(&c->wnew, sizeof(double));
+  add(&c->wref, sizeof(double));
+  add(&c->log_scale, sizeof(double));
   add(&c->escalar, 2 * sizeof(double));
   add(&c->logO, W * sizeof(double2));
   add(&c->logO2, W * sizeof(double2));
@@ -1634,6 +1639,14 @@ afqmc_status afqmc_energy_shift(afqmc_ctx* c, double* e_shift) {
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_log_weight_scale(afqmc_ctx* c, double* log_scale) {
+  GUARD(c);
+  if (!log_scale) return fail(c, AFQMC_E_INVALID, "log_scale is NULL");
+  CK(cudaMemcpyAsync(log_scale, c->log_scale, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_force_bias(afqmc_ctx* c, double* xbar) {
   GUARD(c);
   if (!xbar) return fail(c, AFQMC_E_INVALID, "xbar is NULL");
@@ -1741,7 +1754,9 @@ afqmc_status afqmc_set_state(afqmc_ctx* c, const void* buf, size_t bytes) {
     for (int w = 0; w < W; ++w)
       if (wt[w] > 0.0) { sum += wt[w]; ++live; }
     c->wref_host = live ? sum / live : 1.0;
-    CK(cudaMemcpyAsync(c->wnew, &c->wref_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->wref, &c->wref_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    // the image's weights are absolute: the log scale starts again from 0
+    CK(cudaMemsetAsync(c->log_scale, 0, sizeof(double), c->st));
   }
   c->step = h.step;
   const long long ctr_h[2] = {(long long)c->step, (long long)c->n_meas};

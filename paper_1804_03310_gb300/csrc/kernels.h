@@ -113,12 +113,14 @@ cudaError_t launch_comb(cudaStream_t st, int W, const double* weight, uint64_t s
                         int run_id, const long long* ctr, long step, int* parent,
                         double* scratch, double* wnew, int* status);
 
-// Walker copies after the comb.
+// Walker copies after the comb. When the comb succeeded (*wnew = S/n > 0)
+// every weight becomes 1, *wref 1, and ln(S/n) is added to *log_scale.
 template <typename T>
 cudaError_t launch_gather(cudaStream_t st, int W, long phi_elems, long theta_elems,
                           const int* parent, const T* Phi, T* Phi_out,
                           const T* Theta, T* Theta_out, const double2* logO,
-                          double2* logO_out, const double* wnew, double* weight);
+                          double2* logO_out, const double* wnew, double* weight,
+                          double* wref, double* log_scale);
 
 // Row copies out[j] = in[parent[j]] ([W][elems]).
 template <typename T>

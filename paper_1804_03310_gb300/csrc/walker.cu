@@ -919,7 +919,8 @@ __global__ void gather_kernel(long phi_elems, long theta_elems,
                               T* __restrict__ Theta_out, const double2* __restrict__ logO,
                               double2* __restrict__ logO_out,
                               const double* __restrict__ wnew,
-                              double* __restrict__ weight) {
+                              double* __restrict__ weight, double* __restrict__ wref,
+                              double* __restrict__ log_scale) {
   const int j = blockIdx.x;
   const int p = parent[j];
   for (long e = threadIdx.x; e < phi_elems; e += blockDim.x)
@@ -928,8 +929,16 @@ __global__ void gather_kernel(long phi_elems, long theta_elems,
     Theta_out[(long)j * theta_elems + e] = Theta[(long)p * theta_elems + e];
   if (threadIdx.x == 0) {
     logO_out[j] = logO[p];
-    double wn = *wnew;
-    if (wn > 0.0) weight[j] = wn;
+    // the common weight S/n is divided out: every walker restarts at 1 and
+    // ln(S/n) goes to the log scale (block 0 alone writes the scalars)
+    const double wn = *wnew;
+    if (wn > 0.0) {
+      weight[j] = 1.0;
+      if (j == 0) {
+        *wref = 1.0;
+        *log_scale += log(wn);
+      }
+    }
   }
 }
 
@@ -1226,9 +1235,11 @@ template <typename T>
 cudaError_t launch_gather(cudaStream_t st, int W, long phi_elems, long theta_elems,
                           const int* parent, const T* Phi, T* Phi_out,
                           const T* Theta, T* Theta_out, const double2* logO,
-                          double2* logO_out, const double* wnew, double* weight) {
+                          double2* logO_out, const double* wnew, double* weight,
+                          double* wref, double* log_scale) {
   gather_kernel<T><<<W, 256, 0, st>>>(phi_elems, theta_elems, parent, Phi, Phi_out,
-                                      Theta, Theta_out, logO, logO_out, wnew, weight);
+                                      Theta, Theta_out, logO, logO_out, wnew, weight,
+                                      wref, log_scale);
   return cudaGetLastError();
 }
 
@@ -1341,7 +1352,8 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
                                                double2*);                               \
   template cudaError_t launch_gather<T>(cudaStream_t, int, long, long, const int*,      \
                                         const T*, T*, const T*, T*, const double2*,     \
-                                        double2*, const double*, double*);              \
+                                        double2*, const double*, double*, double*,      \
+                                        double*);                                       \
   template cudaError_t launch_convert<T>(cudaStream_t, long, const double*, T*);        \
   template cudaError_t launch_init_walkers<T>(cudaStream_t, int, int, int, const T*,    \
                                               T*, double*);

@@ -7,7 +7,9 @@ Every quantity is held to the bar per walker:
 * overlaps: |ln O_gpu - ln O_orc| (the phase wrapped to (-pi, pi]), which is
   the relative error of the complex overlap O itself;
 * orbitals and Green's functions: max |a - b| / max |b| per walker;
-* local energies: |E_gpu - E_orc| / max(1 Ha, |E_orc|) per walker.
+* local energies: |E_gpu - E_orc| / max(1 Ha, |E_orc|) per walker;
+* when the whole population is followed, the log of the weight scale the
+  combs divided out.
 """
 from __future__ import annotations
 
@@ -111,6 +113,10 @@ def side_by_side(gpu, orc, n_steps, rtol, walkers=None, energy_at=(), label=""):
         gpu.afqmc_propagate(1)
         orc.step()
         r = compare_state(gpu, orc, rtol=rtol, walkers=walkers, label=f"{label} step {s}")
+        if walkers is None:   # the whole population: the combs' log scale too
+            d = abs(gpu.afqmc_log_weight_scale() - orc.log_scale)
+            assert d <= rtol * max(1.0, abs(orc.log_scale)), f"{label} step {s} log scale {d:.3e}"
+            r["log_scale"] = d
         for k, v in r.items():
             worst[k] = max(worst.get(k, 0.0), v)
         if s in energy_at:

@@ -9,6 +9,8 @@ sampled walkers for 20 steps with the comb moved past step 20 (the oracle
 can follow a subset of walkers only until a comb mixes the population; the
 comb keeps its own bitwise test below).
 """
+import math
+
 import numpy as np
 import pytest
 from scipy.linalg import expm
@@ -202,7 +204,9 @@ def test_comb_matches_oracle_on_given_weights():
                                - Pu[:, 0, 0][None, :]), axis=1)
         parent, wn = O.comb(w, comb_uniform(s.seed, s.run_id, 0))
         assert np.array_equal(got, parent)
-        assert np.all(out["weight"] == wn)
+        # every walker restarts at weight 1; S/n goes to the log scale
+        assert np.all(out["weight"] == 1.0)
+        assert abs(gpu.afqmc_log_weight_scale() - math.log(wn)) <= 1e-15
         gpu.close()
 
 
