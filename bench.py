@@ -744,8 +744,13 @@ def weight_forms_leg(s, precision, n_steps=200):
                 with Afqmc.from_system(p, precision=prec) as ctx:
                     ctx.afqmc_propagate(n_steps)
                     e[prec] = ctx.afqmc_energy_history()[:, 1]
+                    w, _ = ctx.afqmc_weights()
+                    if prec == "fp64":   # how far the comb-off population has degenerated
+                        r["end_killed"] = int(np.count_nonzero(w <= 0))
+                        r["end_top_weight_share"] = round(float(w.max() / w.sum()), 4)
             d = (e[precision] - e["fp64"]) * 1e3
             r["paired_max_abs_mHa"] = round(float(np.max(np.abs(d))), 6)
+            r["paired_median_abs_mHa"] = round(float(np.median(np.abs(d))), 6)
             r["e_fp64_last"] = round(float(e["fp64"][-1]), 6)
         out[key] = r
     alive = {}

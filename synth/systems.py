@@ -288,10 +288,13 @@ def config_c4(**kw) -> System:
 def serving_run(rng: np.random.Generator, run_id: int,
                 m_range=(20, 200), w_range=(128, 2048)) -> System:
     """One request of the serving mix: sizes drawn as the serving workload states.
-    Energy once per 50-step block; the comb every 10 steps, since with
-    n_chol ~ 5M fields of this scale the phaseless cut removes a few percent
-    of the walkers per step at the larger M and a 50-step comb interval can
-    lose the whole population."""
+    Energy once per 50-step block; the comb every 10 steps. The entries of
+    the dense Cholesky vectors have scale 0.5 / M, so that the exchange
+    potential sum_g L_g P L_g (n_chol ~ 5M vectors, M/4 electrons per spin)
+    stays near 0.3 Ha on the diagonal whatever M: with a scale falling only
+    as M^-1/2 it grows linearly with M, the one-body eigenvector trial
+    drifts out of reach (ln |<Psi_T|phi>| near -40 after 40 steps at M = 98)
+    and the phaseless cut empties the population within 50 steps."""
     M = int(rng.integers(m_range[0], m_range[1] + 1))
     n = int(rng.integers(math.ceil(M / 5), M // 3 + 1))
     n_chol = int(rng.integers(4 * M, 6 * M + 1))
@@ -299,7 +302,7 @@ def serving_run(rng: np.random.Generator, run_id: int,
     ham_seed = int(rng.integers(0, 2**31 - 1))
     return make_system(f"serve_{run_id}", M=M, n_up=n, n_dn=n, n_chol=n_chol,
                        ham_seed=ham_seed, l_kind="dense",
-                       l_sigma=0.05 * math.sqrt(10.0 / M), trial="eig",
+                       l_sigma=0.5 / M, trial="eig",
                        dtau=0.005, n_walkers=W, n_steps=500, seed=ham_seed,
                        ortho_every=2, measure_every=50, pc_every=10,
                        run_id=run_id)
