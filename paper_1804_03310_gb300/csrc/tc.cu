@@ -388,28 +388,35 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   __syncthreads();
   if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
-
 // ------------------------------------------------------------------ Taylor
-// One CTA of 128 threads per (walker, 64-column chunk) work item, looping
-// over items. Thread r owns row r of the real 2M-row form (r < 64: real part
-// of orbital row r; r >= 64: imaginary part of row r - 64) and the matching
-// TMEM lane; it keeps the running sum of the series for its row in
-// registers.
+// One CTA of 256 threads per (walker, 64-column chunk) work item, looping
+// over items. The chunk's columns form two independent halves of 32 (the
+// series acts on every column alone), each run by one warpgroup with its
+// own MMA chain, accumulator and barrier, so that one half's products run
+// on the tensor core while the other half's epilogue runs on the CUDA
+// cores. Thread r of a warpgroup owns row r of the real 2M-row form (r < 64:
+// real part of orbital row r; r >= 64: imaginary part of row r - 64) and the
+// matching TMEM lane; it keeps the running sum of the series for its row and
+// its half's 32 columns in registers.
 //
 // The operator, in its real form A = [[Vr, -Vi], [Vi, Vr]] (2M x 2M padded to
-// 128 x 128), is the MMA's A operand in tensor memory: lane r holds row r,
-// one 32-bit column per K index (TF32X3: hi in columns 128..255, lo in
-// 256..383; the accumulator in columns 0..63). Each thread writes its own row
-// with tcgen05.st, so the operand needs no shared-memory swizzle and the
-// MMAs read only the current term t (the B operand) from shared memory.
+// 128 x 128), is the MMA's A operand in tensor memory, shared by both halves:
+// lane r holds row r, one 32-bit column per K index (TF32X3: hi in columns
+// 128..255, lo in 256..383; half h accumulates into columns 64h .. 64h + 63,
+// two chains of 32).
+// Each thread writes its own row (warpgroup h the K columns 64h..64h+63) with
+// tcgen05.st, so the operand needs no shared-memory swizzle and the MMAs read
+// only the current term t of their half (the B operand) from shared memory.
 //
 // With a half-step image (FUSE_B), the symmetric Trotter factors are applied
 // on the tensor cores too: t0 = Phi + (B_half - I) Phi before the series and
 // out = s + (B_half - I) s after it, the identity part added exactly in FP32
 // and (B_half - I) in its real 2M-row form [[dB, 0], [0, dB]] bulk-copied
 // once per CTA into shared memory from a pre-swizzled (and pre-split) image.
+constexpr int TY_THREADS = 256;
 constexpr int TY_A_BYTES = 128 * 128 * 4;     // half-step image, 4 K-blocks
-constexpr int TY_B_BYTES = 64 * 128 * 4;      // current term t, 64 columns
+constexpr int TY_H_BYTES = 32 * 128 * 4;      // one half's term t, 32 columns
+constexpr int TY_B_BYTES = 2 * TY_H_BYTES;    // both halves
 constexpr int TY_V_BYTES = 2 * 64 * 64 * 4;   // raw V of the next walker (TF32X3)
 template <bool SPLIT3>
 constexpr int taylor_smem() {
@@ -437,53 +444,85 @@ __global__ void bhalf_image_kernel(int M, const float* __restrict__ dB, float* _
   }
 }
 
+// One term column into a half's B operand (32 rows of the K-major SW128
+// tile; K index = the thread's row r), hi and (TF32X3) lo parts.
 template <bool SPLIT3>
-__device__ __forceinline__ void put_operand(unsigned char* hi, unsigned char* lo, uint32_t off,
-                                            float x) {
+__device__ __forceinline__ void put_term(uint32_t hi, uint32_t lo, int j, int r, float x) {
+  const uint32_t off = sw128_offset(j, r, 32);
   if (SPLIT3) {
     const float h = tf32_hi(x);
-    *(float*)(hi + off) = h;
-    *(float*)(lo + off) = tf32_lo(x, h);
+    st_shared_f32(hi + off, h);
+    st_shared_f32(lo + off, tf32_lo(x, h));
   } else {
-    *(float*)(hi + off) = x;
+    st_shared_f32(hi + off, x);
   }
 }
 
-// D (+)= A B with both operands in shared memory (the half-step image).
+// The products of one half run as two independent accumulation chains,
+// even and odd K steps into accumulators tD and tD + 32 (summed by the
+// epilogue): consecutive MMAs then never wait for each other's accumulator.
+//
+// D (+)= A B for one half (N = 32) with both operands in shared memory (A =
+// the half-step image, 128 rows per K-block; B = the half's term, 32 rows).
 template <bool SPLIT3>
-__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t Ahi, uint32_t Alo,
-                                               uint32_t Bhi, uint32_t Blo, uint32_t id) {
+__device__ __forceinline__ void issue_half_step(uint32_t tD0, uint32_t Ahi, uint32_t Alo,
+                                                uint32_t Bhi, uint32_t Blo, uint32_t id) {
+  const uint64_t a0 = desc_sw128(Ahi), b0 = desc_sw128(Bhi);
+  const uint64_t al0 = desc_sw128(Alo), bl0 = desc_sw128(Blo);
 #pragma unroll
   for (int ks = 0; ks < 16; ++ks) {
-    const int kb = ks >> 2, koff = (ks & 3) * 32;
-    const uint64_t ad = desc_sw128(Ahi + kb * 16384 + koff);
-    const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
-    mma_tf32(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
+    const uint32_t kb = ks >> 2, koff = (ks & 3) * 32;
+    const uint32_t tD = tD0 + 32u * (uint32_t)(ks & 1);
+    const uint64_t ad = desc_add(a0, kb * 16384 + koff);
+    const uint64_t bd = desc_add(b0, kb * 4096 + koff);
+    mma_tf32(tD, ad, bd, id, ks > 1 ? 1u : 0u);
     if (SPLIT3) {
-      mma_tf32(tmem, ad, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
-      mma_tf32(tmem, desc_sw128(Alo + kb * 16384 + koff), bd, id, 1u);
+      mma_tf32(tD, ad, desc_add(bl0, kb * 4096 + koff), id, 1u);
+      mma_tf32(tD, desc_add(al0, kb * 16384 + koff), bd, id, 1u);
     }
   }
 }
 
-// D = A B with A in tensor memory (the operator) and B in shared memory.
+// D = A B for one half with A in tensor memory (the operator) and B in
+// shared memory.
 template <bool SPLIT3>
-__device__ __forceinline__ void issue_products_ts(uint32_t tD, uint32_t tAhi, uint32_t tAlo,
-                                                  uint32_t Bhi, uint32_t Blo, uint32_t id) {
+__device__ __forceinline__ void issue_term(uint32_t tD0, uint32_t tAhi, uint32_t tAlo,
+                                           uint32_t Bhi, uint32_t Blo, uint32_t id) {
+  const uint64_t b0 = desc_sw128(Bhi), bl0 = desc_sw128(Blo);
 #pragma unroll
   for (int ks = 0; ks < 16; ++ks) {
-    const int kb = ks >> 2, koff = (ks & 3) * 32;
-    const uint64_t bd = desc_sw128(Bhi + kb * 8192 + koff);
-    mma_tf32_ts(tD, tAhi + 8 * ks, bd, id, ks > 0 ? 1u : 0u);
+    const uint32_t kb = ks >> 2, koff = (ks & 3) * 32;
+    const uint32_t tD = tD0 + 32u * (uint32_t)(ks & 1);
+    const uint64_t bd = desc_add(b0, kb * 4096 + koff);
+    mma_tf32_ts(tD, tAhi + 8 * ks, bd, id, ks > 1 ? 1u : 0u);
     if (SPLIT3) {
-      mma_tf32_ts(tD, tAhi + 8 * ks, desc_sw128(Blo + kb * 8192 + koff), id, 1u);
+      mma_tf32_ts(tD, tAhi + 8 * ks, desc_add(bl0, kb * 4096 + koff), id, 1u);
       mma_tf32_ts(tD, tAlo + 8 * ks, bd, id, 1u);
     }
   }
 }
 
+// The sum of a half's two accumulation chains (columns c .. c + 31 and
+// c + 32 .. c + 63 of this thread's lane), 8 columns of each at a time.
+__device__ __forceinline__ void tmem_ld_sum2(uint32_t taddr, float* v) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    float a[8], b[8];
+    tmem_ld8_nowait(taddr + 8u * (uint32_t)g, a);
+    tmem_ld8_nowait(taddr + 32u + 8u * (uint32_t)g, b);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[8 * g + i] = a[i] + b[i];
+  }
+}
+
+// Barrier of one warpgroup (ids 1 and 2; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int h) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + h) : "memory");
+}
+
 template <bool SPLIT3>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TY_THREADS, 1)
 tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
                  const float* Pin, float* Pout,
                  const float* __restrict__ dB_img, int* status) {
@@ -492,12 +531,11 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   // image hi and lo are adjacent so one bulk copy fills both
   unsigned char* Ihi = base;
   unsigned char* Ilo = base + TY_A_BYTES;
-  unsigned char* Bhi = base + TY_A_BYTES * (SPLIT3 ? 2 : 1);
-  unsigned char* Blo = Bhi + TY_B_BYTES;
-  uint64_t* bar = (uint64_t*)(base + (TY_A_BYTES + TY_B_BYTES) * (SPLIT3 ? 2 : 1));
-  uint64_t* lbar = bar + 1;
-  uint64_t* vbar = bar + 2;
-  uint32_t* tslot = (uint32_t*)(bar + 3);
+  unsigned char* Bbase = base + TY_A_BYTES * (SPLIT3 ? 2 : 1);   // hi halves, then lo halves
+  uint64_t* bar = (uint64_t*)(Bbase + TY_B_BYTES * (SPLIT3 ? 2 : 1));   // [2]: one per half
+  uint64_t* lbar = bar + 2;
+  uint64_t* vbar = bar + 3;
+  uint32_t* tslot = (uint32_t*)(bar + 4);
   // TF32X3 with M even: the next walker's V (2 M^2 floats, contiguous) is
   // bulk-copied into the spare shared memory while this walker's series runs
   float* vst = (float*)(base + (TY_A_BYTES + TY_B_BYTES) * 2 + 128);
@@ -506,6 +544,9 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
+  const int h = tid >> 7;                  // half (warpgroup): columns 32h .. 32h + 31
+  const int r = tid & 127;                 // embedded row / K index owned
+  const int rc = r >> 6, rr = r & 63;      // component (0 re, 1 im), orbital row
   const int nchunk = (N + 63) / 64;
   const int items = W * nchunk;
   const bool fuse_b = dB_img != nullptr;
@@ -513,6 +554,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   if (tid == 0) {
     s_fail = 0;
     mbar_init(smem_u32(bar), 1);
+    mbar_init(smem_u32(bar + 1), 1);
     mbar_init(smem_u32(lbar), 1);
     mbar_init(smem_u32(vbar), 1);
     mbar_fence_init();
@@ -523,29 +565,38 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   fence_after_sync();
   const uint32_t tmem = *tslot;
   const uint32_t tAhi = tmem + TY_TMEM_AHI, tAlo = tmem + TY_TMEM_ALO;
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  const uint32_t id = idesc_tf32(128, 64);
-  uint32_t phase = 0;
-  const int r = tid;                       // embedded row / K index owned
-  const int rc = r >> 6, rr = r & 63;      // component (0 re, 1 im), orbital row
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t tD = tmem + 64u * (uint32_t)h;   // this half's two accumulators
+  const uint32_t id = idesc_tf32(128, 32);
   const uint32_t sIhi = smem_u32(Ihi), sIlo = smem_u32(Ilo);
-  const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+  const uint32_t sBhi = smem_u32(Bbase) + (uint32_t)(h * TY_H_BYTES);
+  const uint32_t sBlo = smem_u32(Bbase) + (uint32_t)(TY_B_BYTES + h * TY_H_BYTES);
+  const uint32_t mybar = smem_u32(bar + h);
+  const bool leader = r == 0;              // the half's MMA issuer
   const int MM = M * M;
+  uint32_t phase = 0;
+  // a wait of this thread that gave up: the thread issues no further MMA
+  // (as its half's leader) and waits no more; the leader waits once more,
+  // bounded, for that commit before the CTA frees its tensor memory
+  bool failed = false;
+  uint32_t fail_parity = 0;
 
-  // wait for the MMAs just issued; flags a timeout
   auto wait_mma = [&]() {
-    const bool ok = mbar_wait(smem_u32(bar), phase);
-    phase ^= 1u;
-    if (!ok) {
+    if (!failed && !mbar_wait(mybar, phase)) {
       flag_timeout(status);
       s_fail = 1;
+      failed = true;
+      fail_parity = phase;
     }
+    phase ^= 1u;
     fence_after_sync();
   };
-  auto sync_for_mma = [&]() {
+  // the half's term writes are visible to the tensor core before its leader
+  // issues, and the previous TMEM reads of the accumulator are complete
+  auto sync_half = [&]() {
     fence_proxy_async();
     fence_before_sync();
-    __syncthreads();
+    group_sync(h);
     fence_after_sync();
   };
   bool img_pending = false;
@@ -572,17 +623,20 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int w = item / nchunk;
-    const int j0 = (item - w * nchunk) * 64;
-    const int nc = min(64, N - j0);
+    const int j0 = (item - w * nchunk) * 64 + 32 * h;   // this half's first column
+    const int nc = max(0, min(32, N - j0));             // and its column count
+    const bool active = nc > 0;                          // uniform over the half
     const float* Vw = V + (long)w * 2 * MM;
-    // ---- t0 = the chunk's columns; this thread's row of it seeds the sum
-    float acc[64];
-    const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
+    // ---- t0 = the half's columns; this thread's row of it seeds the sum
+    float acc[32];
+    if (active) {
+      const float* Pw = Pin + ((long)w * N + j0) * 2 * M;
 #pragma unroll
-    for (int j = 0; j < 64; ++j)
-      acc[j] = (j < nc && rr < M) ? Pw[((long)j * 2 + rc) * M + rr] : 0.f;
+      for (int j = 0; j < 32; ++j)
+        acc[j] = (j < nc && rr < M) ? Pw[((long)j * 2 + rc) * M + rr] : 0.f;
 #pragma unroll
-    for (int j = 0; j < 64; ++j) put_operand<SPLIT3>(Bhi, Blo, sw128_offset(j, r, 64), acc[j]);
+      for (int j = 0; j < 32; ++j) put_term<SPLIT3>(sBhi, sBlo, j, r, acc[j]);
+    }
     if (fuse_b) {                          // t0 = Phi + dB Phi
       if (img_pending) {
         if (!mbar_wait(smem_u32(lbar), 0)) {
@@ -591,26 +645,26 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
         }
         img_pending = false;
       }
-      sync_for_mma();
-      if (tid == 0) {
-        issue_products<SPLIT3>(tmem, sIhi, sIlo, sBhi, sBlo, id);
-        mma_commit(smem_u32(bar));
-      }
-      wait_mma();
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 32) {
+      if (active) {
+        sync_half();
+        if (leader && !failed) {
+          issue_half_step<SPLIT3>(tD, sIhi, sIlo, sBhi, sBlo, id);
+          mma_commit(mybar);
+        }
+        wait_mma();
         float v[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+        tmem_ld_sum2(tD + lane_base, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          acc[c0 + j] += v[j];
-          put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64), acc[c0 + j]);
+          acc[j] += v[j];
+          put_term<SPLIT3>(sBhi, sBlo, j, r, acc[j]);
         }
       }
     }
     // ---- the operator into tensor memory: row r of [[Vr, -Vi], [Vi, Vr]],
     // columns 0..63 from plane rc of V, columns 64..127 from the other plane
-    // (negated for the real rows), zero beyond M in each half
+    // (negated for the real rows), zero beyond M in each half; warpgroup h
+    // writes the K columns 64h .. 64h + 63 of its rows
     const float* vsrc = Vw;
     if (vpre) {
       if (!mbar_wait(smem_u32(vbar), vphase)) {
@@ -624,7 +678,7 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     {
       const bool vec = (M & 3) == 0;       // rows 16-byte aligned
 #pragma unroll 1
-      for (int c0 = 0; c0 < 128; c0 += 16) {
+      for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
         const int half = c0 >> 6, k0 = c0 & 63;
         const int plane = half == 0 ? rc : 1 - rc;
         const float sgn = (rc == 0 && half == 1) ? -1.f : 1.f;
@@ -641,14 +695,14 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
           for (int u = 0; u < 16; ++u) x[u] = (rr < M && k0 + u < M) ? src[k0 + u] : 0.f;
         }
         if (SPLIT3) {
-          float h[16], l[16];
+          float hv[16], lv[16];
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
-            h[u] = tf32_hi(sgn * x[u]);
-            l[u] = tf32_lo(sgn * x[u], h[u]);
+            hv[u] = tf32_hi(sgn * x[u]);
+            lv[u] = tf32_lo(sgn * x[u], hv[u]);
           }
-          tmem_st16(tAhi + lane_base + (uint32_t)c0, h);
-          tmem_st16(tAlo + lane_base + (uint32_t)c0, l);
+          tmem_st16(tAhi + lane_base + (uint32_t)c0, hv);
+          tmem_st16(tAlo + lane_base + (uint32_t)c0, lv);
         } else {
 #pragma unroll
           for (int u = 0; u < 16; ++u) x[u] *= sgn;
@@ -657,53 +711,52 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
       }
       tmem_wait_st();
     }
+    // the whole operator and both halves' terms are in place before either
+    // half's series starts; every thread has read vst
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
     if (vpre) {
-      __syncthreads();                    // every thread has read vst
       const int next = item + (int)gridDim.x;
       if (next < items && !s_fail) load_v(next);
     }
-    for (int term = 1; term <= order; ++term) {
-      sync_for_mma();
-      if (tid == 0) {
-        issue_products_ts<SPLIT3>(tmem, tAhi, tAlo, sBhi, sBlo, id);
-        mma_commit(smem_u32(bar));
-      }
-      wait_mma();
-      const float inv = 1.0f / (float)term;
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 32) {
+    if (active) {
+      for (int term = 1; term <= order; ++term) {
+        if (term > 1) sync_half();
+        if (leader && !failed) {
+          issue_term<SPLIT3>(tD, tAhi, tAlo, sBhi, sBlo, id);
+          mma_commit(mybar);
+        }
+        wait_mma();
+        const float inv = 1.0f / (float)term;
         float v[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+        tmem_ld_sum2(tD + lane_base, v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float x = v[j] * inv;
-          acc[c0 + j] += x;
-          if (term < order || fuse_b)
-            put_operand<SPLIT3>(Bhi, Blo, sw128_offset(c0 + j, r, 64),
-                                term < order ? x : acc[c0 + j]);
+          acc[j] += x;
+          if (term < order || fuse_b) put_term<SPLIT3>(sBhi, sBlo, j, r, term < order ? x : acc[j]);
         }
       }
-    }
-    if (fuse_b) {                          // out = s + dB s
-      sync_for_mma();
-      if (tid == 0) {
-        issue_products<SPLIT3>(tmem, sIhi, sIlo, sBhi, sBlo, id);
-        mma_commit(smem_u32(bar));
-      }
-      wait_mma();
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 32) {
+      if (fuse_b) {                        // out = s + dB s
+        sync_half();
+        if (leader && !failed) {
+          issue_half_step<SPLIT3>(tD, sIhi, sIlo, sBhi, sBlo, id);
+          mma_commit(mybar);
+        }
+        wait_mma();
         float v[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+        tmem_ld_sum2(tD + lane_base, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[c0 + j] += v[j];
+        for (int j = 0; j < 32; ++j) acc[j] += v[j];
       }
-    }
-    float* Ow = Pout + ((long)w * N + j0) * 2 * M;
-    if (rr < M) {
+      if (rr < M) {
+        float* Ow = Pout + ((long)w * N + j0) * 2 * M;
 #pragma unroll
-      for (int j = 0; j < 64; ++j)
-        if (j < nc) Ow[((long)j * 2 + rc) * M + rr] = acc[j];
+        for (int j = 0; j < 32; ++j)
+          if (j < nc) Ow[((long)j * 2 + rc) * M + rr] = acc[j];
+      }
     }
     fence_before_sync();
     __syncthreads();
@@ -713,6 +766,8 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
   if (v_inflight && !mbar_wait(smem_u32(vbar), vphase))   // no copy may outlive the CTA
     flag_timeout(status);
   if (img_pending && !mbar_wait(smem_u32(lbar), 0)) flag_timeout(status);
+  if (leader && failed && !mbar_wait(mybar, fail_parity))  // nor an MMA the allocation
+    flag_timeout(status);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kCols);
@@ -1459,14 +1514,14 @@ cudaError_t tc_taylor(TcCtx* t, cudaStream_t st, int W, int M, int N, int order,
     const cudaError_t attr = set_smem(tc_taylor_kernel<true>, taylor_smem<true>());
     if (attr != cudaSuccess) return attr;
     int grid = items < t->num_sms ? items : t->num_sms;
-    tc_taylor_kernel<true><<<grid, 128, taylor_smem<true>(), st>>>(W, M, N, order, V, Pin,
+    tc_taylor_kernel<true><<<grid, TY_THREADS, taylor_smem<true>(), st>>>(W, M, N, order, V, Pin,
                                                                   Pout, (const float*)bhalf_img,
                                                                   status);
   } else {
     const cudaError_t attr = set_smem(tc_taylor_kernel<false>, taylor_smem<false>());
     if (attr != cudaSuccess) return attr;
-    int grid = items < 2 * t->num_sms ? items : 2 * t->num_sms;
-    tc_taylor_kernel<false><<<grid, 128, taylor_smem<false>(), st>>>(W, M, N, order, V, Pin,
+    int grid = items < t->num_sms ? items : t->num_sms;   // 256 threads of 152 registers
+    tc_taylor_kernel<false><<<grid, TY_THREADS, taylor_smem<false>(), st>>>(W, M, N, order, V, Pin,
                                                                     Pout, (const float*)bhalf_img,
                                                                     status);
   }

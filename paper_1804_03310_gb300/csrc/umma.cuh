@@ -45,6 +45,15 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The descriptor of saddr + off from that of saddr, for off a multiple of 16:
+// the start-address field is the only one that moves, and shared-memory
+// addresses stay below 256 KB, so the 14-bit field cannot carry. One add,
+// independent of the other descriptors of a loop, instead of the mask and
+// shifts of desc_sw128 on the MMA issuer's critical path.
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t off) {
+  return d + (uint64_t)(off >> 4);
+}
+
 // Instruction descriptor for kind::tf32, FP32 accumulate, both operands
 // K-major: D format (bits 4-5) = F32, A/B format (bits 7-9, 10-12) = TF32,
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28; bit 13 negates A.
