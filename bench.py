@@ -82,14 +82,15 @@ def load_peaks():
 def roofline_for(kernel_stats, precision, peaks, src, s, workload_name, taylor_fused=None):
     """Dominant kernel of the timed region against its bound. The propagate
     group runs on the tensor cores unless the propagation path is the
-    CUDA-core series (taylor_fused = 0; when the path is not given, the
-    CUDA-core series is assumed above M = 64), where it is rated against the
-    FP32 CUDA-core peak. BF16X3 propagates with BF16 products (BF16 peak);
+    CUDA-core series (taylor_fused = 0, or 4 for block-diagonal Cholesky
+    vectors; when the path is not given, the CUDA-core series is assumed
+    above M = 64), where it is rated against the FP32 CUDA-core peak. BF16X3 propagates with BF16 products (BF16 peak);
     its other contractions are TF32X3 (TF32 peak)."""
     best = max(kernel_stats.items(), key=lambda kv: kv[1]["total_ms"])
     name, st = best
     avg_s = st["total_ms"] / max(1, st["launches"]) / 1e3
-    prop_tc = (taylor_fused != 0) if taylor_fused is not None else s.M <= 64
+    # 0: the CUDA-core series; 4: the block-diagonal series on the CUDA cores
+    prop_tc = (taylor_fused not in (0, 4)) if taylor_fused is not None else s.M <= 64
     tensor_groups = ("force_bias", "one_body", "energy") + (("propagate",) if prop_tc else ())
     if st["is_bytes"]:
         bound, unit = "hbm", "GB/s"
@@ -513,13 +514,13 @@ def serving_leg(precision, n_runs=20, rate=20.0, seed=5, blocks=10, steps=50, mf
             "failures": failures[:4]}
 
 
-def _blocks(s, precision, n_blocks):
+def _blocks(s, precision, n_blocks, **kw):
     """Mean device ms per 20-step block after one warm-up block, and the
     per-kernel-group totals over the timed blocks."""
     import torch
     from paper_1804_03310_gb300 import Afqmc, KERNEL_IDS
     stream = torch.cuda.Stream()
-    ctx = Afqmc.from_system(s, precision=precision, stream=stream.cuda_stream)
+    ctx = Afqmc.from_system(s, precision=precision, stream=stream.cuda_stream, **kw)
     ctx.afqmc_propagate(BLOCK)
     stream.synchronize()
     ctx.afqmc_set_kernel_timing(True)
@@ -703,9 +704,10 @@ def precisions_leg(s, n_blocks=3):
 def shapes_leg(precision):
     """The other workload shapes of the scope, each in its stated arithmetic
     and in FP64 on the GPU (same walkers and seed): the TM-atom shape
-    (M = 150, BF16 hi + lo propagation, operator streamed by TMA) and the
-    multi-determinant shape (200 determinants, batched SMW ratios) in the
-    bench's precision."""
+    (M = 150, BF16 hi + lo arithmetic; its shell-structured Cholesky vectors
+    take the block-diagonal path, timed beside the dense path with the
+    operator streamed by TMA) and the multi-determinant shape (200
+    determinants, batched SMW ratios) in the bench's precision."""
     from synth import CONFIGS
     out = {}
     for name, prec in (("c3", "bf16x3"), ("c4", precision)):
@@ -718,6 +720,11 @@ def shapes_leg(precision):
                      "value": round(v, 1), "unit": METRIC, "ms_per_block": round(ms, 3),
                      "fp64_value": round(v64, 1), "speedup": round(v / v64, 2),
                      "kernels_ms_2_blocks": kms}
+        if name == "c3":   # the dense path on the same inputs
+            msd, kmsd = _blocks(s, prec, 2, block_sparse=2)
+            out[name]["dense"] = {"value": round(s.n_walkers * BLOCK / (msd / 1e3), 1),
+                                  "ms_per_block": round(msd, 3), "kernels_ms_2_blocks": kmsd,
+                                  "block_sparse_speedup": round(msd / ms, 2)}
     return out
 
 

@@ -149,6 +149,19 @@ typedef struct {
                             operators (the propagator's exact form is
                             unchanged; the phaseless cut sees smaller
                             phases); 0: none */
+  int32_t block_sparse;  /* Cholesky vectors that are block-diagonal in a
+                            common partition of the basis (every L_g zero
+                            between different blocks, as for basis shells of
+                            an atom): the one-body operator V = sum s_g L_g
+                            is then block-diagonal too, is built on the
+                            blocks' entries only and its Taylor series is
+                            applied block by block, between the two dense
+                            half steps (same arithmetic, far fewer
+                            operations). 0 (default): use it when the
+                            partition has at least two blocks, none larger
+                            than 32, and at most M^2/4 entries; 1: require
+                            it (AFQMC_E_INVALID otherwise); 2: dense */
+  int32_t reserved[3];   /* must be zero */
 } afqmc_params;
 
 /* Fill *p with defaults: taylor_order 6, fb_cap 1, e_shift NaN, FP64,
@@ -297,7 +310,10 @@ typedef struct {
                              the tensor cores, half steps as separate
                              contractions (1 and 2 need M <= 64); 3 = one
                              fused tensor-core kernel with the operator
-                             streamed from memory by TMA (needs M > 64) */
+                             streamed from memory by TMA (needs M > 64);
+                             4 = the block-diagonal series of
+                             params.block_sparse (the only path, and only
+                             there, when the context uses it) */
   int32_t reserved[2];    /* zero */
 } afqmc_tuning;
 afqmc_status afqmc_get_tuning(afqmc_ctx* ctx, afqmc_tuning* out);

@@ -36,7 +36,8 @@ class afqmc_params(C.Structure):
                 ("graphs", C.c_int32), ("autotune", C.c_int32),
                 ("weight_cap", C.c_int32), ("cs_group", C.c_int32),
                 ("cs_size", C.c_int32), ("weight_mode", C.c_int32),
-                ("mf_subtract", C.c_int32)]
+                ("mf_subtract", C.c_int32), ("block_sparse", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class afqmc_tuning(C.Structure):
@@ -172,7 +173,8 @@ class Inputs:
                  n_walkers, seed=0, run_id=0, precision="fp64", ortho_every=2,
                  measure_every=20, pc_every=20, taylor_order=6, fb_cap=1.0,
                  e_shift=None, fp64_islands=False, graphs=True, autotune=True,
-                 weight_cap=0, cs_group=0, cs_size=0, weight_mode=0, mf_subtract=0):
+                 weight_cap=0, cs_group=0, cs_size=0, weight_mode=0, mf_subtract=0,
+                 block_sparse=0):
         self.h1 = np.ascontiguousarray(h1, dtype=np.float64)
         self.L = np.ascontiguousarray(L, dtype=np.float64)
         self.C_up = np.ascontiguousarray(C_up, dtype=np.float64)
@@ -205,6 +207,7 @@ class Inputs:
         p.cs_size = int(cs_size)
         p.weight_mode = int(weight_mode)
         p.mf_subtract = int(mf_subtract)
+        p.block_sparse = int(block_sparse)
         self.params = p
 
     @classmethod

@@ -80,6 +80,14 @@ struct afqmc_ctx {
   double* lbar;
   double2* lmf;
   double e_mf;
+  // block-diagonal Cholesky vectors: V is built and exponentiated on the
+  // blocks' entries only (nnz of them, rows padded to nnzp); blk holds per
+  // basis index the int4 {offset of its row of V, block size, start of the
+  // block's member list, 0}, then the member lists (M ints)
+  bool sparse;
+  long nnz, nnzp;
+  void* blk;
+  std::vector<int> blk_gidx;   // host, during setup: i*M+j of each packed entry
   int *parent, *status;
   double wref_host;   // staging of a restored reference weight
   long long* ctr;   // device step counters: [0] completed steps, [1] measurements
@@ -433,7 +441,10 @@ afqmc_status propagate_T(afqmc_ctx* c, T* out) {
                (const T*)c->Bhalf, M, 0, T(0), (T*)c->Phi2, M, 0, 1));
   }
   // Phi3 = exp_T(V) Phi2
-  if (c->tc && c->taylor_fused == 2) {
+  if (c->sparse) {
+    LK(launch_taylor_blocks<T>(c->st, W, M, N, c->p.taylor_order, c->nnzp, (const T*)c->V,
+                               c->blk, (const T*)c->Phi2, (T*)c->Phi3));
+  } else if (c->tc && c->taylor_fused == 2) {
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
                  (const float*)c->Phi2, (float*)c->Phi3, nullptr, c->split3, c->bf16,
                  c->status));
@@ -475,7 +486,17 @@ afqmc_status step_T(afqmc_ctx* c) {
                         sqrt(dt), c->p.fb_cap, c->p.seed, c->p.run_id, c->ctr, (T*)c->S,
                         c->ldS, (T*)c->xbar, c->lw, c->lbar, c->lmf));
   }
-  {
+  if (c->sparse) {   // V on the blocks' entries only, [W][2][nnzp]
+    KTimer t(c, 2);
+    if (c->tc) {
+      LK(tc_gemm(c->tc, c->st, 2 * W, (int)c->nnzp, G, (const float*)c->S, c->ldS,
+                 (const float*)c->LT, c->ldS, (float*)c->V, c->nnzp, 1.0f, 0.0f, nullptr, 0,
+                 c->split3, 1, 0, c->status, c->bn_v, (const float*)c->LT_lo));
+    } else {
+      LK(gemm<T>(c->st, false, false, 2 * W, (int)c->nnz, G, T(1), (const T*)c->S, c->ldS, 0,
+                 (const T*)c->L, c->nnz, 0, T(0), (T*)c->V, c->nnzp, 0, 1));
+    }
+  } else {
     KTimer t(c, 2);
     if (c->tc) {
       const long nv = (long)M * c->ldV;
@@ -527,6 +548,72 @@ afqmc_status step_T(afqmc_ctx* c) {
 // Setup
 // ---------------------------------------------------------------------------
 
+// Block structure shared by all Cholesky vectors: the connected components
+// of the graph with an edge i - j wherever some L_g,ij is nonzero. Each
+// block lists its members in ascending order; blocks are ordered by their
+// first member. V = sum_g s_g L_g is block-diagonal in this partition, and
+// its packed form holds block b's b x b entries row by row at offset o_b.
+struct BlockPlan {
+  bool on = false;
+  int nb = 0, maxb = 0;
+  long nnz = 0;
+  std::vector<int> members;             // [M]: block after block
+  std::vector<int> vrow, bsize, ibase;  // per basis index
+  std::vector<int> gidx;                // [nnz]: i * M + j of each packed entry
+};
+
+BlockPlan detect_blocks(const afqmc_params* p, const double* L) {
+  BlockPlan B;
+  const int M = p->M;
+  if (p->block_sparse == 2 || M < 2) return B;
+  std::vector<int> up(M);
+  for (int i = 0; i < M; ++i) up[i] = i;
+  auto root = [&](int i) {
+    while (up[i] != i) { up[i] = up[up[i]]; i = up[i]; }
+    return i;
+  };
+  for (long g = 0; g < p->n_chol; ++g) {
+    const double* Lg = L + g * M * M;
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < i; ++j)
+        if (Lg[(long)i * M + j] != 0.0) {
+          const int a = root(i), b = root(j);
+          if (a != b) up[a < b ? b : a] = a < b ? a : b;
+        }
+  }
+  std::vector<std::vector<int>> blocks;
+  std::vector<int> slot(M, -1);
+  for (int i = 0; i < M; ++i) {        // ascending i: blocks by first member
+    const int r = root(i);
+    if (slot[r] < 0) { slot[r] = (int)blocks.size(); blocks.emplace_back(); }
+    blocks[slot[r]].push_back(i);
+  }
+  B.nb = (int)blocks.size();
+  for (const auto& b : blocks) {
+    B.maxb = std::max(B.maxb, (int)b.size());
+    B.nnz += (long)b.size() * (long)b.size();
+  }
+  if (B.nb < 2 || B.maxb > 32 || B.nnz > (long)M * M / 4) return B;
+  B.on = true;
+  B.vrow.assign(M, 0);
+  B.bsize.assign(M, 0);
+  B.ibase.assign(M, 0);
+  long off = 0;
+  for (const auto& b : blocks) {
+    const int n = (int)b.size(), base = (int)B.members.size();
+    for (int lp = 0; lp < n; ++lp) {
+      const int i = b[lp];
+      B.vrow[i] = (int)(off + (long)lp * n);
+      B.bsize[i] = n;
+      B.ibase[i] = base;
+      for (int lq = 0; lq < n; ++lq) B.gidx.push_back(i * M + b[lq]);
+    }
+    B.members.insert(B.members.end(), b.begin(), b.end());
+    off += (long)n * n;
+  }
+  return B;
+}
+
 // Size and option checks that need no matrix data.
 afqmc_status validate_sizes(const afqmc_params* p) {
   afqmc_ctx* c = nullptr;
@@ -535,6 +622,10 @@ afqmc_status validate_sizes(const afqmc_params* p) {
     return fail(c, AFQMC_E_INVALID, "weight_mode must be 0 (hybrid) or 1 (local energy)");
   if (p->mf_subtract != 0 && p->mf_subtract != 1)
     return fail(c, AFQMC_E_INVALID, "mf_subtract must be 0 or 1");
+  if (p->block_sparse < 0 || p->block_sparse > 2)
+    return fail(c, AFQMC_E_INVALID, "block_sparse must be 0 (auto), 1 (required) or 2 (dense)");
+  for (int i = 0; i < 3; ++i)
+    if (p->reserved[i] != 0) return fail(c, AFQMC_E_INVALID, "reserved fields must be zero");
   if (p->weight_mode == AFQMC_WEIGHT_LOCAL_ENERGY && p->n_det > 1)
     return fail(c, AFQMC_E_INVALID,
                 "the local-energy weight form needs a one-determinant trial");
@@ -620,6 +711,10 @@ afqmc_status validate(const afqmc_params* p, const double* h1, const double* L,
       }
     }
   }
+  if (p->block_sparse == 1 && !detect_blocks(p, L).on)
+    return fail(c, AFQMC_E_INVALID,
+                "block_sparse = 1, but the Cholesky vectors are not block-diagonal in blocks "
+                "of at most 32 orbitals holding at most M^2/4 entries");
   (void)ci;
   return AFQMC_OK;
 }
@@ -734,12 +829,34 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
     void* dst = sig ? c->Yx_dn : c->Yx_up;
     LK(launch_convert<T>(st, J * c->Jp[sig], yx, (T*)dst));
   }
-  LK(launch_convert<T>(st, (long)G * MM, L, (T*)c->L));
+  if (c->sparse) {   // packed operands of the block-diagonal form
+    double *lp, *lpt = nullptr;
+    int* gidx;
+    TM(lp, (size_t)G * c->nnz);
+    if (c->LT) TM(lpt, (size_t)c->nnzp * c->ldS);
+    {
+      cudaError_t e = cudaMalloc((void**)&gidx, c->nnz * sizeof(int));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (void* q : tmp) cudaFree(q);
+        return fail(c, AFQMC_E_OOM, "setup allocation failed");
+      }
+      tmp.push_back(gidx);
+    }
+    CK(cudaMemcpyAsync(gidx, c->blk_gidx.data(), c->nnz * sizeof(int), cudaMemcpyHostToDevice,
+                       st));
+    LK(launch_pack_blocks(st, G, c->nnz, c->nnzp, c->ldS, M, L, gidx, lp, lpt));
+    LK(launch_convert<T>(st, (long)G * c->nnz, lp, (T*)c->L));
+    if (c->LT) LK(launch_convert<T>(st, c->nnzp * c->ldS, lpt, (T*)c->LT));
+    CK(cudaStreamSynchronize(st));   // the host index list is released below
+  } else {
+    LK(launch_convert<T>(st, (long)G * MM, L, (T*)c->L));
+  }
   CK(cudaMemsetAsync(Ltil_pad, 0, (size_t)(G + 1) * c->ldt * sizeof(double), st));
   LK(launch_pad_rows(st, G + 1, (long)c->nu * M, (long)c->nd * M, Ltil, Ltil_pad, c->ldt,
                      c->dn_off));
   LK(launch_convert<T>(st, (long)(G + 1) * c->ldt, Ltil_pad, (T*)c->Ltil));
-  if (c->LT) {   // L transposed [M*ldV][ldS] for the tensor cores
+  if (c->LT && !c->sparse) {   // L transposed [M*ldV][ldS] for the tensor cores
     double *lt;
     const long nv = (long)M * c->ldV;
     TM(lt, nv * c->ldS);
@@ -769,7 +886,8 @@ afqmc_status setup_T(afqmc_ctx* c, const double* h1_h, const double* L_h,
   }
   if (c->split3) {   // the constant operands of the TF32X3 contractions, split once
     LK(tc_split(st, (long)(G + 1) * c->ldt, (float*)c->Ltil, (float*)c->Ltil_lo));
-    LK(tc_split(st, (long)M * c->ldV * c->ldS, (float*)c->LT, (float*)c->LT_lo));
+    LK(tc_split(st, c->sparse ? c->nnzp * c->ldS : (long)M * c->ldV * c->ldS, (float*)c->LT,
+                (float*)c->LT_lo));
     LK(tc_split(st, (long)c->nu * M * c->Jp[0], (float*)c->Yx_up, (float*)c->Yx_up_lo));
     LK(tc_split(st, (long)c->nd * M * c->Jp[1], (float*)c->Yx_dn, (float*)c->Yx_dn_lo));
   }
@@ -909,13 +1027,14 @@ afqmc_status prepare_multidet(afqmc_ctx* c, const int32_t* ou, const int32_t* od
 struct TuneVal {
   int xsplit, bn_fb, bn_v, bn_e, bn_b, fused;
 };
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, long>;
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 
 TuneKey tune_key(const afqmc_ctx* c) {
   return TuneKey(c->M, c->nu, c->nd, c->G, c->W, c->md ? c->nact[0] : -1,
-                 c->md ? c->nact[1] : -1, c->p.precision, c->p.taylor_order);
+                 c->md ? c->nact[1] : -1, c->p.precision, c->p.taylor_order,
+                 c->sparse ? c->nnz : -1L);
 }
 
 // Shortest of three timed runs (after one untimed run) of `f`, in ms;
@@ -988,12 +1107,12 @@ afqmc_status autotune(afqmc_ctx* c) {
     float best = INFINITY;
     for (int bn : bns) {
       const float ms = best_ms(c, [&]() -> afqmc_status {
-        const long nv = (long)M * c->ldV;
+        const long nv = c->sparse ? c->nnzp : (long)M * c->ldV;
         LK(tc_gemm(c->tc, c->st, 2 * W, (int)nv, G, (const float*)c->S, c->ldS,
                    (const float*)c->LT, c->ldS, (float*)c->V, nv, 1.0f, 0.0f, nullptr, 0,
                    c->split3, 1, 0, c->status, bn, (const float*)c->LT_lo,
-                   c->tc_wide_ok && c->split3 ? (float*)c->Vlo : nullptr,
-                   c->tc_wide_ok && c->bf16));
+                   c->tc_wide_ok && c->split3 && !c->sparse ? (float*)c->Vlo : nullptr,
+                   c->tc_wide_ok && c->bf16 && !c->sparse));
         return AFQMC_OK;
       });
       if (ms < best) { best = ms; v.bn_v = bn; }
@@ -1021,8 +1140,9 @@ afqmc_status autotune(afqmc_ctx* c) {
       if (ms < best) { best = ms; v.bn_e = bn; }
     }
   }
-  // propagation path (into the spare walker buffer Phi2)
-  {
+  // propagation path (into the spare walker buffer Phi2); the block-diagonal
+  // form has one path
+  if (!c->sparse) {
     float best = INFINITY;
     for (int fused = c->tc_wide_ok ? 3 : (c->tc_taylor_ok ? 2 : 0); fused >= 0; --fused) {
       if (fused == 3 && !c->tc_wide_ok) continue;
@@ -1259,6 +1379,7 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->lw, W * sizeof(double2));
   add(&c->eloc, W * sizeof(double2));
   add(&c->hist, kHist * sizeof(double2));
+  add(&c->blk, (size_t)M * (sizeof(int4) + sizeof(int)));
   if (P.mf) {
     add(&c->lbar, G * sizeof(double));
     add(&c->lmf, W * sizeof(double2));
@@ -1339,6 +1460,14 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   c->tc_wide_ok = P.tc_wide_ok;
   c->ldV = P.ldV;
   c->taylor_fused = P.tc_taylor_ok ? 1 : (P.tc_wide_ok ? 3 : 0);
+  BlockPlan B = detect_blocks(&c->p, L);
+  c->sparse = B.on;
+  if (c->sparse) {
+    c->nnz = B.nnz;
+    c->nnzp = round4(B.nnz);
+    c->taylor_fused = 4;
+    c->blk_gidx.swap(B.gidx);
+  }
   c->bn_fb = c->bn_v = c->bn_e = c->bn_b = 0;
   if (c->md) {
     const bool f64c = c->fp64_islands;
@@ -1392,6 +1521,19 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     c->mdt.CactT[0] = c->md_ct0;
     c->mdt.CactT[1] = c->md_ct1;
   }
+  {
+    std::vector<int> tab((size_t)M * 5, 0);   // M int4 rows, then the M members
+    if (c->sparse)
+      for (int i = 0; i < M; ++i) {
+        tab[4 * i] = B.vrow[i];
+        tab[4 * i + 1] = B.bsize[i];
+        tab[4 * i + 2] = B.ibase[i];
+        tab[4 * M + i] = B.members[i];
+      }
+    CK(cudaMemcpyAsync(c->blk, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
   CK(cudaMemsetAsync(c->ctr, 0, 2 * sizeof(long long), c->st));
   CK(cudaMemsetAsync(c->lw, 0, W * sizeof(double2), c->st));
@@ -1409,6 +1551,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   }
   afqmc_status s = c->fp64 ? setup_T<double>(c, h1, L, Cu, Cd, ou, od)
                            : setup_T<float>(c, h1, L, Cu, Cd, ou, od);
+  std::vector<int>().swap(c->blk_gidx);
   if (s != AFQMC_OK) return s;
   if (c->tc && c->p.autotune) {
     s = autotune(c);
@@ -1795,8 +1938,9 @@ afqmc_status afqmc_kernel_stats(afqmc_ctx* c, int32_t id, int64_t* launches, dou
   switch (id) {
     case 0: wk = 4.0 * W * G * N * M; break;                         // Theta . L~^T
     case 1: wk = W * 2 * G * es * 3 + W * 16; byt = 1; break;        // X in, S + xbar out
-    case 2: wk = 4.0 * W * G * M * M; break;                         // S . L
-    case 3: wk = 8.0 * T * M * M * N * W + 8.0 * M * M * N * W; break;
+    case 2: wk = 4.0 * W * G * (c->sparse ? (double)c->nnz : M * M); break;   // S . L
+    case 3: wk = 8.0 * T * (c->sparse ? (double)c->nnz : M * M) * N * W + 8.0 * M * M * N * W;
+      break;
     case 4: {
       double f = 0.0;
       for (int sig = 0; sig < 2; ++sig) {
@@ -1869,8 +2013,12 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* c, const afqmc_tuning* t) {
   if (!bn_ok(t->bn_force_bias) || !bn_ok(t->bn_one_body) || !bn_ok(t->bn_energy) ||
       !bn_ok(t->bn_half_step))
     return fail(c, AFQMC_E_INVALID, "tile widths must be 64 or 128");
-  if (t->taylor_fused < 0 || t->taylor_fused > 3)
-    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0, 1, 2 or 3");
+  if (t->taylor_fused < 0 || t->taylor_fused > 4)
+    return fail(c, AFQMC_E_INVALID, "taylor_fused must be 0, 1, 2, 3 or 4");
+  if ((t->taylor_fused == 4) != c->sparse)
+    return fail(c, AFQMC_E_INVALID,
+                c->sparse ? "block-diagonal Cholesky vectors: the propagation path is 4"
+                          : "taylor_fused = 4 needs block-diagonal Cholesky vectors");
   if ((t->taylor_fused == 1 || t->taylor_fused == 2) && !c->tc_taylor_ok)
     return fail(c, AFQMC_E_INVALID, "the on-chip tensor-core Taylor kernel needs M <= 64");
   if (t->taylor_fused == 3 && !c->tc_wide_ok)

@@ -127,6 +127,18 @@ template <typename T>
 cudaError_t launch_gather_rows(cudaStream_t st, int W, long elems, const int* parent,
                                const T* in, T* out);
 
+// Block-diagonal Cholesky vectors. Setup: packed operands Lp [n_chol][nnz]
+// and (LpT non-NULL) LpT [nnzp][ldS] from the FP64 L [n_chol][M*M], gidx
+// [nnz] holding the i*M+j of each packed entry. Step: the Taylor series of
+// the packed V [W][2][nnzp] applied to Pin [W][N][2][M] into Pout, blk
+// holding the M int4 {row offset, block size, member base, 0} and then the
+// M member indices.
+cudaError_t launch_pack_blocks(cudaStream_t st, int G, long nnz, long nnzp, long ldS, int M,
+                               const double* L, const int* gidx, double* Lp, double* LpT);
+template <typename T>
+cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order, long nnzp,
+                                 const T* V, const void* blk, const T* Pin, T* Pout);
+
 // Setup helpers (FP64).
 cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,
                                 const double* L, const double* lbar, double* h1p);

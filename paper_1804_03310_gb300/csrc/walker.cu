@@ -5,6 +5,8 @@
 // (Sec. III, Eq. 5), and the comb (Sec. V).
 #include <float.h>
 
+#include <algorithm>
+
 #include <map>
 #include <mutex>
 #include <utility>
@@ -1334,6 +1336,126 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
   return cudaGetLastError();
 }
 
+// ------------------------------------------- K4 + K5, block-diagonal L_g
+namespace {
+
+// Packed Cholesky operands of the block-diagonal form: Lp[g][e] =
+// L_g[gidx[e]] ([n_chol][nnz]) and, for the tensor cores, its transpose
+// LpT[e][g] ([nnzp][ldS], zero beyond nnz and n_chol). FP64, at setup.
+__global__ void pack_blocks_kernel(int G, long nnz, long nnzp, long ldS, long MM,
+                                   const double* __restrict__ L, const int* __restrict__ gidx,
+                                   double* __restrict__ Lp, double* __restrict__ LpT) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= nnzp * ldS) return;
+  const long r = e / ldS;
+  const int g = (int)(e - r * ldS);
+  const bool in = r < nnz && g < G;
+  const double v = in ? L[(long)g * MM + gidx[r]] : 0.0;
+  if (LpT) LpT[e] = v;
+  if (in) Lp[(long)g * nnz + r] = v;
+}
+
+// K5's series for a block-diagonal V: Pout = sum_{n <= order} V^n Pin / n!,
+// V packed [W][2][nnzp] (real entries, then imaginary; each basis index's
+// row of its block at tab[p].x, tab[p].y entries long, its block's members
+// at members[tab[p].z ..]), Pin / Pout [W][N][2][M]. One block per walker:
+// the walker's V and a chunk of jc columns (current term, next term,
+// running sum) in shared memory; one thread per (column, row) element.
+template <typename T>
+__global__ void taylor_blocks_kernel(int M, int N, int order, long nnzp, int jc, size_t tab_off,
+                                     const T* __restrict__ V, const int4* __restrict__ tab,
+                                     const int* __restrict__ members,
+                                     const T* __restrict__ Pin, T* __restrict__ Pout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* vr = reinterpret_cast<T*>(smem_raw);
+  T* vi = vr + nnzp;
+  const long cs = (long)jc * 2 * M;
+  T* t = vi + nnzp;
+  T* tn = t + cs;
+  T* acc = tn + cs;
+  int4* tb = reinterpret_cast<int4*>(smem_raw + tab_off);
+  int* mem = reinterpret_cast<int*>(tb + M);
+  const int w = blockIdx.x;
+  const T* Vw = V + (long)w * 2 * nnzp;
+  for (long e = threadIdx.x; e < nnzp; e += blockDim.x) {
+    vr[e] = Vw[e];
+    vi[e] = Vw[nnzp + e];
+  }
+  for (int p = threadIdx.x; p < M; p += blockDim.x) {
+    tb[p] = tab[p];
+    mem[p] = members[p];
+  }
+  for (int j0 = 0; j0 < N; j0 += jc) {
+    const int nc = min(jc, N - j0);
+    const long ne = (long)nc * 2 * M;
+    const T* Pw = Pin + ((long)w * N + j0) * 2 * M;
+    __syncthreads();                       // tables ready, the last chunk's reads done
+    for (long e = threadIdx.x; e < ne; e += blockDim.x) {
+      const T x = Pw[e];
+      t[e] = x;
+      acc[e] = x;
+    }
+    T* cur = t;
+    T* nxt = tn;
+    for (int n = 1; n <= order; ++n) {
+      __syncthreads();                     // the previous term is complete
+      const T inv = T(1) / T(n);
+      for (long e = threadIdx.x; e < (long)nc * M; e += blockDim.x) {
+        const int j = (int)(e / M), p = (int)(e - (long)j * M);
+        const int4 d = tb[p];
+        const T* cr = cur + (long)j * 2 * M;
+        const T* ci = cr + M;
+        T sr = T(0), si = T(0);
+        for (int q = 0; q < d.y; ++q) {
+          const int k = mem[d.z + q];
+          const T ar = vr[d.x + q], ai = vi[d.x + q], br = cr[k], bi = ci[k];
+          sr = fma(ar, br, fma(-ai, bi, sr));
+          si = fma(ar, bi, fma(ai, br, si));
+        }
+        sr *= inv;
+        si *= inv;
+        const long o = (long)j * 2 * M + p;
+        nxt[o] = sr;
+        nxt[o + M] = si;
+        acc[o] += sr;
+        acc[o + M] += si;
+      }
+      T* sw = cur;
+      cur = nxt;
+      nxt = sw;
+    }
+    __syncthreads();
+    T* Ow = Pout + ((long)w * N + j0) * 2 * M;
+    for (long e = threadIdx.x; e < ne; e += blockDim.x) Ow[e] = acc[e];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_blocks(cudaStream_t st, int G, long nnz, long nnzp, long ldS, int M,
+                               const double* L, const int* gidx, double* Lp, double* LpT) {
+  const long n = nnzp * ldS;
+  pack_blocks_kernel<<<blocks_for(n, 256), 256, 0, st>>>(G, nnz, nnzp, ldS, (long)M * M, L,
+                                                         gidx, Lp, LpT);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order, long nnzp,
+                                 const T* V, const void* blk, const T* Pin, T* Pout) {
+  if (W < 1 || M < 1 || N < 1 || order < 0) return cudaErrorInvalidValue;
+  const size_t cap = smem_optin((const void*)taylor_blocks_kernel<T>);
+  const size_t tabs = (size_t)M * (sizeof(int4) + sizeof(int));
+  const size_t vbytes = 2 * (size_t)nnzp * sizeof(T), per_col = 6 * (size_t)M * sizeof(T);
+  if (cap < vbytes + per_col + tabs + 16) return cudaErrorInvalidValue;
+  const int jc = (int)std::min<size_t>((size_t)N, (cap - vbytes - tabs - 16) / per_col);
+  const size_t tab_off = (vbytes + (size_t)jc * per_col + 15) & ~(size_t)15;
+  const int4* tab = reinterpret_cast<const int4*>(blk);
+  taylor_blocks_kernel<T><<<W, 256, tab_off + tabs, st>>>(
+      M, N, order, nnzp, jc, tab_off, V, tab, reinterpret_cast<const int*>(tab + M), Pin, Pout);
+  return cudaGetLastError();
+}
+
 #define AFQMC_INST(T)                                                                    \
   template cudaError_t launch_fields<T>(cudaStream_t, int, int, const T*, long, int,    \
                                         long, double, double, uint64_t, int,            \
@@ -1356,7 +1478,9 @@ cudaError_t launch_axpy_d(cudaStream_t st, long n, double a, const double* x, do
                                         double*);                                       \
   template cudaError_t launch_convert<T>(cudaStream_t, long, const double*, T*);        \
   template cudaError_t launch_init_walkers<T>(cudaStream_t, int, int, int, const T*,    \
-                                              T*, double*);
+                                              T*, double*);                             \
+  template cudaError_t launch_taylor_blocks<T>(cudaStream_t, int, int, int, int, long,  \
+                                               const T*, const void*, const T*, T*);
 AFQMC_INST(float)
 AFQMC_INST(double)
 

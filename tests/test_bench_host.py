@@ -46,3 +46,9 @@ def test_small_matrix_kernels_are_rated_against_fp32():
     r = bench.roofline_for(stats("overlap"), "tf32x3", PEAKS, "measured", config_c2(), "c2")
     assert r["bound"] == "alu"
     assert r["traffic"] == bench.lookup_traffic("overlap", "tf32x3", "c2")
+
+
+def test_block_diagonal_series_is_rated_against_fp32():
+    r = bench.roofline_for(stats("propagate"), "bf16x3", PEAKS, "measured", config_c3(), "c3",
+                           taylor_fused=4)
+    assert r["bound"] == "alu"

@@ -75,6 +75,8 @@ def test_invalid_inputs_rejected_before_device(lib, mutate, needle):
     (dict(weight_mode=2), "weight_mode"),
     (dict(mf_subtract=-1), "mf_subtract"),
     (dict(weight_mode=1, n_det=2), "one-determinant"),
+    (dict(block_sparse=3), "block_sparse"),
+    (dict(block_sparse=1), "not block-diagonal"),
 ])
 def test_invalid_params_rejected(lib, kw, needle):
     from paper_1804_03310_gb300 import AfqmcError
