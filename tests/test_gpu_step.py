@@ -337,9 +337,11 @@ def test_streamed_tensor_core_taylor(M, nu, nd, G, W, prec):
 
 @pytest.mark.parametrize("prec,fused", [("tf32x3", 3), ("tf32x3", 0), ("bf16x3", 3)])
 def test_c3_full_size_taylor_paths(prec, fused):
-    """The TM-atom shape at full size with each propagation path forced."""
+    """The TM-atom shape at full size with each dense propagation path forced
+    (its shell-structured Cholesky vectors would otherwise take the
+    block-diagonal path)."""
     s = config_c3(pc_every=0)
-    gpu = gpu_ctx(s, precision=prec)
+    gpu = gpu_ctx(s, precision=prec, block_sparse=2)
     gpu.afqmc_set_tuning(taylor_fused=fused)
     orc = O.OracleRun(s, walker_ids=[0, 2047])
     w = run_side_by_side(gpu, orc, 20, 1e-4, walkers=[0, 2047], energy_at=(20,),
