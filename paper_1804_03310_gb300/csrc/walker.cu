@@ -1397,13 +1397,16 @@ __global__ void taylor_blocks_kernel(int M, int N, int order, long nnzp, int jc,
     }
     T* cur = t;
     T* nxt = tn;
+    // this thread's first element (column j, row p); it then steps by
+    // blockDim.x elements, (j, p) advanced without a division
+    const int e0 = (int)threadIdx.x, step_j = (int)blockDim.x / M, step_p = (int)blockDim.x % M;
     for (int n = 1; n <= order; ++n) {
       __syncthreads();                     // the previous term is complete
       const T inv = T(1) / T(n);
-      for (long e = threadIdx.x; e < (long)nc * M; e += blockDim.x) {
-        const int j = (int)(e / M), p = (int)(e - (long)j * M);
+      int j = e0 / M, p = e0 - j * M;
+      for (; j < nc;) {
         const int4 d = tb[p];
-        const T* cr = cur + (long)j * 2 * M;
+        const T* cr = cur + j * 2 * M;
         const T* ci = cr + M;
         T sr = T(0), si = T(0);
         for (int q = 0; q < d.y; ++q) {
@@ -1414,11 +1417,14 @@ __global__ void taylor_blocks_kernel(int M, int N, int order, long nnzp, int jc,
         }
         sr *= inv;
         si *= inv;
-        const long o = (long)j * 2 * M + p;
+        const int o = j * 2 * M + p;
         nxt[o] = sr;
         nxt[o + M] = si;
         acc[o] += sr;
         acc[o + M] += si;
+        j += step_j;
+        p += step_p;
+        if (p >= M) { p -= M; ++j; }
       }
       T* sw = cur;
       cur = nxt;
@@ -1448,7 +1454,11 @@ cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order
   const size_t tabs = (size_t)M * (sizeof(int4) + sizeof(int));
   const size_t vbytes = 2 * (size_t)nnzp * sizeof(T), per_col = 6 * (size_t)M * sizeof(T);
   if (cap < vbytes + per_col + tabs + 16) return cudaErrorInvalidValue;
-  const int jc = (int)std::min<size_t>((size_t)N, (cap - vbytes - tabs - 16) / per_col);
+  // columns per chunk: all of them if the block stays within 48 KB (several
+  // blocks per SM hide the shared-memory latencies), else as many as fit
+  const size_t want = std::max<size_t>(48 * 1024, vbytes + per_col + tabs + 16);
+  const size_t room = std::min(cap, want) - vbytes - tabs - 16;
+  const int jc = (int)std::max<size_t>(1, std::min<size_t>((size_t)N, room / per_col));
   const size_t tab_off = (vbytes + (size_t)jc * per_col + 15) & ~(size_t)15;
   const int4* tab = reinterpret_cast<const int4*>(blk);
   taylor_blocks_kernel<T><<<W, 256, tab_off + tabs, st>>>(
