@@ -86,6 +86,7 @@ struct afqmc_ctx {
   // block's member list, 0}, then the member lists (M ints)
   bool sparse;
   long nnz, nnzp;
+  int nblk, maxblk;
   void* blk;
   std::vector<int> blk_gidx;   // host, during setup: i*M+j of each packed entry
   int *parent, *status;
@@ -442,8 +443,9 @@ afqmc_status propagate_T(afqmc_ctx* c, T* out) {
   }
   // Phi3 = exp_T(V) Phi2
   if (c->sparse) {
-    LK(launch_taylor_blocks<T>(c->st, W, M, N, c->p.taylor_order, c->nnzp, (const T*)c->V,
-                               c->blk, (const T*)c->Phi2, (T*)c->Phi3));
+    LK(launch_taylor_blocks<T>(c->st, W, M, N, c->p.taylor_order, c->nnzp, c->nblk,
+                               c->maxblk, (const T*)c->V, c->blk, (const T*)c->Phi2,
+                               (T*)c->Phi3));
   } else if (c->tc && c->taylor_fused == 2) {
     LK(tc_taylor(c->tc, c->st, W, M, N, c->p.taylor_order, (const float*)c->V,
                  (const float*)c->Phi2, (float*)c->Phi3, nullptr, c->split3, c->bf16,
@@ -1379,7 +1381,7 @@ std::vector<Buf> buffer_list(afqmc_ctx* c, const Plan& P) {
   add(&c->lw, W * sizeof(double2));
   add(&c->eloc, W * sizeof(double2));
   add(&c->hist, kHist * sizeof(double2));
-  add(&c->blk, (size_t)M * (sizeof(int4) + sizeof(int)));
+  add(&c->blk, (size_t)M * (2 * sizeof(int4) + sizeof(int)));
   if (P.mf) {
     add(&c->lbar, G * sizeof(double));
     add(&c->lmf, W * sizeof(double2));
@@ -1465,6 +1467,8 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
   if (c->sparse) {
     c->nnz = B.nnz;
     c->nnzp = round4(B.nnz);
+    c->nblk = B.nb;
+    c->maxblk = B.maxb;
     c->taylor_fused = 4;
     c->blk_gidx.swap(B.gidx);
   }
@@ -1522,14 +1526,25 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1, const double* L,
     c->mdt.CactT[1] = c->md_ct1;
   }
   {
-    std::vector<int> tab((size_t)M * 5, 0);   // M int4 rows, then the M members
-    if (c->sparse)
+    // M int4 rows, M int4 block slots, then the M members (the int4 arrays
+    // 16-byte aligned)
+    std::vector<int> tab((size_t)M * 9, 0);
+    if (c->sparse) {
+      int nb = 0;
       for (int i = 0; i < M; ++i) {
         tab[4 * i] = B.vrow[i];
         tab[4 * i + 1] = B.bsize[i];
         tab[4 * i + 2] = B.ibase[i];
-        tab[4 * M + i] = B.members[i];
+        tab[8 * (size_t)M + i] = B.members[i];
       }
+      for (int k = 0; k < M; k += B.bsize[B.members[k]], ++nb) {   // blocks in member order
+        const int first = B.members[k];
+        int* bt = &tab[4 * (size_t)M + 4 * (size_t)nb];
+        bt[0] = B.vrow[first];
+        bt[1] = B.bsize[first];
+        bt[2] = k;
+      }
+    }
     CK(cudaMemcpyAsync(c->blk, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice,
                        c->st));
     CK(cudaStreamSynchronize(c->st));

@@ -131,13 +131,15 @@ cudaError_t launch_gather_rows(cudaStream_t st, int W, long elems, const int* pa
 // and (LpT non-NULL) LpT [nnzp][ldS] from the FP64 L [n_chol][M*M], gidx
 // [nnz] holding the i*M+j of each packed entry. Step: the Taylor series of
 // the packed V [W][2][nnzp] applied to Pin [W][N][2][M] into Pout, blk
-// holding the M int4 {row offset, block size, member base, 0} and then the
-// M member indices.
+// holding the M int4 {row offset, block size, member base, 0}, M int4 slots
+// of which the first nb are the blocks' {first row offset, size, member
+// base, 0}, then the M member indices; maxb the largest block.
 cudaError_t launch_pack_blocks(cudaStream_t st, int G, long nnz, long nnzp, long ldS, int M,
                                const double* L, const int* gidx, double* Lp, double* LpT);
 template <typename T>
 cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order, long nnzp,
-                                 const T* V, const void* blk, const T* Pin, T* Pout);
+                                 int nb, int maxb, const T* V, const void* blk, const T* Pin,
+                                 T* Pout);
 
 // Setup helpers (FP64).
 cudaError_t launch_h1_remainder(cudaStream_t st, int M, int n_chol, const double* h1,

@@ -1436,6 +1436,82 @@ __global__ void taylor_blocks_kernel(int M, int N, int order, long nnzp, int jc,
   }
 }
 
+// The same series with one thread per (block, column) task, the block's
+// piece of the column in registers (blocks of at most MAXB orbitals): tasks
+// run column-fastest, so the threads of a warp read the same entries of V
+// (broadcast) and nothing else goes through shared memory. btab holds per
+// block {offset of its first row in V, size, member base, 0}.
+template <typename T, int MAXB>
+__global__ void taylor_blocks_reg_kernel(int M, int N, int order, long nnzp, int nb,
+                                         const T* __restrict__ V, const int4* __restrict__ btab,
+                                         const int* __restrict__ members,
+                                         const T* __restrict__ Pin, T* __restrict__ Pout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* vr = reinterpret_cast<T*>(smem_raw);
+  T* vi = vr + nnzp;
+  const int w = blockIdx.x;
+  const T* Vw = V + (long)w * 2 * nnzp;
+  for (long e = threadIdx.x; e < nnzp; e += blockDim.x) {
+    vr[e] = Vw[e];
+    vi[e] = Vw[nnzp + e];
+  }
+  __syncthreads();
+  for (int task = threadIdx.x; task < nb * N; task += blockDim.x) {
+    const int bl = task / N, j = task - bl * N;
+    const int4 d = btab[bl];
+    const int b = d.y;
+    const T* pr = Pin + ((long)w * N + j) * 2 * M;
+    const T* pi = pr + M;
+    int mem[MAXB];
+    T xr[MAXB], xi[MAXB], sr[MAXB], si[MAXB];
+#pragma unroll
+    for (int p = 0; p < MAXB; ++p) {
+      mem[p] = p < b ? members[d.z + p] : 0;
+      xr[p] = p < b ? pr[mem[p]] : T(0);
+      xi[p] = p < b ? pi[mem[p]] : T(0);
+      sr[p] = xr[p];
+      si[p] = xi[p];
+    }
+    for (int n = 1; n <= order; ++n) {
+      const T inv = T(1) / T(n);
+      T yr[MAXB], yi[MAXB];
+#pragma unroll
+      for (int p = 0; p < MAXB; ++p) {
+        T ar_ = T(0), ai_ = T(0);
+        if (p < b) {
+          const T* vrp = vr + d.x + p * b;
+          const T* vip = vi + d.x + p * b;
+#pragma unroll
+          for (int q = 0; q < MAXB; ++q) {
+            if (q < b) {
+              const T a = vrp[q], c = vip[q];
+              ar_ = fma(a, xr[q], fma(-c, xi[q], ar_));
+              ai_ = fma(a, xi[q], fma(c, xr[q], ai_));
+            }
+          }
+        }
+        yr[p] = ar_ * inv;
+        yi[p] = ai_ * inv;
+      }
+#pragma unroll
+      for (int p = 0; p < MAXB; ++p) {
+        xr[p] = yr[p];
+        xi[p] = yi[p];
+        sr[p] += yr[p];
+        si[p] += yi[p];
+      }
+    }
+    T* qr = Pout + ((long)w * N + j) * 2 * M;
+    T* qi = qr + M;
+#pragma unroll
+    for (int p = 0; p < MAXB; ++p)
+      if (p < b) {
+        qr[mem[p]] = sr[p];
+        qi[mem[p]] = si[p];
+      }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_blocks(cudaStream_t st, int G, long nnz, long nnzp, long ldS, int M,
@@ -1448,8 +1524,22 @@ cudaError_t launch_pack_blocks(cudaStream_t st, int G, long nnz, long nnzp, long
 
 template <typename T>
 cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order, long nnzp,
-                                 const T* V, const void* blk, const T* Pin, T* Pout) {
-  if (W < 1 || M < 1 || N < 1 || order < 0) return cudaErrorInvalidValue;
+                                 int nb, int maxb, const T* V, const void* blk, const T* Pin,
+                                 T* Pout) {
+  if (W < 1 || M < 1 || N < 1 || order < 0 || nb < 1 || nb > M) return cudaErrorInvalidValue;
+  // blk: M int4 rows, M int4 block slots, then the M member indices (every
+  // int4 array at a 16-byte multiple)
+  const int4* tab = reinterpret_cast<const int4*>(blk);
+  const int4* btab = tab + M;
+  const int* members = reinterpret_cast<const int*>(tab + 2 * (long)M);
+  if (maxb <= 8) {   // registers: one thread per (block, column)
+    const size_t smem = 2 * (size_t)nnzp * sizeof(T);
+    if (smem > smem_optin((const void*)taylor_blocks_reg_kernel<T, 8>))
+      return cudaErrorInvalidValue;
+    taylor_blocks_reg_kernel<T, 8><<<W, 256, smem, st>>>(M, N, order, nnzp, nb, V, btab,
+                                                          members, Pin, Pout);
+    return cudaGetLastError();
+  }
   const size_t cap = smem_optin((const void*)taylor_blocks_kernel<T>);
   const size_t tabs = (size_t)M * (sizeof(int4) + sizeof(int));
   const size_t vbytes = 2 * (size_t)nnzp * sizeof(T), per_col = 6 * (size_t)M * sizeof(T);
@@ -1460,9 +1550,8 @@ cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order
   const size_t room = std::min(cap, want) - vbytes - tabs - 16;
   const int jc = (int)std::max<size_t>(1, std::min<size_t>((size_t)N, room / per_col));
   const size_t tab_off = (vbytes + (size_t)jc * per_col + 15) & ~(size_t)15;
-  const int4* tab = reinterpret_cast<const int4*>(blk);
-  taylor_blocks_kernel<T><<<W, 256, tab_off + tabs, st>>>(
-      M, N, order, nnzp, jc, tab_off, V, tab, reinterpret_cast<const int*>(tab + M), Pin, Pout);
+  taylor_blocks_kernel<T><<<W, 256, tab_off + tabs, st>>>(M, N, order, nnzp, jc, tab_off, V,
+                                                          tab, members, Pin, Pout);
   return cudaGetLastError();
 }
 
@@ -1490,7 +1579,8 @@ cudaError_t launch_taylor_blocks(cudaStream_t st, int W, int M, int N, int order
   template cudaError_t launch_init_walkers<T>(cudaStream_t, int, int, int, const T*,    \
                                               T*, double*);                             \
   template cudaError_t launch_taylor_blocks<T>(cudaStream_t, int, int, int, int, long,  \
-                                               const T*, const void*, const T*, T*);
+                                               int, int, const T*, const void*, const T*, \
+                                               T*);
 AFQMC_INST(float)
 AFQMC_INST(double)
 

@@ -10,7 +10,7 @@ import pytest
 
 from gpu_helpers import side_by_side as run_side_by_side
 from oracle import afqmc as O
-from synth import config_c3, make_system
+from synth import config_c3, make_system, small_system
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +76,20 @@ def test_multidet_and_weight_forms_on_shells(prec):
     le = shells(20, 4, 3, 30, 12).replace(weight_mode=1, mf_subtract=1)
     w = side_by_side(le, prec, 12, energy_at=(4, 12))
     print(f"shells local energy mean field {prec} worst", w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_large_blocks_and_scattered_members(prec):
+    """Blocks above 8 orbitals (the shared-memory form of the series) whose
+    members are not contiguous: the same random permutation applied to the
+    basis of a block-diagonal Hamiltonian."""
+    s = small_system(M=40, n_up=5, n_dn=4, n_chol=24, seed=17, l_sigma=0.1, n_walkers=10,
+                     dtau=0.01, ortho_every=2, measure_every=4, pc_every=4)
+    mask = np.zeros((40, 40))
+    for a in range(0, 40, 10):      # four blocks of 10: 400 entries = M^2 / 4
+        mask[a:a + 10, a:a + 10] = 1.0
+    perm = np.random.default_rng(3).permutation(40)
+    mask = mask[np.ix_(perm, perm)]
+    s = s.replace(L=s.L * mask[None])
+    w = side_by_side(s, prec, 8, energy_at=(4, 8))
+    print(f"large scattered blocks {prec} worst", w)
