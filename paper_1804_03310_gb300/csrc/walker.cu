@@ -662,9 +662,13 @@ __global__ void weights_kernel(int W, const double2* __restrict__ logO_new,
 // QR of each walker's spin block, Phi = Q R with R upper triangular and its
 // diagonal real and positive (the factorisation modified Gram-Schmidt
 // produces), computed through the Gram matrix: S = Phi^H Phi = R^H R
-// (Cholesky), then Q = Phi R^-1 row by row. The walkers are re-orthonormalised
-// every few steps, so S stays close to the identity and the Cholesky route is
-// as accurate as Gram-Schmidt. One block per (walker, spin); ln det R =
+// (Cholesky), then Q = Phi R^-1 row by row. The route's loss of
+// orthogonality grows with cond(Phi)^2; walkers re-orthonormalised every
+// step or two stay close to orthonormal (cond(Phi) near 1), where it stays
+// at the level of the arithmetic's own rounding (|Q^H Q - I| below 1e-5 in
+// FP32 at the H-chain and TM-atom shapes with orthonormalisation every 2
+// steps); a larger cadence calls for FP64 arithmetic here (fp64_islands).
+// One block per (walker, spin); ln det R =
 // sum_j ln R_jj is accumulated in FP64 into lr[w][spin].
 template <typename T, typename R>
 __global__ void qr_kernel(int M, int n_up, int n_dn, T* __restrict__ Phi,
