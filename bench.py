@@ -539,32 +539,36 @@ def _blocks(s, precision, n_blocks, **kw):
 
 
 def islands_leg(s, precision, value):
-    """The bench workload with the small inverse and the QR in FP64
-    arithmetic (fp64_islands = 1, the spec form: FP64 only for the
-    orthonormalisation, the log-determinants and the weights) beside the
-    default FP32 arithmetic there."""
+    """The bench workload with FP64 arithmetic islands beside the default
+    FP32 arithmetic there: fp64_islands = 2, the QR alone in FP64 (the
+    spec form: FP64 only for the orthonormalisation, the
+    log-determinants and the weights), and fp64_islands = 1, the small
+    inverse as well."""
     import torch
     from paper_1804_03310_gb300 import Afqmc
-    stream = torch.cuda.Stream()
-    ctx = Afqmc.from_system(s, precision=precision, fp64_islands=True,
-                            stream=stream.cuda_stream)
-    ctx.afqmc_propagate(BLOCK)
-    stream.synchronize()
-    total = 0.0
-    n = 3
-    for _ in range(n):
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+    out = {}
+    for mode, key in ((2, "qr"), (1, "qr_and_inverse")):
+        stream = torch.cuda.Stream()
+        ctx = Afqmc.from_system(s, precision=precision, fp64_islands=mode,
+                                stream=stream.cuda_stream)
         ctx.afqmc_propagate(BLOCK)
-        e.record(stream)
-        e.synchronize()
-        total += a.elapsed_time(e)
-    ctx.close()
-    v = s.n_walkers * BLOCK * n / (total / 1e3)
-    return {"fp64_islands": 1, "value": round(v, 1), "unit": METRIC,
-            "ms_per_block": round(total / n, 3),
-            "ratio_to_default": round(v / value, 3)}
+        stream.synchronize()
+        total = 0.0
+        n = 3
+        for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.afqmc_propagate(BLOCK)
+            e.record(stream)
+            e.synchronize()
+            total += a.elapsed_time(e)
+        ctx.close()
+        v = s.n_walkers * BLOCK * n / (total / 1e3)
+        out[key] = {"fp64_islands": mode, "value": round(v, 1), "unit": METRIC,
+                    "ms_per_block": round(total / n, 3),
+                    "ratio_to_default": round(v / value, 3)}
+    return out
 
 
 def batch_leg(precision, n_blocks=4):

@@ -65,8 +65,8 @@ typedef enum {
  *          as in TF32X3.
  * The reduced modes keep FP64 for walker weights, the accumulation of
  * log-determinants and ln det R, the population-control prefix sums and the
- * energy shift E_T; params.fp64_islands moves the small inverse and
- * Gram-Schmidt arithmetic to FP64 as well. */
+ * energy shift E_T; params.fp64_islands moves the QR (Sec. IV.A), and
+ * optionally the small inverse, to FP64 arithmetic as well. */
 typedef enum {
   AFQMC_FP64 = 0,
   AFQMC_FP32 = 1,
@@ -110,9 +110,11 @@ typedef struct {
   double fb_cap;         /* cap on |xbar_g|; <= 0 disables the cap */
   double e_shift;        /* energy shift E_T; NaN: local energy of the reference determinant */
   int32_t fp64_islands;  /* reduced-precision modes: 1 = Gauss-Jordan inverse and
-                            Gram-Schmidt arithmetic in FP64; 0 (default) = FP32
-                            arithmetic there, with the log-determinant and
-                            ln det R sums still accumulated in FP64 */
+                            Gram-Schmidt (QR) arithmetic in FP64; 2 = the QR
+                            alone in FP64; 0 (default) = FP32 arithmetic
+                            there, with the log-determinant and ln det R
+                            sums still accumulated in FP64. Other values:
+                            AFQMC_E_INVALID */
   int32_t graphs;        /* 1: afqmc_propagate replays whole periods of the
                             ortho / measure / comb cadence as CUDA graphs
                             (same kernels, same results); 0: plain launches */

@@ -199,7 +199,8 @@ class Inputs:
         p.taylor_order = taylor_order
         p.fb_cap = fb_cap
         p.e_shift = math.nan if e_shift is None else e_shift
-        p.fp64_islands = int(bool(fp64_islands))
+        # False/True as 0/1; "qr" (or 2): the QR alone in FP64
+        p.fp64_islands = 2 if fp64_islands == "qr" else int(fp64_islands)
         p.graphs = int(bool(graphs))
         p.autotune = int(bool(autotune))
         p.weight_cap = int(weight_cap)

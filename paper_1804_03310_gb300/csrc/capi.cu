@@ -51,7 +51,8 @@ struct afqmc_ctx {
   afqmc_params p;
   int M, nu, nd, N, G, W, ndet;
   bool fp64;
-  bool fp64_islands;   // Gauss-Jordan and Gram-Schmidt arithmetic in FP64
+  bool fp64_islands;   // Gauss-Jordan (and multi-determinant) arithmetic in FP64
+  bool fp64_qr;        // Gram-Schmidt (QR) arithmetic in FP64
   cudaStream_t st;
   bool own_stream;
   long step;
@@ -361,7 +362,7 @@ template <typename T>
 afqmc_status mgs_T(afqmc_ctx* c) {
   KTimer t(c, 6);
   LK(launch_qr<T>(c->st, c->W, c->M, c->nu, c->nd, (T*)c->Phi, c->logO, c->lr,
-                  c->fp64_islands));
+                  c->fp64_qr));
   return AFQMC_OK;
 }
 
@@ -654,6 +655,8 @@ afqmc_status validate_sizes(const afqmc_params* p) {
   if (p->run_id < 0 || p->run_id >= (1 << 29)) return fail(c, AFQMC_E_INVALID, "run_id out of range");
   if (p->ortho_every < 0 || p->measure_every < 0 || p->pc_every < 0)
     return fail(c, AFQMC_E_INVALID, "cadences must be >= 0");
+  if (p->fp64_islands < 0 || p->fp64_islands > 2)
+    return fail(c, AFQMC_E_INVALID, "fp64_islands must be 0, 1 or 2");
   const int nmax = p->n_up > p->n_dn ? p->n_up : p->n_dn;
   const bool f64 = p->precision == AFQMC_FP64 || p->fp64_islands;
   if (afqmc::overlap_smem(M, nmax, f64 ? 16 : 8) > 227 * 1024)
@@ -1620,7 +1623,8 @@ afqmc_status afqmc_create(const afqmc_params* params, const double* h1, const do
   c->W = params->n_walkers;
   c->ndet = params->n_det;
   c->fp64 = params->precision == AFQMC_FP64;
-  c->fp64_islands = c->fp64 || params->fp64_islands != 0;
+  c->fp64_islands = c->fp64 || params->fp64_islands == 1;
+  c->fp64_qr = c->fp64 || params->fp64_islands != 0;
   c->step = 0;
   c->n_meas = 0;
   c->poisoned = false;
@@ -2055,7 +2059,7 @@ afqmc_status afqmc_footprint(const afqmc_params* p, const int32_t* occ_up,
     if (!occ_up || !occ_dn)
       return fail(nullptr, AFQMC_E_INVALID, "a multi-determinant footprint needs the occupations");
     count_active(p, occ_up, occ_dn, nact);
-    const bool f64c = p->precision == AFQMC_FP64 || p->fp64_islands;
+    const bool f64c = p->precision == AFQMC_FP64 || p->fp64_islands == 1;
     if (md_energy_smem(p->M, p->n_up, p->n_dn, nact[0], nact[1], p->n_det, f64c) > 227 * 1024)
       return fail(nullptr, AFQMC_E_INVALID,
                   "multi-determinant trial too large for the on-chip energy kernel");

@@ -405,9 +405,12 @@ __host__ __device__ __forceinline__ size_t overlap_region(int M, int ns) {
 //  2. Gauss-Jordan elimination with partial pivoting gives (P A)^-1 and the
 //     pivots, which are the diagonal of the U in P A = L U; the
 //     log-determinant sum_k ln U_kk (+ i pi per odd row-swap count) is
-//     accumulated in FP64. Step k reads one buffer and writes the other, so
-//     it needs a single block barrier; the warp that owns column k + 1 picks
-//     the next pivot from the values it has just written.
+//     accumulated in FP64. Up to 32 electrons per spin one warp eliminates
+//     in place with no block barrier (one row per lane, rows left where
+//     they are and the pivot order recorded). Above that, all warps share
+//     each step: step k reads one buffer and writes the other, so it needs a
+//     single block barrier, and the warp that owns column k + 1 picks the
+//     next pivot from the values it has just written.
 //  3. Theta = Phi A^-1 = (Phi (P A)^-1) P: a block product scattered to the
 //     permuted columns. A^-1 itself (for the multi-determinant ratios) is
 //     (P A)^-1 with the same column permutation.
@@ -500,78 +503,152 @@ overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
     }
   }
   __syncthreads();
-  if (warp == 0) {                                    // first pivot: column 0
-    R best = R(-1);
-    int bi = 0;
-    for (int i = lane; i < ns; i += 32) {
-      const cx<R> v = A0[i * lda];
-      const R m = v.x * v.x + v.y * v.y;
-      if (m > best) { best = m; bi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const R ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    publish(A0, 0, bi, best);
-  }
-  __syncthreads();
   cx<R>* cur = A0;
-  cx<R>* nxt = A1;
-  if (!singular) {
-    for (int k = 0; k < ns; ++k) {
-      const int p = piv[k & 1];
-      const cx<R>* prow = cur + p * lda;
-      const cx<R> ipv = ipv_s[k & 1];
-      if (tid == 0) {
-        if (p != k) {
-          const int t = perm[k];
-          perm[k] = perm[p];
-          perm[p] = t;
-          nswap ^= 1;
-        }
-      }
-      // rows k and p trade places: row i of the result comes from row src(i)
-      // (the new pivot row k is row p scaled: p - (1 - 1/pv) p, one formula for all rows)
-      for (int i = lane; i < ns; i += 32) {
-        const cx<R>* irow = cur + (i == k ? p : (i == p ? k : i)) * lda;
-        cx<R> f, colk;
-        if (i == k) {
-          f = mk<R>(R(1) - ipv.x, -ipv.y);
-          colk = ipv;
-        } else {
-          f = mul_c(irow[k], ipv);
-          colk = mk<R>(-f.x, -f.y);
-        }
-        cx<R>* orow = nxt + i * lda;
-        for (int j = warp; j < ns; j += nwarps)
-          orow[j] = (j == k) ? colk : sub_mul(irow[j], f, prow[j]);
-      }
-      const int jn = k + 1;
-      if (jn < ns && jn % nwarps == warp) {           // next pivot, from this warp's own writes
+  if (ns <= 32) {
+    // One warp eliminates in place, lane i owning row i, with no block
+    // barrier: the pivot of column k is the largest |a_ik|^2 among the rows
+    // not yet used as pivots (ties to the lower row); every other row i
+    // subtracts f_i = a_ik / pivot times the pivot row and keeps -f_i in
+    // column k, then the pivot row is scaled by 1 / pivot (1 / pivot in
+    // column k). Row p_k (the pivot row of step k) then holds row k of
+    // (P A)^-1, where row k of P A is row p_k of A; the pivots are the same
+    // U_kk as those of the row-swapping elimination, so ln det A = sum ln U_kk
+    // plus i pi when the permutation k -> p_k is odd.
+    if (warp == 0) {
+      const bool mine = lane < ns;
+      cx<R>* arow = A0 + (mine ? lane : 0) * lda;
+      bool used = !mine, sing_w = false;
+      for (int k = 0; k < ns; ++k) {
         R best = R(-1);
-        int bi = jn;
-        for (int i = lane; i < ns; i += 32) {
-          if (i < jn) continue;
-          const cx<R> v = nxt[i * lda + jn];
+        if (!used) {
+          const cx<R> v = arow[k];
           const R m = v.x * v.x + v.y * v.y;
-          if (m > best) { best = m; bi = i; }
+          if (m > best) best = m;                      // a NaN stays out
         }
+        int bi = lane;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const R ob = __shfl_xor_sync(0xffffffffu, best, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        __syncwarp();                                  // the lanes' writes of column jn
-        publish(nxt, jn, bi, best);
+        if (!(best > R(0))) {                          // uniform over the warp
+          if (lane == 0) singular = 1;
+          sing_w = true;
+          break;
+        }
+        const int p = bi;
+        const cx<R>* prow = A0 + p * lda;
+        const cx<R> pv = prow[k];
+        const R pd = pv.x * pv.x + pv.y * pv.y;
+        const cx<R> ipv = mk<R>(pv.x / pd, -pv.y / pd);
+        if (lane == 0) {
+          pvs[k] = pv;
+          perm[k] = p;
+        }
+        if (mine && lane != p) {                       // reads row p, writes row i
+          const cx<R> f = mul_c(arow[k], ipv);
+          for (int j = 0; j < ns; ++j) arow[j] = sub_mul(arow[j], f, prow[j]);
+          arow[k] = mk<R>(-f.x, -f.y);
+        }
+        __syncwarp();
+        if (mine) {                                    // the pivot row, element j = lane
+          const cx<R> v = A0[p * lda + lane];
+          A0[p * lda + lane] = lane == k ? ipv : mul_c(v, ipv);
+        }
+        if (lane == p) used = true;
+        __syncwarp();
       }
-      __syncthreads();
-      cx<R>* t = cur;
-      cur = nxt;
-      nxt = t;
-      if (singular) break;
+      if (!sing_w) {                                   // parity of k -> p_k by inversions
+        int inv = 0;
+        if (mine)
+          for (int j = lane + 1; j < ns; ++j) inv += perm[j] < perm[lane] ? 1 : 0;
+        inv = warp_sum(inv);
+        if (lane == 0) nswap = inv & 1;
+      }
+    }
+    __syncthreads();
+    if (!singular) {                                   // (P A)^-1 row k = row p_k
+      for (int e = tid; e < ns * ns; e += nt) {
+        const int k = e / ns, j = e - k * ns;
+        A1[k * lda + j] = A0[perm[k] * lda + j];
+      }
+      cur = A1;
+    }
+    __syncthreads();
+  } else {
+    if (warp == 0) {                                    // first pivot: column 0
+      R best = R(-1);
+      int bi = 0;
+      for (int i = lane; i < ns; i += 32) {
+        const cx<R> v = A0[i * lda];
+        const R m = v.x * v.x + v.y * v.y;
+        if (m > best) { best = m; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      publish(A0, 0, bi, best);
+    }
+    __syncthreads();
+    cx<R>* nxt = A1;
+    if (!singular) {
+      for (int k = 0; k < ns; ++k) {
+        const int p = piv[k & 1];
+        const cx<R>* prow = cur + p * lda;
+        const cx<R> ipv = ipv_s[k & 1];
+        if (tid == 0) {
+          if (p != k) {
+            const int t = perm[k];
+            perm[k] = perm[p];
+            perm[p] = t;
+            nswap ^= 1;
+          }
+        }
+        // rows k and p trade places: row i of the result comes from row src(i)
+        // (the new pivot row k is row p scaled: p - (1 - 1/pv) p, one formula for all rows)
+        for (int i = lane; i < ns; i += 32) {
+          const cx<R>* irow = cur + (i == k ? p : (i == p ? k : i)) * lda;
+          cx<R> f, colk;
+          if (i == k) {
+            f = mk<R>(R(1) - ipv.x, -ipv.y);
+            colk = ipv;
+          } else {
+            f = mul_c(irow[k], ipv);
+            colk = mk<R>(-f.x, -f.y);
+          }
+          cx<R>* orow = nxt + i * lda;
+          for (int j = warp; j < ns; j += nwarps)
+            orow[j] = (j == k) ? colk : sub_mul(irow[j], f, prow[j]);
+        }
+        const int jn = k + 1;
+        if (jn < ns && jn % nwarps == warp) {           // next pivot, from this warp's own writes
+          R best = R(-1);
+          int bi = jn;
+          for (int i = lane; i < ns; i += 32) {
+            if (i < jn) continue;
+            const cx<R> v = nxt[i * lda + jn];
+            const R m = v.x * v.x + v.y * v.y;
+            if (m > best) { best = m; bi = i; }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          __syncwarp();                                  // the lanes' writes of column jn
+          publish(nxt, jn, bi, best);
+        }
+        __syncthreads();
+        cx<R>* t = cur;
+        cur = nxt;
+        nxt = t;
+        if (singular) break;
+      }
     }
   }
   const int sing = singular;
@@ -612,7 +689,7 @@ overlap_kernel(int M, int n_up, int n_dn, const T* __restrict__ Phi,
     for (int e = tid; e < ns * ns; e += nt) {
       const int r = e / ns, i = e - r * ns;
       const cx<R> y = sing ? mk<R>(R(0), R(0)) : cur[r * lda + i];
-      Ao[(long)r * nmax + perm[i]] = make_double2((double)y.x, (double)y.y);
+      Ao[(long)r * nmax + (sing ? i : perm[i])] = make_double2((double)y.x, (double)y.y);
     }
   }
 }

@@ -77,6 +77,7 @@ def test_invalid_inputs_rejected_before_device(lib, mutate, needle):
     (dict(weight_mode=1, n_det=2), "one-determinant"),
     (dict(block_sparse=3), "block_sparse"),
     (dict(block_sparse=1), "not block-diagonal"),
+    (dict(fp64_islands=3), "fp64_islands"),
 ])
 def test_invalid_params_rejected(lib, kw, needle):
     from paper_1804_03310_gb300 import AfqmcError

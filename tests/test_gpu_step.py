@@ -109,7 +109,7 @@ def test_c1_twenty_steps_fp32():
     print("c1 fp32 worst", w)
 
 
-@pytest.mark.parametrize("islands", [False, True])
+@pytest.mark.parametrize("islands", [False, True, "qr"])
 def test_c2_full_size_sampled_fp32(islands):
     s = config_c2(pc_every=0)
     w = side_by_side(s, "fp32", 20, 1e-4, walkers=[0, 1023], energy_at=(10, 20),
@@ -290,7 +290,7 @@ def test_c3_full_size_sampled_tf32x3():
 
 
 @pytest.mark.parametrize("shape", ["c2", "c3"])
-@pytest.mark.parametrize("islands", [False, True])
+@pytest.mark.parametrize("islands", [False, True, "qr"])
 def test_orthonormality_after_qr(shape, islands):
     """The QR runs through the Cholesky factor of the Gram matrix, whose
     orthogonality loss grows with cond(Phi)^2; between orthonormalisations
