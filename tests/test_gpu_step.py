@@ -245,7 +245,7 @@ def test_kernel_timing_and_launch_counter():
 # ---------------------------------------------------------------- tensor cores
 # TF32X3 (three TF32 products per term) must meet the reduced-precision bar
 # of 1e-4; plain TF32 (10-bit mantissa operands) misses it and is held to
-# 5e-2 (measured about 1.4e-2 at the H-chain shape).
+# 5e-2 (measured 1.4e-2 to 2.7e-2 at the H-chain shape, per-walker weights).
 TC_TOL = {"tf32x3": 1e-4, "bf16x3": 1e-4, "tf32": 5e-2}   # plain TF32 misses the 1e-4 bar
 
 
