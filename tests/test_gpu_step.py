@@ -268,7 +268,7 @@ def test_c2_full_size_sampled_tensor_cores(prec):
     (64, 20, 12, 129, 9),   # largest on-chip Taylor size
     (70, 5, 9, 130, 40),    # M > 64: CUDA-core Taylor, tensor-core GEMMs
     (12, 4, 0, 9, 3),       # no down electrons
-    (40, 32, 31, 50, 6),    # largest spin block of the one-warp inverse and QR
+    (40, 32, 31, 50, 6),    # largest spin block of the one-warp elimination
     (72, 33, 8, 70, 5),     # spin block above it: block-wide elimination
 ])
 def test_ragged_sizes_tensor_cores(M, nu, nd, G, W):
