@@ -639,11 +639,12 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     }
     if (fuse_b) {                          // t0 = Phi + dB Phi
       if (img_pending) {
-        if (!mbar_wait(smem_u32(lbar), 0)) {
+        if (mbar_wait(smem_u32(lbar), 0)) {
+          img_pending = false;
+        } else {                           // still in flight: drained at teardown
           flag_timeout(status);
           s_fail = 1;
         }
-        img_pending = false;
       }
       if (active) {
         sync_half();
@@ -667,12 +668,13 @@ tc_taylor_kernel(int W, int M, int N, int order, const float* __restrict__ V,
     // writes the K columns 64h .. 64h + 63 of its rows
     const float* vsrc = Vw;
     if (vpre) {
-      if (!mbar_wait(smem_u32(vbar), vphase)) {
+      if (mbar_wait(smem_u32(vbar), vphase)) {
+        vphase ^= 1u;
+        v_inflight = false;
+      } else {                             // still in flight: drained at teardown
         flag_timeout(status);
         s_fail = 1;
       }
-      vphase ^= 1u;
-      v_inflight = false;
       vsrc = vst;
     }
     {
@@ -852,13 +854,19 @@ tc_taylor_bf16_kernel(int W, int M, int N, int order, const float* __restrict__ 
   const uint32_t sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
   const int MM = M * M;
 
+  // a wait of this thread that gave up: the thread issues no further MMA
+  // (as the issuer, thread 0) and waits no more; thread 0 then waits once
+  // more, bounded, for that commit before the CTA frees its tensor memory
+  bool failed = false;
+  uint32_t fail_parity = 0;
   auto wait_mma = [&]() {
-    const bool ok = mbar_wait(smem_u32(bar), phase);
-    phase ^= 1u;
-    if (!ok) {
+    if (!failed && !mbar_wait(smem_u32(bar), phase)) {
       flag_timeout(status);
       s_fail = 1;
+      failed = true;
+      fail_parity = phase;
     }
+    phase ^= 1u;
     fence_after_sync();
   };
   auto sync_for_mma = [&]() {
@@ -914,14 +922,15 @@ tc_taylor_bf16_kernel(int W, int M, int N, int order, const float* __restrict__ 
       put_operand_bf16(sBhi, sBlo, sw128_offset_bf16(j, r, 64), acc[j]);
     if (fuse_b) {                          // t0 = Phi + dB Phi
       if (img_pending) {
-        if (!mbar_wait(smem_u32(lbar), 0)) {
+        if (mbar_wait(smem_u32(lbar), 0)) {
+          img_pending = false;
+        } else {                           // still in flight: drained at teardown
           flag_timeout(status);
           s_fail = 1;
         }
-        img_pending = false;
       }
       sync_for_mma();
-      if (tid == 0) {
+      if (tid == 0 && !failed) {
         half_products();
         mma_commit(smem_u32(bar));
       }
@@ -963,7 +972,7 @@ tc_taylor_bf16_kernel(int W, int M, int N, int order, const float* __restrict__ 
     tmem_wait_st();
     for (int term = 1; term <= order; ++term) {
       sync_for_mma();
-      if (tid == 0) {
+      if (tid == 0 && !failed) {
         series_products();
         mma_commit(smem_u32(bar));
       }
@@ -985,7 +994,7 @@ tc_taylor_bf16_kernel(int W, int M, int N, int order, const float* __restrict__ 
     }
     if (fuse_b) {                          // out = s + dB s
       sync_for_mma();
-      if (tid == 0) {
+      if (tid == 0 && !failed) {
         half_products();
         mma_commit(smem_u32(bar));
       }
@@ -1009,7 +1018,9 @@ tc_taylor_bf16_kernel(int W, int M, int N, int order, const float* __restrict__ 
     fence_after_sync();
     if (s_fail) break;
   }
-  if (img_pending && !mbar_wait(smem_u32(lbar), 0)) flag_timeout(status);
+  if (img_pending && !mbar_wait(smem_u32(lbar), 0)) flag_timeout(status);   // no copy may outlive the CTA
+  if (tid == 0 && failed && !mbar_wait(smem_u32(bar), fail_parity))  // nor an MMA the allocation
+    flag_timeout(status);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, TB_TMEM_COLS);
