@@ -540,9 +540,9 @@ def _blocks(s, precision, n_blocks, **kw):
 
 def islands_leg(s, precision, value):
     """The bench workload with FP64 arithmetic islands beside the default
-    FP32 arithmetic there: fp64_islands = 2, the QR alone in FP64 (the
-    spec form: FP64 only for the orthonormalisation, the
-    log-determinants and the weights), and fp64_islands = 1, the small
+    FP32 arithmetic there: fp64_islands = 2, the QR alone in FP64 (the form
+    the TM-atom configuration states: FP64 only for the orthonormalisation,
+    the log-determinants and the weights), and fp64_islands = 1, the small
     inverse as well."""
     import torch
     from paper_1804_03310_gb300 import Afqmc
